@@ -1,0 +1,182 @@
+/*
+ * bfv_lr.h -- C ABI of the GB300 library for BFV-encrypted logistic-regression scoring.
+ *
+ * Paper: "Scalable privacy-preserving cancer type prediction with homomorphic encryption"
+ * (Sarkar et al.). The calls follow the private inference protocol of Section 4.2.2
+ * (Fig. 2): the client encodes and encrypts its feature matrix X (|X| x f), the server
+ * multiplies the ciphertexts by the encoded transposed weights and adds the encoded
+ * biases, the client decrypts and decodes W x + b. The server product is either the
+ * packed algorithm of Section 4.2.3 / Algorithm 1 (multiply, add_many, rotate and
+ * accumulate, mask, compress) or the "standard" per-element product of Section 5.2.3.
+ *
+ * Conventions for every call:
+ *  - Return value: BFV_OK (0) or a negative BFV_ERR_* code. On error nothing that the
+ *    caller owns is freed, and output buffers hold unspecified values.
+ *  - Device buffers are plain device pointers (for example from torch tensors); the
+ *    library never takes ownership of caller memory. `stream` is a cudaStream_t passed as
+ *    uintptr_t (0 = legacy default stream). Calls that take a stream enqueue work and
+ *    return without synchronising unless stated otherwise.
+ *  - Handles (bfv_ctx, bfv_keys, bfv_model) are opaque, owned by the library, freed by the
+ *    matching *_free call, and bound to the CUDA device that was current at creation.
+ *  - A ciphertext crossing the boundary is uint64[2][L][N] in coefficient form, limb-major:
+ *    component c (0 or 1), prime index l, coefficient k; every residue is in [0, q_l).
+ *    A plaintext is uint64[N], coefficients in [0, t).
+ *  - Arithmetic is exact modular integer arithmetic; results are bit-for-bit deterministic.
+ */
+#ifndef BFV_LR_H
+#define BFV_LR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define BFV_OK 0
+#define BFV_ERR_INVALID_ARG (-1) /* null pointer, size out of range, handle mismatch */
+#define BFV_ERR_BAD_PARAMS (-2)  /* unsupported or inconsistent BFV parameters */
+#define BFV_ERR_OOM (-3)         /* a device allocation failed */
+#define BFV_ERR_OVER_BUDGET (-4) /* caller's workspace or memory budget too small */
+#define BFV_ERR_TIMEOUT (-5)     /* a bounded wait ran out */
+#define BFV_ERR_CUDA (-6)        /* a CUDA runtime call failed */
+
+/* BFV parameter shape. Primes: the L+1 largest primes below 2^prime_bits that are 1 mod 2N,
+ * in descending order; the first L form the ciphertext modulus Q, the last is the
+ * key-switching prime P. Supported: N in {4096, 8192, 16384}, 1 <= L <= 15,
+ * 30 <= prime_bits <= 60, t prime with t = 1 mod 2N and t < 2^31. The Gaussian error has
+ * width sigma = sigma_num / sigma_den and is truncated at floor(6 sigma). */
+typedef struct bfv_params {
+    uint32_t N;
+    uint32_t L;
+    uint32_t prime_bits;
+    uint32_t reserved;
+    uint64_t t;
+    uint32_t sigma_num;
+    uint32_t sigma_den;
+} bfv_params;
+
+typedef struct bfv_ctx bfv_ctx;
+typedef struct bfv_keys bfv_keys;
+typedef struct bfv_model bfv_model;
+
+/* ------------------------------------------------------------------ host-only helpers */
+
+/* Library ABI version (currently 1). */
+int bfv_abi_version(void);
+
+/* The L+1 primes of a parameter shape (host computation, no GPU needed).
+ * primes_out: caller buffer of L+1 uint64. */
+int bfv_params_primes(const bfv_params *p, uint64_t *primes_out);
+
+/* Gaussian sampler thresholds T_k = floor(2^64 Pr[|e| <= k]), k = 0 .. len-1, for width
+ * sigma_num/sigma_den (host computation). out: caller buffer of at least 32 uint64;
+ * *len receives the count (floor(6 sigma)). */
+int bfv_gaussian_table(uint32_t sigma_num, uint32_t sigma_den, uint64_t *out, int *len);
+
+/* ------------------------------------------------------------------ context and keys */
+
+/* Builds the parameter set (primes, NTT tables, CRT and rounding constants) on the current
+ * CUDA device. The paper uses SEAL's BFV (Section 5.2); these are its textbook parts. */
+int bfv_setup(const bfv_params *p, bfv_ctx **out);
+int bfv_ctx_free(bfv_ctx *ctx);
+
+/* Copies out: primes (L+1 uint64, may be NULL), the slot-map root omega mod t (may be NULL),
+ * and floor(Q/t) mod q_l for l < L (L uint64, may be NULL). */
+int bfv_ctx_query(const bfv_ctx *ctx, uint64_t *primes, uint64_t *omega, uint64_t *delta_mod_q);
+
+/* Generates the secret key s (ternary), the public key pk = ([-(a s + e)]_Q, a) and the
+ * Galois keys for the rotate-and-sum of Algorithm 1 (the row swap 2N-1, then 3^(N/4), ...,
+ * 3^1 mod 2N), one key-switching digit per ciphertext prime over Q*P. Randomness: ChaCha20
+ * (RFC 8439) blocks keyed by `seed`. Keys stay resident on the device. Synchronises `stream`. */
+int bfv_keygen(bfv_ctx *ctx, uint64_t seed, uintptr_t stream, bfv_keys **out);
+int bfv_keys_free(bfv_keys *keys);
+
+/* Debug / parity export of key material in coefficient form (device buffers):
+ * sk: int8[N] (may be NULL); pk: uint64[2][L][N] (may be NULL);
+ * gk: uint64[n_galois][L][2][L+1][N] (may be NULL), n_galois = log2 N. Synchronises. */
+int bfv_keys_export(const bfv_ctx *ctx, const bfv_keys *keys, int8_t *sk, uint64_t *pk, uint64_t *gk,
+                    uintptr_t stream);
+
+/* ------------------------------------------------------------------ client side */
+
+/* Batch encoding (Section 4.2.2: n values per plaintext): slots int64[count][N] (any integers,
+ * taken mod t) -> plaintext polynomials uint64[count][N] with m(omega^e_l) = slot_l, where
+ * slot l = r*(N/2) + c sits at exponent e_l = 3^c (r = 0) or 2N - 3^c (r = 1) mod 2N and
+ * omega = g^((t-1)/2N), g the smallest primitive root mod t. Device buffers. */
+int bfv_encode(bfv_ctx *ctx, const int64_t *slots, size_t count, uint64_t *pt, uintptr_t stream);
+
+/* Inverse of bfv_encode: plaintexts uint64[count][N] -> slot values int64[count][N] in [0, t). */
+int bfv_decode(bfv_ctx *ctx, const uint64_t *pt, size_t count, int64_t *slots, uintptr_t stream);
+
+/* Packs and encodes the client's binary/integer feature matrix X (uint8[nX][f], device) for the
+ * packed product: plaintext (i, k) holds features k*N .. k*N+N-1 of individual i in slots
+ * 0 .. N-1, zero past f (Section 4.2.2: X is |X| x ceil(f/n) plaintexts).
+ * pt: uint64[nX][ceil(f/N)][N]. */
+int bfv_encode_features(bfv_ctx *ctx, const uint8_t *X, size_t nX, size_t f, uint64_t *pt, uintptr_t stream);
+
+/* Packs and encodes X (uint8[nX][f], device, nX <= N) for the standard product: plaintext f
+ * holds feature f of individual i in slot i (zero for i >= nX). pt: uint64[f][N]. */
+int bfv_encode_feature_columns(bfv_ctx *ctx, const uint8_t *X, size_t nX, size_t f, uint64_t *pt,
+                               uintptr_t stream);
+
+/* Public-key encryption c = ([pk0 u + e1 + Delta m]_Q, [pk1 u + e2]_Q), Delta = floor(Q/t),
+ * of count plaintexts pt (uint64[count][N]) into ct (uint64[count][2][L][N]). Ciphertext c
+ * draws (u, e1, e2) from ChaCha20 blocks keyed by `seed` with nonce (6, obj0 + c, 0): block k
+ * gives u_k (word 0), e1_k (words 1-3), e2_k (words 4-6). ws: device workspace of at least
+ * bfv_encrypt_workspace(count) bytes. */
+int bfv_encrypt_workspace(const bfv_ctx *ctx, size_t count, size_t *bytes);
+int bfv_encrypt(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *pt, size_t count, uint64_t seed,
+                uint32_t obj0, uint64_t *ct, void *ws, size_t ws_bytes, uintptr_t stream);
+
+/* Decryption m = round(t [c0 + c1 s]_Q / Q) mod t, computed exactly (mixed-radix CRT and
+ * multi-word integer division, no floating point): ct uint64[count][2][L][N] ->
+ * pt uint64[count][N]. ws: at least bfv_decrypt_workspace(count) bytes. */
+int bfv_decrypt_workspace(const bfv_ctx *ctx, size_t count, size_t *bytes);
+int bfv_decrypt(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *ct, size_t count, uint64_t *pt,
+                void *ws, size_t ws_bytes, uintptr_t stream);
+
+/* ------------------------------------------------------------------ server side */
+
+/* Encodes the model (Section 4.2.2): the transposed weights W^T as |Y| x ceil(f/N)
+ * plaintexts (weight (k*N + s, j) in slot s of plaintext (j, k)), kept on the device in the
+ * evaluation form of every ciphertext prime, and the biases b_j (added as Delta [b_j]_t).
+ * W: int64[f][nY] row-major, b: int64[nY], both HOST pointers. Synchronises `stream`. */
+int bfv_model_prepare(bfv_ctx *ctx, const int64_t *W, const int64_t *b, size_t f, size_t nY,
+                      uintptr_t stream, bfv_model **out);
+int bfv_model_free(bfv_model *model);
+
+/* Packed product, Algorithm 1 with bias: for each pair g = i*|Y| + j,
+ *   c = sum_k X[i][k] * W[j][k];  c += rot_g(c) for the log2 N Galois elements in order;
+ *   c0 += Delta [b_j]_t;  c *= mask_g (one-hot at slot g mod N);  Y[g / N] += c.
+ * X_ct: uint64[nX][ceil(f/N)][2][L][N] (device); Y_ct: uint64[ceil(nX*nY/N)][2][L][N].
+ * Decrypting Y gives (x_i . W[:, j] + b_j) mod t in slot g mod N of output g / N.
+ * ws: at least bfv_lr_scores_packed_workspace(nX) bytes. Up to `pair_chunk` pairs are
+ * in flight at once (0 = the library's choice); the workspace size depends on it. */
+int bfv_lr_scores_packed_workspace(const bfv_ctx *ctx, const bfv_model *model, size_t nX, size_t pair_chunk,
+                                   size_t *bytes);
+int bfv_lr_scores_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint64_t *X_ct,
+                         size_t nX, uint64_t *Y_ct, void *ws, size_t ws_bytes, size_t pair_chunk,
+                         uintptr_t stream);
+
+/* Standard product (Section 5.2.3): ciphertext f of X_ct holds feature f of individual i in
+ * slot i (nX <= N); output j = sum_f w[f][j] X_ct[f] + Delta [b_j]_t, weights as integer
+ * scalars. X_ct: uint64[f][2][L][N]; Y_ct: uint64[nY][2][L][N]. Needs no workspace. */
+int bfv_lr_scores_standard(bfv_ctx *ctx, const bfv_model *model, const uint64_t *X_ct, size_t nX,
+                           uint64_t *Y_ct, uintptr_t stream);
+
+/* ------------------------------------------------------------------ diagnostics */
+
+/* Copies pair g's ciphertext out of a packed-product workspace, in coefficient form
+ * (uint64[2][L][N]): after a bfv_lr_scores_packed call whose last chunk contained g this is
+ * the masked pair ciphertext before compression. For parity tests at full size. */
+int bfv_lr_packed_pair_from_workspace(bfv_ctx *ctx, const bfv_model *model, size_t nX, size_t pair_chunk,
+                                      const void *ws, size_t g, uint64_t *ct_out, uintptr_t stream);
+
+/* Number of kernel launches the library issued since bfv_setup (for launch accounting). */
+int bfv_launch_count(const bfv_ctx *ctx, uint64_t *count);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* BFV_LR_H */

@@ -1,0 +1,349 @@
+"""GB300 (sm_103a) library for BFV-encrypted logistic-regression scoring.
+
+Thin Python binding over the C ABI in include/bfv_lr.h: every call marshals torch
+tensors (device memory, streams) into plain pointers and calls the CUDA library of the
+same name; every step of the encrypted path runs in the library's kernels. There is no
+fallback: if the compiled library is missing, importing the binding's calls raises.
+
+Paper: "Scalable privacy-preserving cancer type prediction with homomorphic encryption",
+Section 4.2.2 (protocol), Section 4.2.3 / Algorithm 1 (packed product), Section 5.2.3
+(standard product).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+from concurrent.futures import ThreadPoolExecutor
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_CSRC = os.path.join(_HERE, "csrc")
+_BUILD = os.path.join(_HERE, "_build")
+LIB_PATH = os.path.join(_BUILD, "libbfv_lr.so")
+_ROOT = os.path.dirname(_HERE)
+_INCLUDE = os.path.join(_ROOT, "include")
+SOURCES = ["capi.cu", "k_scheme.cu", "k_packed.cu", "k_standard.cu"]
+ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
+
+BFV_OK, BFV_ERR_INVALID_ARG, BFV_ERR_BAD_PARAMS, BFV_ERR_OOM = 0, -1, -2, -3
+BFV_ERR_OVER_BUDGET, BFV_ERR_TIMEOUT, BFV_ERR_CUDA = -4, -5, -6
+_ERRS = {-1: "INVALID_ARG", -2: "BAD_PARAMS", -3: "OOM", -4: "OVER_BUDGET", -5: "TIMEOUT", -6: "CUDA"}
+
+
+class BfvError(RuntimeError):
+    def __init__(self, fn, rc):
+        super().__init__(f"{fn} failed: BFV_ERR_{_ERRS.get(rc, rc)} ({rc})")
+        self.code = rc
+
+
+def _nvcc():
+    for c in (os.environ.get("NVCC"), "/usr/local/cuda/bin/nvcc", "nvcc"):
+        if c and (os.path.sep not in c or os.path.exists(c)):
+            return c
+    return "nvcc"
+
+
+def build(force: bool = False, verbose: bool = False) -> str:
+    """Compile the CUDA library in-tree for sm_103a (translation units in parallel)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    deps = [os.path.join(_CSRC, f) for f in os.listdir(_CSRC)] + [os.path.join(_INCLUDE, "bfv_lr.h")]
+    newest = max(os.path.getmtime(d) for d in deps)
+    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
+        return LIB_PATH
+    nvcc = _nvcc()
+    flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
+                    "-I", _INCLUDE, "-I", _CSRC]
+
+    def compile_one(src):
+        obj = os.path.join(_BUILD, src.replace(".cu", ".o"))
+        cmd = [nvcc, "-c", os.path.join(_CSRC, src), "-o", obj] + flags
+        r = subprocess.run(cmd, capture_output=True, text=True)
+        if r.returncode != 0:
+            raise RuntimeError(f"nvcc failed for {src}:\n{r.stdout}\n{r.stderr}")
+        if verbose:
+            print(r.stdout, r.stderr)
+        return obj
+
+    with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
+        objs = list(ex.map(compile_one, SOURCES))
+    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    r = subprocess.run([nvcc, "-shared", "-cudart", "shared", "-o", tmp] + ARCH + objs, capture_output=True, text=True)
+    if r.returncode != 0:
+        raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
+    os.replace(tmp, LIB_PATH)
+    return LIB_PATH
+
+
+class Params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint32), ("L", ctypes.c_uint32), ("prime_bits", ctypes.c_uint32),
+                ("reserved", ctypes.c_uint32), ("t", ctypes.c_uint64), ("sigma_num", ctypes.c_uint32),
+                ("sigma_den", ctypes.c_uint32)]
+
+
+_lib = None
+_lock = threading.Lock()
+_vp, _u64, _sz, _up = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_size_t
+
+# (name, argtypes) of every exported function; the CPU tests check the library exports these.
+SIGNATURES = {
+    "bfv_abi_version": [],
+    "bfv_params_primes": [ctypes.POINTER(Params), _vp],
+    "bfv_gaussian_table": [ctypes.c_uint32, ctypes.c_uint32, _vp, ctypes.POINTER(ctypes.c_int)],
+    "bfv_setup": [ctypes.POINTER(Params), ctypes.POINTER(_vp)],
+    "bfv_ctx_free": [_vp],
+    "bfv_ctx_query": [_vp, _vp, _vp, _vp],
+    "bfv_keygen": [_vp, _u64, _up, ctypes.POINTER(_vp)],
+    "bfv_keys_free": [_vp],
+    "bfv_keys_export": [_vp, _vp, _vp, _vp, _vp, _up],
+    "bfv_encode": [_vp, _vp, _sz, _vp, _up],
+    "bfv_decode": [_vp, _vp, _sz, _vp, _up],
+    "bfv_encode_features": [_vp, _vp, _sz, _sz, _vp, _up],
+    "bfv_encode_feature_columns": [_vp, _vp, _sz, _sz, _vp, _up],
+    "bfv_encrypt_workspace": [_vp, _sz, ctypes.POINTER(_sz)],
+    "bfv_encrypt": [_vp, _vp, _vp, _sz, _u64, ctypes.c_uint32, _vp, _vp, _sz, _up],
+    "bfv_decrypt_workspace": [_vp, _sz, ctypes.POINTER(_sz)],
+    "bfv_decrypt": [_vp, _vp, _vp, _sz, _vp, _vp, _sz, _up],
+    "bfv_model_prepare": [_vp, _vp, _vp, _sz, _sz, _up, ctypes.POINTER(_vp)],
+    "bfv_model_free": [_vp],
+    "bfv_lr_scores_packed_workspace": [_vp, _vp, _sz, _sz, ctypes.POINTER(_sz)],
+    "bfv_lr_scores_packed": [_vp, _vp, _vp, _vp, _sz, _vp, _vp, _sz, _sz, _up],
+    "bfv_lr_scores_standard": [_vp, _vp, _vp, _sz, _vp, _up],
+    "bfv_lr_packed_pair_from_workspace": [_vp, _vp, _sz, _sz, _vp, _sz, _vp, _up],
+    "bfv_launch_count": [_vp, ctypes.POINTER(_u64)],
+}
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built (no fallback path)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"CUDA library not built ({LIB_PATH}); run __graft_entry__.build()")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, args in SIGNATURES.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            _lib = L
+    return _lib
+
+
+def _call(name, *args):
+    rc = getattr(lib(), name)(*args)
+    if rc != BFV_OK:
+        raise BfvError(name, rc)
+
+
+def _ptr(t):
+    return ctypes.c_void_p(t.data_ptr()) if t is not None else None
+
+
+def _stream(stream=None):
+    import torch
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return s.cuda_stream
+
+
+def primes(N: int, L: int, prime_bits: int, t: int) -> list[int]:
+    """The L+1 primes of a parameter shape (host computation)."""
+    p = Params(N, L, prime_bits, 0, t, 16, 5)
+    out = (ctypes.c_uint64 * (L + 1))()
+    _call("bfv_params_primes", ctypes.byref(p), ctypes.cast(out, _vp))
+    return list(out)
+
+
+def gaussian_table(num: int = 16, den: int = 5) -> list[int]:
+    out = (ctypes.c_uint64 * 32)()
+    n = ctypes.c_int()
+    _call("bfv_gaussian_table", num, den, ctypes.cast(out, _vp), ctypes.byref(n))
+    return list(out)[: n.value]
+
+
+class Keys:
+    def __init__(self, ctx, handle):
+        self.ctx, self.handle = ctx, handle
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bfv_keys_free(self.handle)
+            self.handle = None
+
+
+class Model:
+    def __init__(self, ctx, handle, f, nY):
+        self.ctx, self.handle, self.f, self.nY = ctx, handle, f, nY
+        self.K = -(-f // ctx.N)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bfv_model_free(self.handle)
+            self.handle = None
+
+
+class Context:
+    """A BFV parameter set on the current CUDA device (bfv_setup)."""
+
+    def __init__(self, N: int, L: int, prime_bits: int, t: int, sigma_num: int = 16, sigma_den: int = 5):
+        import torch
+        if not torch.cuda.is_available():
+            raise RuntimeError("no CUDA device: the library has no CPU path")
+        self.N, self.L, self.t = N, L, t
+        self.params = Params(N, L, prime_bits, 0, t, sigma_num, sigma_den)
+        h = _vp()
+        _call("bfv_setup", ctypes.byref(self.params), ctypes.byref(h))
+        self.handle = h
+        pr = (ctypes.c_uint64 * (L + 1))()
+        om = ctypes.c_uint64()
+        de = (ctypes.c_uint64 * L)()
+        _call("bfv_ctx_query", h, ctypes.cast(pr, _vp), ctypes.byref(om), ctypes.cast(de, _vp))
+        self.primes, self.omega, self.delta_mod_q = list(pr), om.value, list(de)
+        self.device = torch.cuda.current_device()
+
+    @classmethod
+    def from_shape(cls, shape):
+        return cls(shape.N, shape.L, shape.prime_bits, shape.t, shape.sigma_num, shape.sigma_den)
+
+    def __del__(self):
+        if getattr(self, "handle", None) and _lib is not None:
+            _lib.bfv_ctx_free(self.handle)
+            self.handle = None
+
+    # -- helpers
+    def _empty_u64(self, *shape):
+        import torch
+        return torch.empty(shape, dtype=torch.int64, device=f"cuda:{self.device}")
+
+    def launch_count(self) -> int:
+        n = _u64()
+        _call("bfv_launch_count", self.handle, ctypes.byref(n))
+        return n.value
+
+    # -- keys
+    def keygen(self, seed: int, stream=None) -> Keys:
+        h = _vp()
+        _call("bfv_keygen", self.handle, seed, _stream(stream), ctypes.byref(h))
+        return Keys(self, h)
+
+    def keys_export(self, keys: Keys, stream=None):
+        """(sk int8[N], pk [2][L][N], gk [log2 N][L][2][L+1][N]) in coefficient form, device tensors."""
+        import torch
+        ng = int(round(np.log2(self.N)))
+        sk = torch.empty(self.N, dtype=torch.int8, device=f"cuda:{self.device}")
+        pk = self._empty_u64(2, self.L, self.N)
+        gk = self._empty_u64(ng, self.L, 2, self.L + 1, self.N)
+        _call("bfv_keys_export", self.handle, keys.handle, _ptr(sk), _ptr(pk), _ptr(gk), _stream(stream))
+        return sk, pk, gk
+
+    # -- client
+    def encode(self, slots, stream=None):
+        count = slots.numel() // self.N
+        pt = self._empty_u64(*slots.shape)
+        _call("bfv_encode", self.handle, _ptr(slots.contiguous()), count, _ptr(pt), _stream(stream))
+        return pt
+
+    def decode(self, pt, stream=None):
+        import torch
+        count = pt.numel() // self.N
+        out = torch.empty(pt.shape, dtype=torch.int64, device=pt.device)
+        _call("bfv_decode", self.handle, _ptr(pt.contiguous()), count, _ptr(out), _stream(stream))
+        return out
+
+    def encode_features(self, X, stream=None):
+        nX, f = X.shape
+        K = -(-f // self.N)
+        pt = self._empty_u64(nX, K, self.N)
+        _call("bfv_encode_features", self.handle, _ptr(X.contiguous()), nX, f, _ptr(pt), _stream(stream))
+        return pt
+
+    def encode_feature_columns(self, X, stream=None):
+        nX, f = X.shape
+        pt = self._empty_u64(f, self.N)
+        _call("bfv_encode_feature_columns", self.handle, _ptr(X.contiguous()), nX, f, _ptr(pt), _stream(stream))
+        return pt
+
+    def encrypt_workspace(self, count: int) -> int:
+        n = _sz()
+        _call("bfv_encrypt_workspace", self.handle, count, ctypes.byref(n))
+        return n.value
+
+    def encrypt(self, keys: Keys, pt, seed: int, obj0: int = 0, out=None, ws=None, stream=None):
+        import torch
+        count = pt.numel() // self.N
+        ct = out if out is not None else self._empty_u64(*pt.shape[:-1], 2, self.L, self.N)
+        need = self.encrypt_workspace(count)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(max(need, 1), dtype=torch.uint8, device=pt.device)
+        _call("bfv_encrypt", self.handle, keys.handle, _ptr(pt.contiguous()), count, seed, obj0, _ptr(ct), _ptr(ws),
+              ws.numel(), _stream(stream))
+        return ct
+
+    def decrypt_workspace(self, count: int) -> int:
+        n = _sz()
+        _call("bfv_decrypt_workspace", self.handle, count, ctypes.byref(n))
+        return n.value
+
+    def decrypt(self, keys: Keys, ct, out=None, ws=None, stream=None):
+        import torch
+        count = ct.numel() // (2 * self.L * self.N)
+        pt = out if out is not None else self._empty_u64(*ct.shape[:-3], self.N)
+        need = self.decrypt_workspace(count)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(max(need, 1), dtype=torch.uint8, device=ct.device)
+        _call("bfv_decrypt", self.handle, keys.handle, _ptr(ct.contiguous()), count, _ptr(pt), _ptr(ws), ws.numel(),
+              _stream(stream))
+        return pt
+
+    # -- server
+    def model_prepare(self, W, b, stream=None) -> Model:
+        W = np.ascontiguousarray(W, dtype=np.int64)
+        b = np.ascontiguousarray(b, dtype=np.int64)
+        f, nY = W.shape
+        h = _vp()
+        _call("bfv_model_prepare", self.handle, W.ctypes.data_as(_vp), b.ctypes.data_as(_vp), f, nY,
+              _stream(stream), ctypes.byref(h))
+        return Model(self, h, f, nY)
+
+    def packed_workspace(self, model: Model, nX: int, pair_chunk: int = 0) -> int:
+        n = _sz()
+        _call("bfv_lr_scores_packed_workspace", self.handle, model.handle, nX, pair_chunk, ctypes.byref(n))
+        return n.value
+
+    def lr_scores_packed(self, keys: Keys, model: Model, X_ct, out=None, ws=None, pair_chunk: int = 0, stream=None):
+        import torch
+        nX = X_ct.shape[0]
+        nout = -(-nX * model.nY // self.N)
+        Y = out if out is not None else self._empty_u64(nout, 2, self.L, self.N)
+        need = self.packed_workspace(model, nX, pair_chunk)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=X_ct.device)
+        _call("bfv_lr_scores_packed", self.handle, keys.handle, model.handle, _ptr(X_ct.contiguous()), nX, _ptr(Y),
+              _ptr(ws), ws.numel(), pair_chunk, _stream(stream))
+        return Y
+
+    def lr_scores_standard(self, model: Model, X_ct, nX: int, out=None, stream=None):
+        Y = out if out is not None else self._empty_u64(model.nY, 2, self.L, self.N)
+        _call("bfv_lr_scores_standard", self.handle, model.handle, _ptr(X_ct.contiguous()), nX, _ptr(Y),
+              _stream(stream))
+        return Y
+
+    def packed_pair_from_workspace(self, model: Model, nX: int, pair_chunk: int, ws, g: int, stream=None):
+        out = self._empty_u64(2, self.L, self.N)
+        _call("bfv_lr_packed_pair_from_workspace", self.handle, model.handle, nX, pair_chunk, _ptr(ws), g, _ptr(out),
+              _stream(stream))
+        return out
+
+
+def as_u64(t) -> np.ndarray:
+    """Device/host int64 tensor holding raw 64-bit words -> numpy uint64 array."""
+    return t.detach().cpu().numpy().view(np.uint64)
+
+
+def unpack_packed_scores(N: int, slots, nX: int, nY: int):
+    """Decoded packed output slots [nout][N] -> scores [nX][nY] (pair g = i nY + j at slot g mod N
+    of output g // N)."""
+    flat = np.asarray(slots).reshape(-1)
+    return flat[: nX * nY].reshape(nX, nY)

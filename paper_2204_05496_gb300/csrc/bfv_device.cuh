@@ -1,0 +1,289 @@
+// bfv_device.cuh -- device-side modular arithmetic and the shared-memory negacyclic NTT.
+//
+// Residues are 64-bit words modulo primes below 2^61. Constant operands (twiddles, keys,
+// encoded weights, P^-1) are multiplied with Shoup's method (a precomputed companion
+// w' = floor(w 2^64 / q) turns the reduction into one high and two low 64-bit products);
+// variable x variable products use Barrett reduction with mu = floor(2^(2b) / q).
+// Butterflies keep values lazily in [0, 4q) (Cooley-Tukey forward) or [0, 2q)
+// (Gentleman-Sande inverse), Harvey's bounds.
+//
+// NTT layout: forward transform of a (coefficient order) leaves at position p the value
+// a(psi^(2 brev(p) + 1)) (bit-reversed evaluation order); the inverse transform takes that
+// layout back to coefficients and folds in N^-1. Every evaluation-form array in the library
+// (keys, encoded weights, ciphertexts in flight) uses this layout.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+typedef unsigned long long u64;
+typedef unsigned int u32;
+
+#define BFV_MAXP 16      // ciphertext primes + special prime
+#define BFV_MAXMOD 17    // + the plaintext modulus t (index nqp)
+#define BFV_MAXW 16      // 64-bit words of Q (and of t*Q) for exact decryption
+
+// Per-modulus constants, resident in device memory (one entry per prime and one for t).
+struct ModTab {
+    u64 q, q2;              // q and 2q
+    u64 ninv, ninvp;        // N^-1 mod q and its Shoup companion
+    u64 ilast, ilastp;      // psi^-brev(1) * N^-1 (last inverse stage) and companion
+    u64 mu;                 // Barrett constant floor(2^(2 bits) / q)
+    int bits;               // bit length of q
+    int pad_;
+    u64 pinv, pinvp;        // P^-1 mod q and companion (ciphertext primes only)
+    u64 phalf;              // floor(P/2) mod q
+    u64 delta;              // floor(Q/t) mod q
+    u64 r64, r64p;          // 2^64 mod q and companion
+    const u64 *fw, *fwp;    // forward twiddles psi^brev(k), k < N, and companions
+    const u64 *iw, *iwp;    // inverse twiddles psi^-brev(k) and companions
+};
+
+// ------------------------------------------------------------------ modular arithmetic
+
+__device__ __forceinline__ u64 mul_shoup(u64 x, u64 w, u64 wp, u64 q) {
+    // x < 2^64, w < q, wp = floor(w 2^64 / q): result in [0, 2q)
+    const u64 h = __umul64hi(x, wp);
+    return x * w - h * q;
+}
+__device__ __forceinline__ u64 red2(u64 x, u64 q2) { return x >= q2 ? x - q2 : x; }
+__device__ __forceinline__ u64 red1(u64 x, u64 q) { return x >= q ? x - q : x; }
+__device__ __forceinline__ u64 add_mod(u64 a, u64 b, u64 q) { return red1(a + b, q); }
+__device__ __forceinline__ u64 sub_mod(u64 a, u64 b, u64 q) { return a >= b ? a - b : a + q - b; }
+
+// a * b mod q for a, b < q (Barrett, q < 2^61, mu = floor(2^(2 bits) / q)).
+__device__ __forceinline__ u64 mul_barrett(u64 a, u64 b, u64 q, u64 mu, int bits) {
+    const u64 lo = a * b, hi = __umul64hi(a, b);
+    // z >> (bits - 1), z = hi:lo < 2^(2 bits)
+    const int s = bits - 1;
+    const u64 z1 = (lo >> s) | (hi << (64 - s));
+    // q_est = floor(z1 * mu / 2^(bits + 1)); z1 < 2^(bits+1), mu < 2^(bits+1)
+    const u64 plo = z1 * mu, phi = __umul64hi(z1, mu);
+    const int s2 = bits + 1;
+    const u64 qe = (plo >> s2) | (phi << (64 - s2));
+    u64 r = lo - qe * q;
+    r = red1(r, q);
+    r = red1(r, q);
+    return red1(r, q);
+}
+
+// Shoup companion floor(w 2^64 / q) by long division (setup-time helper on the device).
+__device__ __forceinline__ u64 shoup_companion(u64 w, u64 q) {
+    u64 rem = w, quo = 0;
+#pragma unroll 1
+    for (int i = 0; i < 64; ++i) {
+        rem <<= 1;
+        quo <<= 1;
+        if (rem >= q) { rem -= q; quo |= 1; }
+    }
+    return quo;
+}
+
+// ------------------------------------------------------------------ butterflies
+
+__device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 q2) {
+    const u64 x = red2(X, q2);
+    const u64 t = mul_shoup(Y, w, wp, q);
+    X = x + t;
+    Y = x - t + q2;
+}
+__device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 q2) {
+    const u64 s = X + Y, d = X - Y + q2;
+    X = red2(s, q2);
+    Y = mul_shoup(d, w, wp, q);
+}
+__device__ __forceinline__ void gs_bfly_last(u64 &X, u64 &Y, u64 ni, u64 nip, u64 w, u64 wp, u64 q, u64 q2) {
+    const u64 s = X + Y, d = X - Y + q2;
+    X = mul_shoup(s, ni, nip, q);
+    Y = mul_shoup(d, w, wp, q);
+}
+
+// Shared-memory index with one pad word every 16 words (conflict-free strided groups).
+__device__ __forceinline__ int padi(int p) { return p + (p >> 4); }
+template <int M> struct PadSize { static constexpr int value = M + (M >> 4); };
+
+// ------------------------------------------------------------------ radix-2^R register kernels
+
+// Forward Cooley-Tukey stages s .. s+R-1 (global stage numbers) on a group of 2^R values
+// x[r] = a[base + r * t_last]; gblock is the global block index at stage s.
+template <int R>
+__device__ __forceinline__ void fwd_radix(u64 (&x)[1 << R], int s, int gblock, const u64 *__restrict__ fw,
+                                          const u64 *__restrict__ fwp, u64 q, u64 q2) {
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+        const int half = 1 << (R - 1 - u);
+#pragma unroll
+        for (int k = 0; k < (1 << u); ++k) {
+            const int ti = (1 << (s + u)) + (gblock << u) + k;
+            const u64 w = __ldg(fw + ti), wp = __ldg(fwp + ti);
+#pragma unroll
+            for (int j = 0; j < half; ++j) ct_bfly(x[k * 2 * half + j], x[k * 2 * half + j + half], w, wp, q, q2);
+        }
+    }
+}
+
+// Inverse Gentleman-Sande stages s0 .. s0+R-1 (stride 2^(s0+u)) on a full-size array;
+// block is the block index of size 2^(s0+R). When LASTSTAGE, the final stage of the whole
+// transform is stage s0+R-1 and N^-1 is folded into it. (Indexing by r keeps x[] in
+// registers; the repeated twiddle loads of one stage hit the same address.)
+template <int R, bool LASTSTAGE>
+__device__ __forceinline__ void inv_radix(u64 (&x)[1 << R], int s0, int block, int N, const u64 *__restrict__ iw,
+                                          const u64 *__restrict__ iwp, u64 ni, u64 nip, u64 il, u64 ilp, u64 q,
+                                          u64 q2) {
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+#pragma unroll
+        for (int r = 0; r < (1 << R); ++r) {
+            if (r & (1 << u)) continue;
+            if (LASTSTAGE && u == R - 1) {
+                gs_bfly_last(x[r], x[r + (1 << u)], ni, nip, il, ilp, q, q2);
+            } else {
+                const int ti = (N >> (s0 + u + 1)) + (block << (R - 1 - u)) + (r >> (u + 1));
+                gs_bfly(x[r], x[r + (1 << u)], __ldg(iw + ti), __ldg(iwp + ti), q, q2);
+            }
+        }
+    }
+}
+
+// Pass schedule: LOGM stages in ceil(LOGM/4) passes of radix 2^3 or 2^4, larger first.
+template <int LOGM> struct Sched {
+    static constexpr int NP = (LOGM + 3) / 4;
+    template <int P> struct R { static constexpr int value = LOGM / NP + (P < LOGM % NP ? 1 : 0); };
+};
+
+// ------------------------------------------------------------------ forward NTT driver
+//
+// Transforms a sub-array of M = 2^LOGM points: sub-array `hidx` of the full size-N
+// transform after its first C stages (C = log2 N - LOGM). load(p) returns the input at local
+// position p (for C > 0: the value after stage C-1, produced by the caller); store(p, v)
+// receives the final value in [0, q). sm: shared buffer of PadSize<M> words. Values given by
+// load must be < 4q. The driver ends without a barrier after the last store.
+
+template <int LOGM, int NT, int P, int S, class Load, class Store>
+__device__ __forceinline__ void fwd_passes(u64 *sm, const ModTab &T, int C, int hidx, Load &load, Store &store) {
+    constexpr int NP = Sched<LOGM>::NP;
+    constexpr int R = Sched<LOGM>::template R<P>::value;
+    constexpr int M = 1 << LOGM;
+    constexpr int TL = M >> (S + R);
+    constexpr int G = M >> R;
+    const u64 q = T.q, q2 = T.q2;
+#pragma unroll 1
+    for (int g = threadIdx.x; g < G; g += NT) {
+        const int block = g / TL, off = g % TL;
+        const int base = block * (TL << R) + off;
+        u64 x[1 << R];
+#pragma unroll
+        for (int r = 0; r < (1 << R); ++r) {
+            if constexpr (P == 0) x[r] = load(base + r * TL);
+            else x[r] = sm[padi(base + r * TL)];
+        }
+        fwd_radix<R>(x, S + C, (hidx << S) + block, T.fw, T.fwp, q, q2);
+#pragma unroll
+        for (int r = 0; r < (1 << R); ++r) {
+            if constexpr (P == NP - 1) store(base + r * TL, red1(red2(x[r], q2), q));
+            else sm[padi(base + r * TL)] = x[r];
+        }
+    }
+    if constexpr (P < NP - 1) {
+        __syncthreads();
+        fwd_passes<LOGM, NT, P + 1, S + R>(sm, T, C, hidx, load, store);
+    }
+}
+
+template <int LOGM, int NT, class Load, class Store>
+__device__ __forceinline__ void ntt_forward(u64 *sm, const ModTab &T, int C, int hidx, Load load, Store store) {
+    fwd_passes<LOGM, NT, 0, 0>(sm, T, C, hidx, load, store);
+}
+
+// ------------------------------------------------------------------ inverse NTT driver (full size)
+// load(p) must return values < 2q in the bit-reversed evaluation layout; store(p, v) gets
+// coefficient p in [0, q).
+
+template <int LOGN, int NT, int P, int S, class Load, class Store>
+__device__ __forceinline__ void inv_passes(u64 *sm, const ModTab &T, Load &load, Store &store) {
+    constexpr int NP = Sched<LOGN>::NP;
+    constexpr int R = Sched<LOGN>::template R<P>::value;
+    constexpr int N = 1 << LOGN;
+    constexpr int TL = 1 << S;
+    constexpr int G = N >> R;
+    const u64 q = T.q, q2 = T.q2;
+#pragma unroll 1
+    for (int g = threadIdx.x; g < G; g += NT) {
+        const int block = g >> S, off = g & (TL - 1);
+        const int base = block * (TL << R) + off;
+        u64 x[1 << R];
+#pragma unroll
+        for (int r = 0; r < (1 << R); ++r) {
+            if constexpr (P == 0) x[r] = load(base + r * TL);
+            else x[r] = sm[padi(base + r * TL)];
+        }
+        inv_radix<R, P == NP - 1>(x, S, block, N, T.iw, T.iwp, T.ninv, T.ninvp, T.ilast, T.ilastp, q, q2);
+#pragma unroll
+        for (int r = 0; r < (1 << R); ++r) {
+            if constexpr (P == NP - 1) store(base + r * TL, red1(x[r], q));
+            else sm[padi(base + r * TL)] = x[r];
+        }
+    }
+    if constexpr (P < NP - 1) {
+        __syncthreads();
+        inv_passes<LOGN, NT, P + 1, S + R>(sm, T, load, store);
+    }
+}
+
+template <int LOGN, int NT, class Load, class Store>
+__device__ __forceinline__ void ntt_inverse(u64 *sm, const ModTab &T, Load load, Store store) {
+    inv_passes<LOGN, NT, 0, 0>(sm, T, load, store);
+}
+
+// ------------------------------------------------------------------ index maps
+
+// Bit reversal of p over logn bits.
+__device__ __forceinline__ int brev_n(int p, int logn) { return (int)(__brev((u32)p) >> (32 - logn)); }
+
+// Evaluation-layout automorphism X -> X^g: sigma_g(a) at position p is a at position
+// brev(((2 brev(p) + 1) g mod 2N - 1) / 2).
+__device__ __forceinline__ int auto_src(int p, u32 g, int logn) {
+    const u32 e = 2u * (u32)brev_n(p, logn) + 1u;
+    const u32 e2 = (e * g) & ((2u << logn) - 1u);
+    return brev_n((int)((e2 - 1u) >> 1), logn);
+}
+
+// ------------------------------------------------------------------ ChaCha20 (RFC 8439)
+
+__device__ __forceinline__ u32 rotl(u32 x, int n) { return __funnelshift_l(x, x, n); }
+#define BFV_QR(a, b, c, d)                                  \
+    a += b; d ^= a; d = rotl(d, 16); c += d; b ^= c; b = rotl(b, 12); \
+    a += b; d ^= a; d = rotl(d, 8);  c += d; b ^= c; b = rotl(b, 7);
+
+// Block `counter` of the stream keyed by the 64-bit seed (zero-extended to 256 bits) with
+// nonce (n0, n1, n2); writes the 16 output words.
+__device__ __forceinline__ void chacha20_block(u64 seed, u32 counter, u32 n0, u32 n1, u32 n2, u32 (&o)[16]) {
+    const u32 s0 = 0x61707865u, s1 = 0x3320646eu, s2 = 0x79622d32u, s3 = 0x6b206574u;
+    const u32 k0 = (u32)seed, k1 = (u32)(seed >> 32);
+    u32 x0 = s0, x1 = s1, x2 = s2, x3 = s3, x4 = k0, x5 = k1, x6 = 0, x7 = 0, x8 = 0, x9 = 0, x10 = 0, x11 = 0,
+        x12 = counter, x13 = n0, x14 = n1, x15 = n2;
+#pragma unroll 1
+    for (int r = 0; r < 10; ++r) {
+        BFV_QR(x0, x4, x8, x12) BFV_QR(x1, x5, x9, x13) BFV_QR(x2, x6, x10, x14) BFV_QR(x3, x7, x11, x15)
+        BFV_QR(x0, x5, x10, x15) BFV_QR(x1, x6, x11, x12) BFV_QR(x2, x7, x8, x13) BFV_QR(x3, x4, x9, x14)
+    }
+    o[0] = x0 + s0; o[1] = x1 + s1; o[2] = x2 + s2; o[3] = x3 + s3;
+    o[4] = x4 + k0; o[5] = x5 + k1; o[6] = x6; o[7] = x7;
+    o[8] = x8; o[9] = x9; o[10] = x10; o[11] = x11;
+    o[12] = x12 + counter; o[13] = x13 + n0; o[14] = x14 + n1; o[15] = x15 + n2;
+}
+#undef BFV_QR
+
+// Ternary value {-1, 0, 1} from one word: floor(3 w / 2^32) - 1.
+__device__ __forceinline__ int ternary_of(u32 w) { return (int)(((u64)w * 3ull) >> 32) - 1; }
+
+// Discrete Gaussian from a 64-bit draw and a sign word: magnitude = number of thresholds
+// not above the draw; negative when the sign bit is set and the magnitude is non-zero.
+__device__ __forceinline__ int gauss_of(u32 lo, u32 hi, u32 sgn, const u64 *cdt, int n) {
+    const u64 r = (u64)lo | ((u64)hi << 32);
+    int mag = 0;
+    for (int k = 0; k < n; ++k) mag += (r >= cdt[k]) ? 1 : 0;
+    return (mag != 0 && (sgn & 1u)) ? -mag : mag;
+}
+
+// Small signed integer lifted into [0, q).
+__device__ __forceinline__ u64 lift_small(int v, u64 q) { return v >= 0 ? (u64)v : q - (u64)(-v); }

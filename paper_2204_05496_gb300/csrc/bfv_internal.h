@@ -1,0 +1,100 @@
+// bfv_internal.h -- host-side structures shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <vector>
+#include <atomic>
+#include <cuda_runtime.h>
+
+#include "bfv_device.cuh"
+#include "../../include/bfv_lr.h"
+
+// Constants for exact decryption (mixed-radix CRT plus multi-word division), device copy.
+struct DecConst {
+    int L, W;                        // primes, 64-bit words of t*Q + Q/2
+    int tbits;                       // bit length of t
+    int pad_;
+    u64 t;
+    u64 inv[BFV_MAXP][BFV_MAXP];     // q_i^-1 mod q_j (i < j)
+    u64 invp[BFV_MAXP][BFV_MAXP];    // Shoup companions
+    u64 qhalf[BFV_MAXW];             // floor(Q/2)
+    u64 qshift[32][BFV_MAXW];        // Q << b for b < tbits
+};
+
+struct bfv_ctx {
+    int device = 0;
+    int N = 0, logN = 0, L = 0, nqp = 0, bits = 0;
+    u64 t = 0, omega = 0;
+    uint32_t sigma_num = 16, sigma_den = 5;
+    std::vector<u64> primes;         // L+1 (index L = P)
+    std::vector<ModTab> hmods;       // host copy, nqp + 1 entries (index nqp = t)
+    ModTab *dmods = nullptr;         // device copy
+    u64 *dtw = nullptr;              // twiddle tables [nqp+1][4][N]
+    u32 *dslot = nullptr;            // [N] evaluation position of slot l (mod-t transform)
+    u32 *dmaskpow = nullptr;         // [2N] N^-1 omega^i mod t
+    u64 *dcdt = nullptr;             // Gaussian thresholds
+    int cdt_len = 0;
+    DecConst *ddec = nullptr;        // decryption constants
+    std::vector<u64> galois;         // rotate-and-sum Galois elements, in order
+    std::vector<u64> delta_host;     // floor(Q/t) mod q_l
+    std::atomic<uint64_t> launches{0};
+};
+
+struct bfv_keys {
+    const bfv_ctx *ctx = nullptr;
+    int8_t *sk = nullptr;            // [N] ternary
+    u64 *sk_eval = nullptr;          // [nqp][2][N]: value, companion (evaluation layout)
+    u64 *pk_eval = nullptr;          // [2][L][2][N]: value, companion
+    u64 *gk_eval = nullptr;          // [ng][L digits][2 comps][nqp][2][N]: value, companion
+    int ng = 0;
+};
+
+struct bfv_model {
+    const bfv_ctx *ctx = nullptr;
+    size_t f = 0, nY = 0, K = 0;
+    u64 *w_eval = nullptr;           // [nY][K][L][2][N]: value, companion (packed product)
+    int64_t *w_int = nullptr;        // [f][nY] integer weights (standard product)
+    u64 *bias_delta = nullptr;       // [nY][L]: Delta [b_j]_t mod q_l
+    int64_t wmax = 0;                // max |w| (bounds the standard product's accumulators)
+};
+
+// Launch-count bookkeeping.
+inline void count_launch(const bfv_ctx *c, uint64_t n = 1) {
+    const_cast<bfv_ctx *>(c)->launches.fetch_add(n, std::memory_order_relaxed);
+}
+
+#define BFV_CUDA_TRY(expr)                              \
+    do {                                                \
+        cudaError_t e_ = (expr);                        \
+        if (e_ != cudaSuccess) return BFV_ERR_CUDA;     \
+    } while (0)
+
+// ------------------------------------------------------------------ launchers (k_*.cu)
+// Each returns BFV_OK or BFV_ERR_CUDA (launch error); all are asynchronous on `st`.
+
+int launch_ntt_limbs(const bfv_ctx *c, const u64 *in, u64 *out, size_t nct, bool forward, cudaStream_t st);
+int launch_encode(const bfv_ctx *c, const int64_t *slots, size_t count, u64 *pt, cudaStream_t st);
+int launch_decode(const bfv_ctx *c, const u64 *pt, size_t count, int64_t *slots, cudaStream_t st);
+int launch_encode_features(const bfv_ctx *c, const uint8_t *X, size_t nX, size_t f, u64 *pt, cudaStream_t st);
+int launch_encode_columns(const bfv_ctx *c, const uint8_t *X, size_t nX, size_t f, u64 *pt, cudaStream_t st);
+int launch_keygen(const bfv_ctx *c, bfv_keys *k, u64 seed, cudaStream_t st);
+int launch_keys_export(const bfv_ctx *c, const bfv_keys *k, int8_t *sk, u64 *pk, u64 *gk, cudaStream_t st);
+int launch_encrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *pt, size_t count, u64 seed, uint32_t obj0,
+                   u64 *ct, void *ws, cudaStream_t st);
+int launch_decrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *ct, size_t count, u64 *pt, void *ws,
+                   cudaStream_t st);
+int launch_model_weights(const bfv_ctx *c, bfv_model *m, const u64 *w_pt, cudaStream_t st);
+
+struct PackedPlan {
+    size_t nX, nY, K, npairs, nout, chunk;
+    size_t off_xntt, off_yacc, off_state, off_digits, off_u, off_r, total;
+};
+PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t chunk);
+int launch_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const u64 *X_ct, size_t nX,
+                  u64 *Y_ct, void *ws, const PackedPlan &plan, cudaStream_t st);
+int launch_pair_export(const bfv_ctx *c, const PackedPlan &plan, const void *ws, size_t slot_in_chunk, u64 *ct_out,
+                       cudaStream_t st);
+int launch_standard(const bfv_ctx *c, const bfv_model *m, const u64 *X_ct, u64 *Y_ct, cudaStream_t st);
+
+// Threads per CTA for a transform of 2^logm points.
+constexpr int nt_for(int logm) { return logm >= 14 ? 512 : (logm == 13 ? 512 : (logm == 12 ? 256 : 128)); }

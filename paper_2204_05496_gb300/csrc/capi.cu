@@ -1,0 +1,593 @@
+// capi.cu -- C ABI entry points and host-side precomputation (primes, NTT tables,
+// CRT/rounding constants, Gaussian thresholds). Kernels live in k_*.cu.
+#include <algorithm>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "bfv_internal.h"
+
+typedef unsigned __int128 u128;
+
+namespace {
+
+// ------------------------------------------------------------------ number theory (host)
+
+u64 mulmod_h(u64 a, u64 b, u64 q) { return (u64)((u128)a * b % q); }
+u64 powmod_h(u64 a, u64 e, u64 q) {
+    u64 r = 1 % q;
+    a %= q;
+    while (e) {
+        if (e & 1) r = mulmod_h(r, a, q);
+        a = mulmod_h(a, a, q);
+        e >>= 1;
+    }
+    return r;
+}
+u64 inv_h(u64 a, u64 q) { return powmod_h(a, q - 2, q); }  // q prime
+
+// Deterministic Miller-Rabin for 64-bit n (bases 2..37 are exact below 3.3e24).
+bool is_prime_h(u64 n) {
+    static const u64 bases[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+    if (n < 2) return false;
+    for (u64 b : bases)
+        if (n % b == 0) return n == b;
+    u64 d = n - 1;
+    int s = 0;
+    while ((d & 1) == 0) { d >>= 1; ++s; }
+    for (u64 a : bases) {
+        u64 x = powmod_h(a, d, n);
+        if (x == 1 || x == n - 1) continue;
+        bool comp = true;
+        for (int i = 1; i < s; ++i) {
+            x = mulmod_h(x, x, n);
+            if (x == n - 1) { comp = false; break; }
+        }
+        if (comp) return false;
+    }
+    return true;
+}
+
+int ilog2_h(u64 n) { int l = 0; while ((1ull << l) < n) ++l; return l; }
+u64 brev_h(u64 x, int bits) {
+    u64 r = 0;
+    for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1ull) << (bits - 1 - i);
+    return r;
+}
+u64 shoup_h(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+
+// Primes below 2^bits that are 1 mod 2N, descending.
+bool ntt_primes_h(int bits, u64 N, int count, std::vector<u64> &out) {
+    out.clear();
+    const u64 m = 2 * N;
+    u64 q = (1ull << bits) - m + 1;
+    while ((int)out.size() < count) {
+        if (q < (1ull << (bits - 1))) return false;
+        if (is_prime_h(q)) out.push_back(q);
+        q -= m;
+    }
+    return true;
+}
+
+// A primitive 2N-th root of unity mod q: x^((q-1)/2N) for the first x >= 2 whose N-th power is -1.
+u64 root_2n_h(u64 q, u64 N) {
+    for (u64 x = 2;; ++x) {
+        u64 r = powmod_h(x, (q - 1) / (2 * N), q);
+        if (powmod_h(r, N, q) == q - 1) return r;
+    }
+}
+
+// Smallest primitive root modulo the prime p.
+u64 smallest_primitive_root_h(u64 p) {
+    std::vector<u64> fs;
+    u64 n = p - 1;
+    for (u64 d = 2; d * d <= n; ++d)
+        if (n % d == 0) { fs.push_back(d); while (n % d == 0) n /= d; }
+    if (n > 1) fs.push_back(n);
+    for (u64 g = 2;; ++g) {
+        bool ok = true;
+        for (u64 f : fs)
+            if (powmod_h(g, (p - 1) / f, p) == 1) { ok = false; break; }
+        if (ok) return g;
+    }
+}
+
+// ------------------------------------------------------------------ multi-word integers (little-endian)
+
+typedef std::vector<u64> MW;
+void mw_mul_small(MW &a, u64 m) {
+    u64 carry = 0;
+    for (auto &w : a) {
+        u128 v = (u128)w * m + carry;
+        w = (u64)v;
+        carry = (u64)(v >> 64);
+    }
+    if (carry) a.push_back(carry);
+}
+u64 mw_divmod_small(MW &a, u64 d) {  // a <- floor(a / d), returns remainder
+    u128 rem = 0;
+    for (int i = (int)a.size() - 1; i >= 0; --i) {
+        u128 cur = (rem << 64) | a[i];
+        a[i] = (u64)(cur / d);
+        rem = cur % d;
+    }
+    while (a.size() > 1 && a.back() == 0) a.pop_back();
+    return (u64)rem;
+}
+u64 mw_mod_small(const MW &a, u64 d) {
+    u128 rem = 0;
+    for (int i = (int)a.size() - 1; i >= 0; --i) rem = ((rem << 64) | a[i]) % d;
+    return (u64)rem;
+}
+
+// ------------------------------------------------------------------ Gaussian thresholds
+// exp(-k^2 / (2 sigma^2)), sigma = num/den, in 120-bit binary fixed point with exact integer
+// arithmetic: base = exp(-1 / (2 num^2)) by its Taylor series, raised to (k den)^2 by squaring.
+
+const int FB = 120;
+u128 fx_mul(u128 a, u128 b) {  // (a * b) >> FB, a, b < 2^124
+    u64 a0 = (u64)a, a1 = (u64)(a >> 64), b0 = (u64)b, b1 = (u64)(b >> 64);
+    u128 p00 = (u128)a0 * b0, p01 = (u128)a0 * b1, p10 = (u128)a1 * b0, p11 = (u128)a1 * b1;
+    // 256-bit sum: p11 << 128 + (p01 + p10) << 64 + p00
+    u128 mid = p01 + p10;  // < 2^125, no overflow for our operand sizes
+    u128 lo = p00 + (mid << 64);
+    u128 carry = (lo < p00) ? 1 : 0;
+    u128 hi = p11 + (mid >> 64) + carry;
+    // shift right by FB = 120: result = hi << 8 | lo >> 120
+    return (hi << (128 - FB)) | (lo >> FB);
+}
+u128 fx_pow(u128 b, u64 e) {
+    u128 r = (u128)1 << FB;
+    while (e) {
+        if (e & 1) r = fx_mul(r, b);
+        b = fx_mul(b, b);
+        e >>= 1;
+    }
+    return r;
+}
+int gaussian_table_h(uint32_t num, uint32_t den, u64 *out) {
+    if (num == 0 || den == 0) return -1;
+    const int tail = (int)(6ull * num / den);
+    if (tail < 1 || tail > 32) return -1;
+    // base = exp(-x), x = 1 / (2 num^2): alternating series, positive and negative parts apart
+    const u64 d = 2ull * num * num;
+    u128 term = (u128)1 << FB, pos = term, neg = 0;
+    for (int n = 1; n < 40 && term; ++n) {
+        term = term / d / (u64)n;
+        if (n & 1) neg += term; else pos += term;
+    }
+    const u128 base = pos - neg;
+    std::vector<u128> rho(tail + 1);
+    for (int k = 0; k <= tail; ++k) rho[k] = fx_pow(base, (u64)k * k * den * den);
+    u128 Z = rho[0];
+    for (int k = 1; k <= tail; ++k) Z += 2 * rho[k];
+    u128 cum = 0;
+    for (int k = 0; k < tail; ++k) {
+        cum += (k == 0) ? rho[0] : 2 * rho[k];
+        // floor(2^64 cum / Z) by binary long division
+        u128 rem = cum;
+        u64 q = 0;
+        for (int i = 0; i < 64; ++i) {
+            rem <<= 1;
+            q <<= 1;
+            if (rem >= Z) { rem -= Z; q |= 1; }
+        }
+        out[k] = q;
+    }
+    return tail;
+}
+
+bool params_ok(const bfv_params *p) {
+    if (!p) return false;
+    if (p->N != 4096 && p->N != 8192 && p->N != 16384) return false;
+    if (p->L < 1 || p->L > BFV_MAXP - 1) return false;
+    if (p->prime_bits < 30 || p->prime_bits > 60) return false;
+    if (p->t < 3 || p->t >= (1ull << 31) || (p->t - 1) % (2ull * p->N) != 0 || !is_prime_h(p->t)) return false;
+    if (p->sigma_num == 0 || p->sigma_den == 0) return false;
+    return true;
+}
+
+template <class T> int dalloc(T **p, size_t n) {
+    if (cudaMalloc((void **)p, sizeof(T) * (n ? n : 1)) != cudaSuccess) { *p = nullptr; return BFV_ERR_OOM; }
+    return BFV_OK;
+}
+
+void free_ctx(bfv_ctx *c) {
+    if (!c) return;
+    cudaFree(c->dmods);
+    cudaFree(c->dtw);
+    cudaFree(c->dslot);
+    cudaFree(c->dmaskpow);
+    cudaFree(c->dcdt);
+    cudaFree(c->ddec);
+    delete c;
+}
+
+cudaStream_t S(uintptr_t s) { return (cudaStream_t)s; }
+
+}  // namespace
+
+// ====================================================================== C ABI
+
+extern "C" {
+
+int bfv_abi_version(void) { return 1; }
+
+int bfv_params_primes(const bfv_params *p, uint64_t *primes_out) {
+    if (!params_ok(p) || !primes_out) return BFV_ERR_INVALID_ARG;
+    std::vector<u64> ps;
+    if (!ntt_primes_h((int)p->prime_bits, p->N, (int)p->L + 1, ps)) return BFV_ERR_BAD_PARAMS;
+    std::copy(ps.begin(), ps.end(), primes_out);
+    return BFV_OK;
+}
+
+int bfv_gaussian_table(uint32_t sigma_num, uint32_t sigma_den, uint64_t *out, int *len) {
+    if (!out || !len) return BFV_ERR_INVALID_ARG;
+    int n = gaussian_table_h(sigma_num, sigma_den, (u64 *)out);
+    if (n < 0) return BFV_ERR_BAD_PARAMS;
+    *len = n;
+    return BFV_OK;
+}
+
+int bfv_setup(const bfv_params *p, bfv_ctx **out) {
+    if (!out) return BFV_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (!params_ok(p)) return BFV_ERR_BAD_PARAMS;
+    bfv_ctx *c = new (std::nothrow) bfv_ctx();
+    if (!c) return BFV_ERR_OOM;
+    if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return BFV_ERR_CUDA; }
+    c->N = (int)p->N;
+    c->logN = ilog2_h(p->N);
+    c->L = (int)p->L;
+    c->nqp = c->L + 1;
+    c->bits = (int)p->prime_bits;
+    c->t = p->t;
+    c->sigma_num = p->sigma_num;
+    c->sigma_den = p->sigma_den;
+    if (!ntt_primes_h(c->bits, p->N, c->nqp, c->primes)) { delete c; return BFV_ERR_BAD_PARAMS; }
+    const u64 N = (u64)c->N;
+    const int nmod = c->nqp + 1;
+    const u64 P = c->primes[c->L];
+
+    // Q, floor(Q/t), floor(Q/2) as multi-word integers
+    MW Q{1};
+    for (int l = 0; l < c->L; ++l) mw_mul_small(Q, c->primes[l]);
+    MW Qdt = Q;
+    mw_divmod_small(Qdt, c->t);
+
+    // twiddles and per-modulus constants
+    std::vector<u64> tw((size_t)nmod * 4 * N);
+    c->hmods.assign(nmod, ModTab{});
+    c->delta_host.assign(c->L, 0);
+    int rc = dalloc(&c->dtw, tw.size());
+    if (rc) { free_ctx(c); return rc; }
+    for (int j = 0; j < nmod; ++j) {
+        const u64 q = (j < c->nqp) ? c->primes[j] : c->t;
+        u64 psi;
+        if (j < c->nqp) {
+            psi = root_2n_h(q, N);
+        } else {
+            psi = powmod_h(smallest_primitive_root_h(q), (q - 1) / (2 * N), q);
+            c->omega = psi;
+        }
+        const u64 psii = inv_h(psi, q);
+        u64 *fw = &tw[((size_t)j * 4 + 0) * N], *fwp = &tw[((size_t)j * 4 + 1) * N];
+        u64 *iw = &tw[((size_t)j * 4 + 2) * N], *iwp = &tw[((size_t)j * 4 + 3) * N];
+        std::vector<u64> pw(N), ipw(N);
+        pw[0] = ipw[0] = 1;
+        for (u64 i = 1; i < N; ++i) { pw[i] = mulmod_h(pw[i - 1], psi, q); ipw[i] = mulmod_h(ipw[i - 1], psii, q); }
+        for (u64 k = 0; k < N; ++k) {
+            const u64 b = brev_h(k, c->logN);
+            fw[k] = pw[b]; fwp[k] = shoup_h(fw[k], q);
+            iw[k] = ipw[b]; iwp[k] = shoup_h(iw[k], q);
+        }
+        ModTab &T = c->hmods[j];
+        T.q = q;
+        T.q2 = 2 * q;
+        T.ninv = inv_h(N % q, q);
+        T.ninvp = shoup_h(T.ninv, q);
+        T.ilast = mulmod_h(iw[1], T.ninv, q);
+        T.ilastp = shoup_h(T.ilast, q);
+        T.bits = ilog2_h(q + 1);
+        T.mu = (u64)(((u128)1 << (2 * T.bits)) / q);
+        if (j < c->L) {
+            T.pinv = inv_h(P % q, q);
+            T.pinvp = shoup_h(T.pinv, q);
+            T.phalf = (P / 2) % q;
+            T.delta = mw_mod_small(Qdt, q);
+            c->delta_host[j] = T.delta;
+        } else if (j == c->L) {
+            T.phalf = P / 2;
+        }
+        T.r64 = (u64)(((u128)1 << 64) % q);
+        T.r64p = shoup_h(T.r64, q);
+        const u64 *base = c->dtw + (size_t)j * 4 * N;
+        T.fw = base; T.fwp = base + N; T.iw = base + 2 * N; T.iwp = base + 3 * N;
+    }
+    if (cudaMemcpy(c->dtw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) { free_ctx(c); return BFV_ERR_CUDA; }
+    if ((rc = dalloc(&c->dmods, nmod))) { free_ctx(c); return rc; }
+    if (cudaMemcpy(c->dmods, c->hmods.data(), sizeof(ModTab) * nmod, cudaMemcpyHostToDevice) != cudaSuccess) { free_ctx(c); return BFV_ERR_CUDA; }
+
+    // slot map: slot l at exponent e_l (3^c or 2N - 3^c), evaluation position brev((e_l - 1)/2)
+    std::vector<u32> slot(N);
+    {
+        u64 g = 1;
+        for (u64 cc = 0; cc < N / 2; ++cc) {
+            slot[cc] = (u32)brev_h((g - 1) / 2, c->logN);
+            slot[cc + N / 2] = (u32)brev_h((2 * N - g - 1) / 2, c->logN);
+            g = g * 3 % (2 * N);
+        }
+    }
+    if ((rc = dalloc(&c->dslot, N))) { free_ctx(c); return rc; }
+    cudaMemcpy(c->dslot, slot.data(), N * 4, cudaMemcpyHostToDevice);
+    // N^-1 omega^i mod t, i < 2N (one-hot mask coefficients)
+    std::vector<u32> mp(2 * N);
+    {
+        const u64 ninvt = inv_h(N % c->t, c->t);
+        u64 w = ninvt;
+        for (u64 i = 0; i < 2 * N; ++i) { mp[i] = (u32)w; w = mulmod_h(w, c->omega, c->t); }
+    }
+    if ((rc = dalloc(&c->dmaskpow, 2 * N))) { free_ctx(c); return rc; }
+    cudaMemcpy(c->dmaskpow, mp.data(), 2 * N * 4, cudaMemcpyHostToDevice);
+
+    // Gaussian thresholds
+    u64 cdt[32];
+    c->cdt_len = gaussian_table_h(c->sigma_num, c->sigma_den, cdt);
+    if (c->cdt_len < 0) { free_ctx(c); return BFV_ERR_BAD_PARAMS; }
+    if ((rc = dalloc(&c->dcdt, 32))) { free_ctx(c); return rc; }
+    cudaMemcpy(c->dcdt, cdt, 32 * 8, cudaMemcpyHostToDevice);
+
+    // decryption constants
+    DecConst dc;
+    std::memset(&dc, 0, sizeof dc);
+    dc.L = c->L;
+    dc.t = c->t;
+    dc.tbits = ilog2_h(c->t + 1);
+    for (int i = 0; i < c->L; ++i)
+        for (int j = i + 1; j < c->L; ++j) {
+            dc.inv[i][j] = inv_h(c->primes[i] % c->primes[j], c->primes[j]);
+            dc.invp[i][j] = shoup_h(dc.inv[i][j], c->primes[j]);
+        }
+    MW tq = Q;
+    mw_mul_small(tq, c->t);
+    dc.W = (int)tq.size() + 1;
+    if (dc.W > BFV_MAXW) { free_ctx(c); return BFV_ERR_BAD_PARAMS; }
+    MW qh = Q;
+    mw_divmod_small(qh, 2);
+    for (size_t i = 0; i < qh.size(); ++i) dc.qhalf[i] = qh[i];
+    for (int b = 0; b < dc.tbits; ++b) {
+        MW s = Q;
+        mw_mul_small(s, 1ull << b);
+        for (size_t i = 0; i < s.size() && (int)i < BFV_MAXW; ++i) dc.qshift[b][i] = s[i];
+    }
+    if ((rc = dalloc(&c->ddec, 1))) { free_ctx(c); return rc; }
+    cudaMemcpy(c->ddec, &dc, sizeof dc, cudaMemcpyHostToDevice);
+
+    // rotate-and-sum Galois elements: 2N-1, then 3^(N/4), ..., 3^1 mod 2N
+    c->galois.push_back(2 * N - 1);
+    for (u64 s = N / 4; s >= 1; s >>= 1) c->galois.push_back(powmod_h(3, s, 2 * N));
+
+    if (cudaDeviceSynchronize() != cudaSuccess) { free_ctx(c); return BFV_ERR_CUDA; }
+    *out = c;
+    return BFV_OK;
+}
+
+int bfv_ctx_free(bfv_ctx *ctx) {
+    if (!ctx) return BFV_ERR_INVALID_ARG;
+    free_ctx(ctx);
+    return BFV_OK;
+}
+
+int bfv_ctx_query(const bfv_ctx *ctx, uint64_t *primes, uint64_t *omega, uint64_t *delta_mod_q) {
+    if (!ctx) return BFV_ERR_INVALID_ARG;
+    if (primes) std::copy(ctx->primes.begin(), ctx->primes.end(), primes);
+    if (omega) *omega = ctx->omega;
+    if (delta_mod_q) std::copy(ctx->delta_host.begin(), ctx->delta_host.end(), delta_mod_q);
+    return BFV_OK;
+}
+
+int bfv_keygen(bfv_ctx *ctx, uint64_t seed, uintptr_t stream, bfv_keys **out) {
+    if (!ctx || !out) return BFV_ERR_INVALID_ARG;
+    *out = nullptr;
+    bfv_keys *k = new (std::nothrow) bfv_keys();
+    if (!k) return BFV_ERR_OOM;
+    k->ctx = ctx;
+    k->ng = (int)ctx->galois.size();
+    const size_t N = ctx->N, L = ctx->L, nqp = ctx->nqp;
+    int rc = BFV_OK;
+    if ((rc = dalloc(&k->sk, N)) || (rc = dalloc(&k->sk_eval, nqp * 2 * N)) || (rc = dalloc(&k->pk_eval, 2 * L * 2 * N)) ||
+        (rc = dalloc(&k->gk_eval, (size_t)k->ng * L * 2 * nqp * 2 * N))) {
+        bfv_keys_free(k);
+        return rc;
+    }
+    rc = launch_keygen(ctx, k, seed, S(stream));
+    if (rc == BFV_OK && cudaStreamSynchronize(S(stream)) != cudaSuccess) rc = BFV_ERR_CUDA;
+    if (rc) { bfv_keys_free(k); return rc; }
+    *out = k;
+    return BFV_OK;
+}
+
+int bfv_keys_free(bfv_keys *k) {
+    if (!k) return BFV_ERR_INVALID_ARG;
+    cudaFree(k->sk);
+    cudaFree(k->sk_eval);
+    cudaFree(k->pk_eval);
+    cudaFree(k->gk_eval);
+    delete k;
+    return BFV_OK;
+}
+
+int bfv_keys_export(const bfv_ctx *ctx, const bfv_keys *keys, int8_t *sk, uint64_t *pk, uint64_t *gk, uintptr_t stream) {
+    if (!ctx || !keys || keys->ctx != ctx) return BFV_ERR_INVALID_ARG;
+    int rc = launch_keys_export(ctx, keys, sk, (u64 *)pk, (u64 *)gk, S(stream));
+    if (rc) return rc;
+    return cudaStreamSynchronize(S(stream)) == cudaSuccess ? BFV_OK : BFV_ERR_CUDA;
+}
+
+int bfv_encode(bfv_ctx *ctx, const int64_t *slots, size_t count, uint64_t *pt, uintptr_t stream) {
+    if (!ctx || (count && (!slots || !pt))) return BFV_ERR_INVALID_ARG;
+    if (!count) return BFV_OK;
+    return launch_encode(ctx, slots, count, (u64 *)pt, S(stream));
+}
+
+int bfv_decode(bfv_ctx *ctx, const uint64_t *pt, size_t count, int64_t *slots, uintptr_t stream) {
+    if (!ctx || (count && (!slots || !pt))) return BFV_ERR_INVALID_ARG;
+    if (!count) return BFV_OK;
+    return launch_decode(ctx, (const u64 *)pt, count, slots, S(stream));
+}
+
+int bfv_encode_features(bfv_ctx *ctx, const uint8_t *X, size_t nX, size_t f, uint64_t *pt, uintptr_t stream) {
+    if (!ctx || (nX && f && (!X || !pt))) return BFV_ERR_INVALID_ARG;
+    if (!nX || !f) return BFV_OK;
+    return launch_encode_features(ctx, X, nX, f, (u64 *)pt, S(stream));
+}
+
+int bfv_encode_feature_columns(bfv_ctx *ctx, const uint8_t *X, size_t nX, size_t f, uint64_t *pt, uintptr_t stream) {
+    if (!ctx || nX > (size_t)ctx->N || (nX && f && (!X || !pt))) return BFV_ERR_INVALID_ARG;
+    if (!f) return BFV_OK;
+    if (!nX) return cudaMemsetAsync(pt, 0, f * ctx->N * 8, S(stream)) == cudaSuccess ? BFV_OK : BFV_ERR_CUDA;
+    return launch_encode_columns(ctx, X, nX, f, (u64 *)pt, S(stream));
+}
+
+static size_t align256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+int bfv_encrypt_workspace(const bfv_ctx *ctx, size_t count, size_t *bytes) {
+    if (!ctx || !bytes) return BFV_ERR_INVALID_ARG;
+    *bytes = align256(count * 3 * (size_t)ctx->N);
+    return BFV_OK;
+}
+
+int bfv_encrypt(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *pt, size_t count, uint64_t seed, uint32_t obj0,
+                uint64_t *ct, void *ws, size_t ws_bytes, uintptr_t stream) {
+    if (!ctx || !keys || keys->ctx != ctx) return BFV_ERR_INVALID_ARG;
+    if (!count) return BFV_OK;
+    if (!pt || !ct || !ws) return BFV_ERR_INVALID_ARG;
+    size_t need;
+    bfv_encrypt_workspace(ctx, count, &need);
+    if (ws_bytes < need) return BFV_ERR_OVER_BUDGET;
+    return launch_encrypt(ctx, keys, (const u64 *)pt, count, seed, obj0, (u64 *)ct, ws, S(stream));
+}
+
+int bfv_decrypt_workspace(const bfv_ctx *ctx, size_t count, size_t *bytes) {
+    if (!ctx || !bytes) return BFV_ERR_INVALID_ARG;
+    *bytes = align256(count * (size_t)ctx->L * ctx->N * 8);
+    return BFV_OK;
+}
+
+int bfv_decrypt(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *ct, size_t count, uint64_t *pt, void *ws,
+                size_t ws_bytes, uintptr_t stream) {
+    if (!ctx || !keys || keys->ctx != ctx) return BFV_ERR_INVALID_ARG;
+    if (!count) return BFV_OK;
+    if (!ct || !pt || !ws) return BFV_ERR_INVALID_ARG;
+    size_t need;
+    bfv_decrypt_workspace(ctx, count, &need);
+    if (ws_bytes < need) return BFV_ERR_OVER_BUDGET;
+    return launch_decrypt(ctx, keys, (const u64 *)ct, count, (u64 *)pt, ws, S(stream));
+}
+
+int bfv_model_prepare(bfv_ctx *ctx, const int64_t *W, const int64_t *b, size_t f, size_t nY, uintptr_t stream,
+                      bfv_model **out) {
+    if (!ctx || !W || !b || !out || f == 0 || nY == 0) return BFV_ERR_INVALID_ARG;
+    *out = nullptr;
+    const size_t N = ctx->N, L = ctx->L, K = (f + N - 1) / N;
+    bfv_model *m = new (std::nothrow) bfv_model();
+    if (!m) return BFV_ERR_OOM;
+    m->ctx = ctx;
+    m->f = f;
+    m->nY = nY;
+    m->K = K;
+    int rc;
+    int64_t *dslots = nullptr;
+    u64 *dpt = nullptr;
+    if ((rc = dalloc(&m->w_eval, nY * K * L * 2 * N)) || (rc = dalloc(&m->w_int, f * nY)) ||
+        (rc = dalloc(&m->bias_delta, nY * L)) || (rc = dalloc(&dslots, nY * K * N)) || (rc = dalloc(&dpt, nY * K * N))) {
+        cudaFree(dslots);
+        cudaFree(dpt);
+        bfv_model_free(m);
+        return rc;
+    }
+    for (size_t x = 0; x < f * nY; ++x) {
+        const int64_t a = W[x] < 0 ? -W[x] : W[x];
+        if (a > m->wmax) m->wmax = a;
+    }
+    // transposed, packed weights: slot s of plaintext (j, k) = W[k N + s][j]
+    std::vector<int64_t> slots(nY * K * N, 0);
+    for (size_t j = 0; j < nY; ++j)
+        for (size_t r = 0; r < f; ++r) slots[(j * K + r / N) * N + r % N] = W[r * nY + j];
+    std::vector<u64> bd(nY * L);
+    for (size_t j = 0; j < nY; ++j) {
+        int64_t bt = b[j] % (int64_t)ctx->t;
+        if (bt < 0) bt += (int64_t)ctx->t;
+        for (size_t l = 0; l < L; ++l) bd[j * L + l] = mulmod_h(ctx->delta_host[l], (u64)bt % ctx->primes[l], ctx->primes[l]);
+    }
+    cudaStream_t st = S(stream);
+    rc = BFV_OK;
+    if (cudaMemcpyAsync(dslots, slots.data(), slots.size() * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(m->w_int, W, f * nY * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(m->bias_delta, bd.data(), bd.size() * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        rc = BFV_ERR_CUDA;
+    if (!rc) rc = launch_encode(ctx, dslots, nY * K, dpt, st);
+    if (!rc) rc = launch_model_weights(ctx, m, dpt, st);
+    if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = BFV_ERR_CUDA;
+    cudaFree(dslots);
+    cudaFree(dpt);
+    if (rc) { bfv_model_free(m); return rc; }
+    *out = m;
+    return BFV_OK;
+}
+
+int bfv_model_free(bfv_model *m) {
+    if (!m) return BFV_ERR_INVALID_ARG;
+    cudaFree(m->w_eval);
+    cudaFree(m->w_int);
+    cudaFree(m->bias_delta);
+    delete m;
+    return BFV_OK;
+}
+
+int bfv_lr_scores_packed_workspace(const bfv_ctx *ctx, const bfv_model *model, size_t nX, size_t pair_chunk,
+                                   size_t *bytes) {
+    if (!ctx || !model || model->ctx != ctx || !bytes || nX == 0) return BFV_ERR_INVALID_ARG;
+    *bytes = packed_plan(ctx, model, nX, pair_chunk).total;
+    return BFV_OK;
+}
+
+int bfv_lr_scores_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint64_t *X_ct, size_t nX,
+                         uint64_t *Y_ct, void *ws, size_t ws_bytes, size_t pair_chunk, uintptr_t stream) {
+    if (!ctx || !keys || !model || keys->ctx != ctx || model->ctx != ctx) return BFV_ERR_INVALID_ARG;
+    if (nX == 0) return BFV_OK;
+    if (!X_ct || !Y_ct || !ws) return BFV_ERR_INVALID_ARG;
+    PackedPlan plan = packed_plan(ctx, model, nX, pair_chunk);
+    if (ws_bytes < plan.total) return BFV_ERR_OVER_BUDGET;
+    return launch_packed(ctx, keys, model, (const u64 *)X_ct, nX, (u64 *)Y_ct, ws, plan, S(stream));
+}
+
+int bfv_lr_scores_standard(bfv_ctx *ctx, const bfv_model *model, const uint64_t *X_ct, size_t nX, uint64_t *Y_ct,
+                           uintptr_t stream) {
+    if (!ctx || !model || model->ctx != ctx || nX > (size_t)ctx->N) return BFV_ERR_INVALID_ARG;
+    if (!X_ct || !Y_ct) return BFV_ERR_INVALID_ARG;
+    // signed 64-bit accumulators of w * (28-bit halves) stay exact while |w| f < 2^35
+    if (model->wmax >= (1ll << 31) || (double)model->wmax * (double)model->f >= 34359738368.0) return BFV_ERR_BAD_PARAMS;
+    return launch_standard(ctx, model, (const u64 *)X_ct, (u64 *)Y_ct, S(stream));
+}
+
+int bfv_lr_packed_pair_from_workspace(bfv_ctx *ctx, const bfv_model *model, size_t nX, size_t pair_chunk,
+                                      const void *ws, size_t g, uint64_t *ct_out, uintptr_t stream) {
+    if (!ctx || !model || model->ctx != ctx || !ws || !ct_out) return BFV_ERR_INVALID_ARG;
+    PackedPlan plan = packed_plan(ctx, model, nX, pair_chunk);
+    if (g >= plan.npairs) return BFV_ERR_INVALID_ARG;
+    const size_t last_chunk_start = ((plan.npairs - 1) / plan.chunk) * plan.chunk;
+    if (g < last_chunk_start) return BFV_ERR_INVALID_ARG;
+    int rc = launch_pair_export(ctx, plan, ws, g - last_chunk_start, (u64 *)ct_out, S(stream));
+    if (rc) return rc;
+    return cudaStreamSynchronize(S(stream)) == cudaSuccess ? BFV_OK : BFV_ERR_CUDA;
+}
+
+int bfv_launch_count(const bfv_ctx *ctx, uint64_t *count) {
+    if (!ctx || !count) return BFV_ERR_INVALID_ARG;
+    *count = ctx->launches.load();
+    return BFV_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,341 @@
+// k_packed.cu -- the packed matrix product of Algorithm 1 (Section 4.2.3) with bias.
+//
+// Pairs g = i*|Y| + j are processed in chunks. Per chunk, in evaluation form:
+//   MAC          C[g] = sum_k X[i][k] (.) W[j][k]                         (Algorithm 1 lines 5-13)
+//   log2 N times C[g] += rot_gal(C[g])                                    (lines 14-17)
+//       rot(c) = (sigma(c0) + u0', u1'), (u0', u1') = KS(sigma(c1)):
+//       ks_prep     c1 limb l -> sigma -> inverse NTT -> digit d_l (coefficients);
+//                   c0 limb l -> c0 + sigma(c0)
+//       ks_modup    for target limb j of QP and half h of the evaluation points:
+//                   U_c[j] = sum_i NTT_j(d_i mod q_j) (.) key[i][c][j]; the first
+//                   Cooley-Tukey stage is folded into the load, so each CTA transforms
+//                   only its half of the points
+//       ks_moddown_p  inverse NTT of U_c[P], r = [U_c[P] + floor(P/2)]_P
+//       ks_moddown  C_c[l] += (U_c[l] + NTT_l(floor(P/2) - r)) * P^-1
+//   bias+mask    C0 += Delta b_j; C *= NTT(mask_g), mask_g one-hot at slot g mod N (18-22)
+//   compress     Yacc[g / N] += C[g]                                       (25-42)
+// and finally Y = inverse NTT(Yacc).
+#include <algorithm>
+
+#include "bfv_internal.h"
+
+namespace {
+
+template <int M> constexpr size_t pad_bytes() { return sizeof(u64) * PadSize<M>::value; }
+template <class K> void set_smem(K kern, size_t bytes) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// ------------------------------------------------------------------ MAC (lines 5-13)
+// C[g][c][l][p] = sum_k Xe[i][k][c][l][p] * We[j][k][l][p]; grid.x = (g, c, l), grid.y = tile.
+__global__ void __launch_bounds__(256) k_mac(const ModTab *__restrict__ mods, int N, int L, int K, int nY, size_t g0,
+                                             const u64 *__restrict__ Xe, const u64 *__restrict__ We, u64 *C) {
+    const size_t x = blockIdx.x;
+    const int l = (int)(x % L), c = (int)((x / L) % 2);
+    const size_t gl = x / (2 * L), g = g0 + gl;
+    const size_t i = g / nY, j = g % nY;
+    const u64 q = mods[l].q, q2 = 2 * q;
+    const size_t ctw = 2 * (size_t)L * N;
+    const int p0 = blockIdx.y * 1024 + threadIdx.x;
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+        const int p = p0 + e * 256;
+        if (p >= N) break;
+        u64 acc = 0;
+        for (int k = 0; k < K; ++k) {
+            const u64 xv = Xe[(i * K + k) * ctw + ((size_t)c * L + l) * N + p];
+            const u64 *w = We + (((j * K + k) * L + l) * 2) * (size_t)N;
+            acc = red2(acc + mul_shoup(xv, w[p], w[N + p], q), q2);
+        }
+        C[gl * ctw + ((size_t)c * L + l) * N + p] = red1(acc, q);
+    }
+}
+
+// ------------------------------------------------------------------ key switching
+
+// grid.x = (g, c, l). c = 1: digit D[g][l] = INTT(sigma(C1[g][l])); c = 0: C0 += sigma(C0).
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 gal, u64 *C,
+                                                           u64 *D) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const int l = blockIdx.x % L, c = (blockIdx.x / L) % 2;
+    const size_t g = blockIdx.x / (2 * L);
+    const ModTab T = mods[l];
+    u64 *limb = C + ((g * 2 + c) * L + l) * (size_t)N;
+    if (c == 1) {
+        u64 *dst = D + (g * L + l) * (size_t)N;
+        ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return limb[auto_src(p, gal, LOGN)]; },
+                              [&](int p, u64 v) { dst[p] = v; });
+    } else {
+        for (int p = threadIdx.x; p < N; p += NT) sm[p] = limb[p];
+        __syncthreads();
+        for (int p = threadIdx.x; p < N; p += NT) limb[p] = add_mod(sm[p], sm[auto_src(p, gal, LOGN)], T.q);
+    }
+}
+
+// grid.x = (g, j, h): U[g][c][j][h N/2 + p] = sum_i NTT_j(D[g][i] mod q_j)[h N/2 + p] * key[i][c][j].
+// The digit of index j itself is sigma(C1[g][j]) in evaluation form already.
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN - 1)) k_ks_modup(const ModTab *__restrict__ mods, int L, u32 gal,
+                                                                const u64 *__restrict__ C, const u64 *__restrict__ D,
+                                                                const u64 *__restrict__ key, u64 *U) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, H = N / 2, NT = nt_for(LOGN - 1);
+    u64 *acc0 = sm + PadSize<H>::value, *acc1 = acc0 + H;
+    const int nqp = L + 1;
+    const int h = blockIdx.x % 2, j = (blockIdx.x / 2) % nqp;
+    const size_t g = blockIdx.x / (2 * nqp);
+    const ModTab T = mods[j];
+    const u64 q = T.q, q2 = T.q2;
+    const u64 w1 = T.fw[1], w1p = T.fwp[1];
+    for (int p = threadIdx.x; p < H; p += NT) { acc0[p] = 0; acc1[p] = 0; }
+    const size_t keystride = (size_t)nqp * 2 * N;     // one (digit, component) block
+#pragma unroll 1
+    for (int i = 0; i < L; ++i) {
+        const u64 *k0 = key + ((size_t)i * 2 + 0) * keystride + (size_t)j * 2 * N + (size_t)h * H;
+        const u64 *k1 = key + ((size_t)i * 2 + 1) * keystride + (size_t)j * 2 * N + (size_t)h * H;
+        if (i == j) {
+            const u64 *c1 = C + ((g * 2 + 1) * L + j) * (size_t)N;
+            __syncthreads();
+            for (int p = threadIdx.x; p < H; p += NT) {
+                const u64 v = c1[auto_src(h * H + p, gal, LOGN)];
+                acc0[p] = red2(acc0[p] + mul_shoup(v, k0[p], k0[N + p], q), q2);
+                acc1[p] = red2(acc1[p] + mul_shoup(v, k1[p], k1[N + p], q), q2);
+            }
+        } else {
+            const u64 *d = D + (g * L + i) * (size_t)N;
+            ntt_forward<LOGN - 1, NT>(
+                sm, T, 1, h,
+                [&](int p) {
+                    const u64 a = red1(d[p], q), b = red1(d[p + H], q);
+                    const u64 t = mul_shoup(b, w1, w1p, q);
+                    return h == 0 ? a + t : a - t + q2;
+                },
+                [&](int p, u64 v) { sm[padi(p)] = v; });
+            __syncthreads();
+            for (int p = threadIdx.x; p < H; p += NT) {
+                const u64 v = sm[padi(p)];
+                acc0[p] = red2(acc0[p] + mul_shoup(v, k0[p], k0[N + p], q), q2);
+                acc1[p] = red2(acc1[p] + mul_shoup(v, k1[p], k1[N + p], q), q2);
+            }
+            __syncthreads();
+        }
+    }
+    __syncthreads();
+    u64 *u0 = U + ((g * 2 + 0) * nqp + j) * (size_t)N + (size_t)h * H;
+    u64 *u1 = U + ((g * 2 + 1) * nqp + j) * (size_t)N + (size_t)h * H;
+    for (int p = threadIdx.x; p < H; p += NT) { u0[p] = red1(acc0[p], q); u1[p] = red1(acc1[p], q); }
+}
+
+// grid.x = (g, c): R[g][c] = [INTT_P(U[g][c][P]) + floor(P/2)]_P.
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_ks_moddown_p(const ModTab *__restrict__ mods, int L,
+                                                                const u64 *__restrict__ U, u64 *R) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const int nqp = L + 1;
+    const size_t gc = blockIdx.x;
+    const ModTab T = mods[L];
+    const u64 *src = U + (gc * nqp + L) * (size_t)N;
+    u64 *dst = R + gc * N;
+    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return src[p]; },
+                          [&](int p, u64 v) { dst[p] = add_mod(v, T.phalf, T.q); });
+}
+
+// grid.x = (g, c, l): C[g][c][l] += (U[g][c][l] + NTT_l(floor(P/2) - r)) * P^-1.
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_ks_moddown(const ModTab *__restrict__ mods, int L,
+                                                              const u64 *__restrict__ U, const u64 *__restrict__ R,
+                                                              u64 *C) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const int nqp = L + 1;
+    const int l = blockIdx.x % L, c = (blockIdx.x / L) % 2;
+    const size_t g = blockIdx.x / (2 * L);
+    const ModTab T = mods[l];
+    const u64 *r = R + (g * 2 + c) * (size_t)N;
+    ntt_forward<LOGN, NT>(sm, T, 0, 0, [&](int p) { return T.phalf + (T.q - red1(r[p], T.q)); },
+                          [&](int p, u64 v) { sm[padi(p)] = v; });
+    __syncthreads();
+    const u64 *u = U + ((g * 2 + c) * nqp + l) * (size_t)N;
+    u64 *dst = C + ((g * 2 + c) * L + l) * (size_t)N;
+    for (int p = threadIdx.x; p < N; p += NT) {
+        const u64 v = red1(mul_shoup(u[p] + sm[padi(p)], T.pinv, T.pinvp, T.q), T.q);
+        dst[p] = add_mod(dst[p], v, T.q);
+    }
+}
+
+// ------------------------------------------------------------------ bias + mask (lines 18-22)
+// grid.x = (g, l): C0 += Delta [b_j]_t; C *= NTT(centred lift of the one-hot plaintext at slot
+// (g0+g) mod N), whose coefficient k is N^-1 omega^(-e k) mod t, e the slot's exponent.
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_bias_mask(const ModTab *__restrict__ mods, int L, int tmod, int nY,
+                                                             size_t g0, const u32 *__restrict__ maskpow,
+                                                             const u64 *__restrict__ bias_delta, u64 *C) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const int l = blockIdx.x % L;
+    const size_t gl = blockIdx.x / L, g = g0 + gl;
+    const int j = (int)(g % nY), s = (int)(g % N);
+    const ModTab T = mods[l];
+    const u64 t = mods[tmod].q, th = (t - 1) / 2;
+    const u32 twoN = 2u * N;
+    u32 e = 1, base = 3;                               // e = 3^(s mod N/2) mod 2N
+    for (u32 x = (u32)(s % (N / 2)); x; x >>= 1) {
+        if (x & 1) e = (e * base) & (twoN - 1);
+        base = (base * base) & (twoN - 1);
+    }
+    if (s >= N / 2) e = twoN - e;
+    ntt_forward<LOGN, NT>(
+        sm, T, 0, 0,
+        [&](int p) {
+            const u32 idx = (twoN - ((e * (u32)p) & (twoN - 1))) & (twoN - 1);
+            const u64 v = maskpow[idx];
+            return v <= th ? v : T.q - (t - v);
+        },
+        [&](int p, u64 v) { sm[padi(p)] = v; });
+    __syncthreads();
+    const u64 bd = bias_delta[(size_t)j * L + l];
+    u64 *c0 = C + ((gl * 2 + 0) * L + l) * (size_t)N, *c1 = C + ((gl * 2 + 1) * L + l) * (size_t)N;
+    for (int p = threadIdx.x; p < N; p += NT) {
+        const u64 m = sm[padi(p)];
+        c0[p] = mul_barrett(add_mod(c0[p], bd, T.q), m, T.q, T.mu, T.bits);
+        c1[p] = mul_barrett(c1[p], m, T.q, T.mu, T.bits);
+    }
+}
+
+// ------------------------------------------------------------------ compression (lines 25-42)
+// Yacc[e] += sum_{g in [ga, gb)} C[g - g0][e] for every element e of one output ciphertext.
+__global__ void __launch_bounds__(256) k_compress(const ModTab *__restrict__ mods, int N, int L, size_t ga, size_t gb,
+                                                  size_t g0, const u64 *__restrict__ C, u64 *Yacc) {
+    const size_t ctw = 2 * (size_t)L * N;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= ctw) return;
+    const u64 q = mods[(e / N) % L].q;
+    u64 acc = Yacc[e];
+    size_t g = ga;
+    for (; g + 4 <= gb; g += 4) {
+        const u64 a = C[(g - g0) * ctw + e], b = C[(g + 1 - g0) * ctw + e];
+        const u64 c = C[(g + 2 - g0) * ctw + e], d = C[(g + 3 - g0) * ctw + e];
+        acc = red1(acc + red1(a + b, q), q);
+        acc = red1(acc + red1(c + d, q), q);
+    }
+    for (; g < gb; ++g) acc = red1(acc + C[(g - g0) * ctw + e], q);
+    Yacc[e] = acc;
+}
+
+// Pair state (evaluation form) -> coefficient form.
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_intt_copy(const ModTab *__restrict__ mods, int L,
+                                                             const u64 *__restrict__ in, u64 *out) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const size_t x = blockIdx.x;
+    const ModTab T = mods[x % L];
+    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return in[x * N + p]; }, [&](int p, u64 v) { out[x * N + p] = v; });
+}
+
+int last_err() { return cudaGetLastError() == cudaSuccess ? BFV_OK : BFV_ERR_CUDA; }
+
+template <int LOGN>
+int run_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const u64 *X_ct, u64 *Y_ct, char *ws,
+               const PackedPlan &pl, cudaStream_t st) {
+    constexpr int N = 1 << LOGN;
+    const int L = c->L, nqp = c->nqp;
+    const size_t ctw = 2 * (size_t)L * N;
+    u64 *Xe = (u64 *)(ws + pl.off_xntt), *Yacc = (u64 *)(ws + pl.off_yacc), *C = (u64 *)(ws + pl.off_state);
+    u64 *D = (u64 *)(ws + pl.off_digits), *U = (u64 *)(ws + pl.off_u), *R = (u64 *)(ws + pl.off_r);
+    const size_t full = pad_bytes<N>(), half = pad_bytes<N / 2>() + 2 * sizeof(u64) * (N / 2);
+    set_smem(k_ks_prep<LOGN>, full);
+    set_smem(k_ks_modup<LOGN>, half);
+    set_smem(k_ks_moddown_p<LOGN>, full);
+    set_smem(k_ks_moddown<LOGN>, full);
+    set_smem(k_bias_mask<LOGN>, full);
+
+    int rc = launch_ntt_limbs(c, X_ct, Xe, pl.nX * pl.K, true, st);
+    if (rc) return rc;
+    if (cudaMemsetAsync(Yacc, 0, pl.nout * ctw * sizeof(u64), st) != cudaSuccess) return BFV_ERR_CUDA;
+    const size_t keyblock = (size_t)L * 2 * nqp * 2 * N;   // one Galois element
+    for (size_t g0 = 0; g0 < pl.npairs; g0 += pl.chunk) {
+        const size_t ng = std::min(pl.chunk, pl.npairs - g0);
+        k_mac<<<dim3((unsigned)(ng * 2 * L), (unsigned)((N + 1023) / 1024)), 256, 0, st>>>(
+            c->dmods, N, L, (int)pl.K, (int)pl.nY, g0, Xe, m->w_eval, C);
+        count_launch(c);
+        for (int s = 0; s < k->ng; ++s) {
+            const u32 gal = (u32)c->galois[s];
+            const u64 *key = k->gk_eval + (size_t)s * keyblock;
+            k_ks_prep<LOGN><<<(unsigned)(ng * 2 * L), nt_for(LOGN), full, st>>>(c->dmods, L, gal, C, D);
+            k_ks_modup<LOGN><<<(unsigned)(ng * nqp * 2), nt_for(LOGN - 1), half, st>>>(c->dmods, L, gal, C, D, key, U);
+            k_ks_moddown_p<LOGN><<<(unsigned)(ng * 2), nt_for(LOGN), full, st>>>(c->dmods, L, U, R);
+            k_ks_moddown<LOGN><<<(unsigned)(ng * 2 * L), nt_for(LOGN), full, st>>>(c->dmods, L, U, R, C);
+            count_launch(c, 4);
+        }
+        k_bias_mask<LOGN><<<(unsigned)(ng * L), nt_for(LOGN), full, st>>>(c->dmods, L, nqp, (int)pl.nY, g0, c->dmaskpow,
+                                                                         m->bias_delta, C);
+        count_launch(c);
+        for (size_t o = g0 / N; o <= (g0 + ng - 1) / N; ++o) {
+            const size_t ga = std::max(g0, o * N), gb = std::min(g0 + ng, (o + 1) * N);
+            k_compress<<<(unsigned)((ctw + 255) / 256), 256, 0, st>>>(c->dmods, N, L, ga, gb, g0, C, Yacc + o * ctw);
+            count_launch(c);
+        }
+        if ((rc = last_err())) return rc;
+    }
+    return launch_ntt_limbs(c, Yacc, Y_ct, pl.nout, false, st);
+}
+
+}  // namespace
+
+static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
+
+PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t chunk) {
+    PackedPlan p{};
+    const size_t N = c->N, L = c->L, nqp = c->nqp;
+    p.nX = nX;
+    p.nY = m->nY;
+    p.K = m->K;
+    p.npairs = nX * m->nY;
+    p.nout = (p.npairs + N - 1) / N;
+    p.chunk = chunk ? std::min(chunk, p.npairs) : std::min<size_t>(p.npairs, 2048);
+    const size_t ctb = 2 * L * N * sizeof(u64);
+    size_t off = 0;
+    p.off_xntt = off; off += al256(nX * p.K * ctb);
+    p.off_yacc = off; off += al256(p.nout * ctb);
+    p.off_state = off; off += al256(p.chunk * ctb);
+    p.off_digits = off; off += al256(p.chunk * L * N * sizeof(u64));
+    p.off_u = off; off += al256(p.chunk * 2 * nqp * N * sizeof(u64));
+    p.off_r = off; off += al256(p.chunk * 2 * N * sizeof(u64));
+    p.total = off;
+    return p;
+}
+
+int launch_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const u64 *X_ct, size_t nX, u64 *Y_ct,
+                  void *ws, const PackedPlan &plan, cudaStream_t st) {
+    (void)nX;
+    switch (c->logN) {
+        case 12: return run_packed<12>(c, k, m, X_ct, Y_ct, (char *)ws, plan, st);
+        case 13: return run_packed<13>(c, k, m, X_ct, Y_ct, (char *)ws, plan, st);
+        case 14: return run_packed<14>(c, k, m, X_ct, Y_ct, (char *)ws, plan, st);
+        default: return BFV_ERR_BAD_PARAMS;
+    }
+}
+
+int launch_pair_export(const bfv_ctx *c, const PackedPlan &plan, const void *ws, size_t slot, u64 *ct_out,
+                       cudaStream_t st) {
+    const size_t ctw = 2 * (size_t)c->L * c->N;
+    const u64 *C = (const u64 *)((const char *)ws + plan.off_state) + slot * ctw;
+#define L_(LG)                                                                                              \
+    {                                                                                                       \
+        set_smem(k_intt_copy<LG>, pad_bytes<(1 << LG)>());                                                  \
+        k_intt_copy<LG><<<2 * c->L, nt_for(LG), pad_bytes<(1 << LG)>(), st>>>(c->dmods, c->L, C, ct_out);   \
+    }
+    switch (c->logN) {
+        case 12: L_(12); break;
+        case 13: L_(13); break;
+        case 14: L_(14); break;
+        default: return BFV_ERR_BAD_PARAMS;
+    }
+#undef L_
+    count_launch(c);
+    return last_err();
+}

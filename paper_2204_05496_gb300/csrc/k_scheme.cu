@@ -1,0 +1,525 @@
+// k_scheme.cu -- BFV scheme kernels: limb NTTs, batch encode/decode, key generation,
+// public-key encryption and exact decryption, model (weight) encoding.
+#include "bfv_internal.h"
+
+namespace {
+
+constexpr int kSkPurpose = 1, kPkA = 2, kPkE = 3, kGkA = 4, kGkE = 5, kEnc = 6;
+
+template <int LOGN> constexpr size_t smem_full() { return sizeof(u64) * PadSize<(1 << LOGN)>::value; }
+
+template <class K> void set_smem(K kern, size_t bytes) {
+    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+}
+
+// uniform residue mod q from four ChaCha words taken as a 128-bit integer
+__device__ __forceinline__ u64 uniform_of(const u32 *w, const ModTab &T) {
+    const u64 lo = (u64)w[0] | ((u64)w[1] << 32), hi = (u64)w[2] | ((u64)w[3] << 32);
+    const u64 h = red1(mul_shoup(hi % T.q, T.r64, T.r64p, T.q), T.q);
+    return add_mod(h, lo % T.q, T.q);
+}
+
+// ------------------------------------------------------------------ limb transforms
+// in/out: [nlimbs][N]; limb x uses modulus x % L.
+template <int LOGN, bool FWD>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_ntt_limbs(const ModTab *__restrict__ mods, int L,
+                                                             const u64 *in, u64 *out) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const size_t x = blockIdx.x;
+    const ModTab T = mods[x % L];
+    const u64 *src = in + x * N;
+    u64 *dst = out + x * N;
+    if constexpr (FWD)
+        ntt_forward<LOGN, NT>(sm, T, 0, 0, [&](int p) { return src[p]; }, [&](int p, u64 v) { dst[p] = v; });
+    else
+        ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return src[p]; }, [&](int p, u64 v) { dst[p] = v; });
+}
+
+// Inverse transform of value arrays stored as [limb][2][N] (value, companion); limb x uses
+// modulus x % M; output [limb][N].
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_intt_pairs(const ModTab *__restrict__ mods, int M,
+                                                              const u64 *__restrict__ in, u64 *out) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const size_t x = blockIdx.x;
+    const ModTab T = mods[x % M];
+    const u64 *src = in + x * 2 * N;
+    u64 *dst = out + x * N;
+    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return src[p]; }, [&](int p, u64 v) { dst[p] = v; });
+}
+
+// ------------------------------------------------------------------ encode / decode (mod t)
+
+// slots [count][N] -> plaintext [count][N]; slot l goes to evaluation position slot_pos[l].
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_encode(const ModTab *__restrict__ mods, int tmod,
+                                                          const u32 *__restrict__ slot_pos, const int64_t *slots,
+                                                          u64 *pt) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const ModTab T = mods[tmod];
+    const int64_t *src = slots + (size_t)blockIdx.x * N;
+    const int64_t t = (int64_t)T.q;
+    for (int l = threadIdx.x; l < N; l += NT) {
+        int64_t v = src[l] % t;
+        if (v < 0) v += t;
+        sm[padi(slot_pos[l])] = (u64)v;
+    }
+    __syncthreads();
+    u64 *dst = pt + (size_t)blockIdx.x * N;
+    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return sm[padi(p)]; }, [&](int p, u64 v) { dst[p] = v; });
+}
+
+// Packed features: plaintext (i, k) slot s = X[i][k N + s] (0 past f).
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_encode_features(const ModTab *__restrict__ mods, int tmod,
+                                                                   const u32 *__restrict__ slot_pos,
+                                                                   const uint8_t *__restrict__ X, size_t f, int K,
+                                                                   u64 *pt) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const ModTab T = mods[tmod];
+    const size_t i = blockIdx.x / K, k = blockIdx.x % K;
+    const uint8_t *row = X + i * f;
+    for (int s = threadIdx.x; s < N; s += NT) {
+        const size_t col = k * N + s;
+        sm[padi(slot_pos[s])] = col < f ? (u64)row[col] % T.q : 0;
+    }
+    __syncthreads();
+    u64 *dst = pt + (size_t)blockIdx.x * N;
+    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return sm[padi(p)]; }, [&](int p, u64 v) { dst[p] = v; });
+}
+
+// Feature columns: plaintext f' slot i = X[i][f'] for i < nX.
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_encode_columns(const ModTab *__restrict__ mods, int tmod,
+                                                                  const u32 *__restrict__ slot_pos,
+                                                                  const uint8_t *__restrict__ X, size_t nX, size_t f,
+                                                                  u64 *pt) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const ModTab T = mods[tmod];
+    const size_t col = blockIdx.x;
+    for (int s = threadIdx.x; s < N; s += NT) sm[padi(slot_pos[s])] = (size_t)s < nX ? (u64)X[s * f + col] % T.q : 0;
+    __syncthreads();
+    u64 *dst = pt + col * N;
+    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return sm[padi(p)]; }, [&](int p, u64 v) { dst[p] = v; });
+}
+
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_decode(const ModTab *__restrict__ mods, int tmod,
+                                                          const u32 *__restrict__ slot_pos, const u64 *pt,
+                                                          int64_t *slots) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const ModTab T = mods[tmod];
+    const u64 *src = pt + (size_t)blockIdx.x * N;
+    ntt_forward<LOGN, NT>(sm, T, 0, 0, [&](int p) { return src[p]; }, [&](int p, u64 v) { sm[padi(p)] = v; });
+    __syncthreads();
+    int64_t *dst = slots + (size_t)blockIdx.x * N;
+    for (int l = threadIdx.x; l < N; l += NT) dst[l] = (int64_t)sm[padi(slot_pos[l])];
+}
+
+// ------------------------------------------------------------------ key generation
+
+__global__ void k_keygen_sk(u64 seed, int N, int8_t *sk) {
+    const int k = blockIdx.x * blockDim.x + threadIdx.x;
+    if (k >= N) return;
+    u32 w[16];
+    chacha20_block(seed, (u32)k, kSkPurpose, 0, 0, w);
+    sk[k] = (int8_t)ternary_of(w[0]);
+}
+
+// Evaluation form of s for every modulus of QP: out [nqp][2][N] (value, companion).
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_keygen_sk_eval(const ModTab *__restrict__ mods,
+                                                                  const int8_t *__restrict__ sk, u64 *out) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const int j = blockIdx.x;
+    const ModTab T = mods[j];
+    u64 *dst = out + (size_t)j * 2 * N;
+    ntt_forward<LOGN, NT>(sm, T, 0, 0, [&](int p) { return lift_small(sk[p], T.q); },
+                          [&](int p, u64 v) { dst[p] = v; dst[N + p] = shoup_companion(v, T.q); });
+}
+
+// Public key limb l: pk1 = a (uniform), pk0 = -(a s + e); out [2][L][2][N].
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_keygen_pk(const ModTab *__restrict__ mods, const u64 *__restrict__ cdt,
+                                                             int cdt_len, u64 seed, int L, const u64 *__restrict__ sk_eval,
+                                                             u64 *pk) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const int l = blockIdx.x;
+    const ModTab T = mods[l];
+    u64 *pk0 = pk + (size_t)l * 2 * N, *pk1 = pk + ((size_t)L + l) * 2 * N;
+    const u64 *s = sk_eval + (size_t)l * 2 * N;
+    ntt_forward<LOGN, NT>(
+        sm, T, 0, 0,
+        [&](int p) { u32 w[16]; chacha20_block(seed, (u32)p, kPkA, 0, (u32)l, w); return uniform_of(w, T); },
+        [&](int p, u64 v) {
+            pk1[p] = v; pk1[N + p] = shoup_companion(v, T.q);
+            pk0[p] = red1(mul_shoup(v, s[p], s[N + p], T.q), T.q);   // a s, finished below
+        });
+    __syncthreads();
+    ntt_forward<LOGN, NT>(
+        sm, T, 0, 0,
+        [&](int p) { u32 w[16]; chacha20_block(seed, (u32)p, kPkE, 0, 0, w); return lift_small(gauss_of(w[0], w[1], w[2], cdt, cdt_len), T.q); },
+        [&](int p, u64 v) {
+            const u64 r = sub_mod(0, add_mod(pk0[p], v, T.q), T.q);
+            pk0[p] = r; pk0[N + p] = shoup_companion(r, T.q);
+        });
+}
+
+// Galois key (element gi, digit i, limb j of QP):
+//   k1 = a, k0 = -a s + e + [i == j] [P]_{q_j} sigma_g(s); out [ng][L][2][nqp][2][N].
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_keygen_galois(const ModTab *__restrict__ mods, const u64 *__restrict__ cdt,
+                                                                 int cdt_len, u64 seed, int L, const u64 *__restrict__ gal,
+                                                                 const u64 *__restrict__ sk_eval, u64 *gk) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const int nqp = L + 1;
+    const int j = blockIdx.x % nqp, i = (blockIdx.x / nqp) % L, gi = blockIdx.x / (nqp * L);
+    const ModTab T = mods[j];
+    const u32 obj = (u32)gi * 256u + (u32)i;
+    const u32 g = (u32)gal[gi];
+    u64 *k0 = gk + ((((size_t)gi * L + i) * 2 + 0) * nqp + j) * 2 * N;
+    u64 *k1 = gk + ((((size_t)gi * L + i) * 2 + 1) * nqp + j) * 2 * N;
+    const u64 *s = sk_eval + (size_t)j * 2 * N;
+    ntt_forward<LOGN, NT>(
+        sm, T, 0, 0,
+        [&](int p) { u32 w[16]; chacha20_block(seed, (u32)p, kGkA, obj, (u32)j, w); return uniform_of(w, T); },
+        [&](int p, u64 v) {
+            k1[p] = v; k1[N + p] = shoup_companion(v, T.q);
+            k0[p] = red1(mul_shoup(v, s[p], s[N + p], T.q), T.q);
+        });
+    __syncthreads();
+    const u64 pmod = mods[L].q % T.q;
+    ntt_forward<LOGN, NT>(
+        sm, T, 0, 0,
+        [&](int p) { u32 w[16]; chacha20_block(seed, (u32)p, kGkE, obj, 0, w); return lift_small(gauss_of(w[0], w[1], w[2], cdt, cdt_len), T.q); },
+        [&](int p, u64 v) {
+            u64 r = sub_mod(v, k0[p], T.q);
+            if (i == j) r = add_mod(r, mul_barrett(pmod, s[auto_src(p, g, LOGN)], T.q, T.mu, T.bits), T.q);
+            k0[p] = r; k0[N + p] = shoup_companion(r, T.q);
+        });
+}
+
+// ------------------------------------------------------------------ encryption
+
+// Randomness of ciphertext c (object obj0 + c): u, e1, e2 per coefficient -> ws [count][3][N] int8.
+__global__ void k_enc_sample(const u64 *__restrict__ cdt, int cdt_len, u64 seed, u32 obj0, int N, size_t total,
+                             int8_t *ws) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const size_t c = idx / N;
+    const int k = (int)(idx % N);
+    u32 w[16];
+    chacha20_block(seed, (u32)k, kEnc, obj0 + (u32)c, 0, w);
+    int8_t *dst = ws + c * 3 * N;
+    dst[k] = (int8_t)ternary_of(w[0]);
+    dst[N + k] = (int8_t)gauss_of(w[1], w[2], w[3], cdt, cdt_len);
+    dst[2 * N + k] = (int8_t)gauss_of(w[4], w[5], w[6], cdt, cdt_len);
+}
+
+// CTA (c, comp, l): comp 0 -> pk0 u + e1 + Delta m, comp 1 -> pk1 u + e2 (limb l).
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_enc_main(const ModTab *__restrict__ mods, int L,
+                                                            const u64 *__restrict__ pk, const int8_t *__restrict__ rnd,
+                                                            const u64 *__restrict__ pt, u64 *ct) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const int l = blockIdx.x % L, comp = (blockIdx.x / L) % 2;
+    const size_t c = blockIdx.x / (2 * L);
+    const ModTab T = mods[l];
+    const int8_t *u = rnd + c * 3 * N, *e = rnd + c * 3 * N + (size_t)(1 + comp) * N;
+    const u64 *key = pk + ((size_t)comp * L + l) * 2 * N;
+    const u64 *m = pt + c * N;
+    u64 *out = ct + ((c * 2 + comp) * L + l) * (size_t)N;
+    ntt_forward<LOGN, NT>(sm, T, 0, 0, [&](int p) { return lift_small(u[p], T.q); },
+                          [&](int p, u64 v) { sm[padi(p)] = mul_shoup(v, key[p], key[N + p], T.q); });
+    __syncthreads();
+    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return sm[padi(p)]; }, [&](int p, u64 v) {
+        u64 r = add_mod(v, lift_small(e[p], T.q), T.q);
+        if (comp == 0) r = add_mod(r, mul_barrett(T.delta, m[p] % T.q, T.q, T.mu, T.bits), T.q);
+        out[p] = r;
+    });
+}
+
+// ------------------------------------------------------------------ decryption
+
+// CTA (c, l): x_l = [c0 + c1 s]_{q_l} -> ws [count][L][N].
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_dec_inner(const ModTab *__restrict__ mods, int L,
+                                                             const u64 *__restrict__ sk_eval, const u64 *__restrict__ ct,
+                                                             u64 *x) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const int l = blockIdx.x % L;
+    const size_t c = blockIdx.x / L;
+    const ModTab T = mods[l];
+    const u64 *c0 = ct + (c * 2 * L + l) * (size_t)N, *c1 = ct + ((c * 2 + 1) * L + l) * (size_t)N;
+    const u64 *s = sk_eval + (size_t)l * 2 * N;
+    ntt_forward<LOGN, NT>(sm, T, 0, 0, [&](int p) { return c1[p]; },
+                          [&](int p, u64 v) { sm[padi(p)] = mul_shoup(v, s[p], s[N + p], T.q); });
+    __syncthreads();
+    u64 *dst = x + (c * L + l) * (size_t)N;
+    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return sm[padi(p)]; },
+                          [&](int p, u64 v) { dst[p] = add_mod(v, c0[p], T.q); });
+}
+
+// m = floor((t x + floor(Q/2)) / Q) mod t per coefficient, x = CRT(x_0..x_{L-1}) in [0, Q):
+// Garner mixed-radix digits, Horner to a multi-word integer, binary long division.
+__global__ void k_dec_round(const ModTab *__restrict__ mods, const DecConst *__restrict__ dc, const u64 *__restrict__ x,
+                            int N, size_t total, u64 *pt) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const size_t c = idx / N;
+    const int k = (int)(idx % N);
+    const int L = dc->L, W = dc->W;
+    u64 v[BFV_MAXP];
+    for (int i = 0; i < L; ++i) {
+        const u64 qi = mods[i].q;
+        u64 a = x[(c * L + i) * (size_t)N + k];
+        for (int j = 0; j < i; ++j) {
+            a = sub_mod(a, red1(v[j], qi), qi);
+            a = red1(mul_shoup(a, dc->inv[j][i], dc->invp[j][i], qi), qi);
+        }
+        v[i] = a;
+    }
+    u64 w[BFV_MAXW];
+    for (int i = 0; i < W; ++i) w[i] = 0;
+    w[0] = v[L - 1];
+    for (int i = L - 2; i >= 0; --i) {            // w = w * q_i + v_i
+        const u64 qi = mods[i].q;
+        u64 carry = v[i];
+        for (int n = 0; n < W; ++n) {
+            const u64 lo = w[n] * qi, hi = __umul64hi(w[n], qi);
+            const u64 s = lo + carry;
+            carry = hi + (s < lo ? 1 : 0);
+            w[n] = s;
+        }
+    }
+    {                                             // w = w * t + floor(Q/2)
+        u64 carry = 0;
+        for (int n = 0; n < W; ++n) {
+            const u64 lo = w[n] * dc->t, hi = __umul64hi(w[n], dc->t);
+            u64 s = lo + carry;
+            u64 c1 = hi + (s < lo ? 1 : 0);
+            const u64 s2 = s + dc->qhalf[n];
+            c1 += (s2 < s ? 1 : 0);
+            w[n] = s2;
+            carry = c1;
+        }
+    }
+    u64 m = 0;
+    for (int b = dc->tbits - 1; b >= 0; --b) {    // quotient bits, high to low
+        const u64 *qs = dc->qshift[b];
+        int cmp = 0;
+        for (int n = W - 1; n >= 0 && cmp == 0; --n) cmp = (w[n] > qs[n]) - (w[n] < qs[n]);
+        if (cmp >= 0) {
+            u64 borrow = 0;
+            for (int n = 0; n < W; ++n) {
+                const u64 a = w[n], bq = qs[n];
+                const u64 d = a - bq - borrow;
+                borrow = (a < bq) || (a == bq && borrow) ? 1 : 0;
+                w[n] = d;
+            }
+            m |= 1ull << b;
+        }
+    }
+    pt[idx] = m % dc->t;
+}
+
+// ------------------------------------------------------------------ model weights
+// plaintext (j, k) mod t -> centred lift into q_l -> evaluation form; out [nY*K][L][2][N].
+template <int LOGN>
+__global__ void __launch_bounds__(nt_for(LOGN)) k_model_weights(const ModTab *__restrict__ mods, int L, int tmod,
+                                                                 const u64 *__restrict__ pt, u64 *out) {
+    extern __shared__ u64 sm[];
+    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    const int l = blockIdx.x % L;
+    const size_t jk = blockIdx.x / L;
+    const ModTab T = mods[l];
+    const u64 t = mods[tmod].q, th = (t - 1) / 2;
+    const u64 *src = pt + jk * N;
+    u64 *dst = out + (jk * L + l) * 2 * (size_t)N;
+    ntt_forward<LOGN, NT>(sm, T, 0, 0,
+                          [&](int p) { const u64 v = src[p]; return v <= th ? v : T.q - (t - v); },
+                          [&](int p, u64 v) { dst[p] = v; dst[N + p] = shoup_companion(v, T.q); });
+}
+
+// ------------------------------------------------------------------ dispatch helper
+
+#define DISPATCH_LOGN(c, FN)          \
+    switch ((c)->logN) {               \
+        case 12: FN(12); break;        \
+        case 13: FN(13); break;        \
+        case 14: FN(14); break;        \
+        default: return BFV_ERR_BAD_PARAMS; \
+    }
+
+int last_err() { return cudaGetLastError() == cudaSuccess ? BFV_OK : BFV_ERR_CUDA; }
+
+}  // namespace
+
+// ====================================================================== launchers
+
+int launch_ntt_limbs(const bfv_ctx *c, const u64 *in, u64 *out, size_t nct, bool forward, cudaStream_t st) {
+    const size_t nl = nct * 2 * c->L;
+    if (!nl) return BFV_OK;
+#define L_(LG)                                                                                          \
+    {                                                                                                   \
+        auto k = forward ? k_ntt_limbs<LG, true> : k_ntt_limbs<LG, false>;                              \
+        set_smem(k, smem_full<LG>());                                                                   \
+        k<<<(unsigned)nl, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->L, in, out);                  \
+    }
+    DISPATCH_LOGN(c, L_)
+#undef L_
+    count_launch(c);
+    return last_err();
+}
+
+int launch_encode(const bfv_ctx *c, const int64_t *slots, size_t count, u64 *pt, cudaStream_t st) {
+#define L_(LG)                                                                                                  \
+    {                                                                                                           \
+        set_smem(k_encode<LG>, smem_full<LG>());                                                                \
+        k_encode<LG><<<(unsigned)count, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->nqp, c->dslot, slots, pt); \
+    }
+    DISPATCH_LOGN(c, L_)
+#undef L_
+    count_launch(c);
+    return last_err();
+}
+
+int launch_decode(const bfv_ctx *c, const u64 *pt, size_t count, int64_t *slots, cudaStream_t st) {
+#define L_(LG)                                                                                                  \
+    {                                                                                                           \
+        set_smem(k_decode<LG>, smem_full<LG>());                                                                \
+        k_decode<LG><<<(unsigned)count, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->nqp, c->dslot, pt, slots); \
+    }
+    DISPATCH_LOGN(c, L_)
+#undef L_
+    count_launch(c);
+    return last_err();
+}
+
+int launch_encode_features(const bfv_ctx *c, const uint8_t *X, size_t nX, size_t f, u64 *pt, cudaStream_t st) {
+    const int K = (int)((f + c->N - 1) / c->N);
+#define L_(LG)                                                                                                 \
+    {                                                                                                          \
+        set_smem(k_encode_features<LG>, smem_full<LG>());                                                      \
+        k_encode_features<LG><<<(unsigned)(nX * K), nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->nqp, c->dslot, X, \
+                                                                                        f, K, pt);            \
+    }
+    DISPATCH_LOGN(c, L_)
+#undef L_
+    count_launch(c);
+    return last_err();
+}
+
+int launch_encode_columns(const bfv_ctx *c, const uint8_t *X, size_t nX, size_t f, u64 *pt, cudaStream_t st) {
+#define L_(LG)                                                                                                  \
+    {                                                                                                           \
+        set_smem(k_encode_columns<LG>, smem_full<LG>());                                                        \
+        k_encode_columns<LG><<<(unsigned)f, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->nqp, c->dslot, X, nX, f, pt); \
+    }
+    DISPATCH_LOGN(c, L_)
+#undef L_
+    count_launch(c);
+    return last_err();
+}
+
+int launch_keygen(const bfv_ctx *c, bfv_keys *k, u64 seed, cudaStream_t st) {
+    u64 *dgal = nullptr;
+    if (cudaMalloc(&dgal, sizeof(u64) * c->galois.size()) != cudaSuccess) return BFV_ERR_OOM;
+    cudaMemcpyAsync(dgal, c->galois.data(), sizeof(u64) * c->galois.size(), cudaMemcpyHostToDevice, st);
+    k_keygen_sk<<<(c->N + 255) / 256, 256, 0, st>>>(seed, c->N, k->sk);
+#define L_(LG)                                                                                                   \
+    {                                                                                                            \
+        set_smem(k_keygen_sk_eval<LG>, smem_full<LG>());                                                         \
+        set_smem(k_keygen_pk<LG>, smem_full<LG>());                                                              \
+        set_smem(k_keygen_galois<LG>, smem_full<LG>());                                                          \
+        k_keygen_sk_eval<LG><<<c->nqp, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, k->sk, k->sk_eval);          \
+        k_keygen_pk<LG><<<c->L, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->dcdt, c->cdt_len, seed, c->L,    \
+                                                                   k->sk_eval, k->pk_eval);                      \
+        k_keygen_galois<LG><<<(unsigned)(k->ng * c->L * c->nqp), nt_for(LG), smem_full<LG>(), st>>>(             \
+            c->dmods, c->dcdt, c->cdt_len, seed, c->L, dgal, k->sk_eval, k->gk_eval);                            \
+    }
+    int rc = BFV_OK;
+    switch (c->logN) {
+        case 12: L_(12); break;
+        case 13: L_(13); break;
+        case 14: L_(14); break;
+        default: rc = BFV_ERR_BAD_PARAMS;
+    }
+#undef L_
+    count_launch(c, 4);
+    if (!rc) rc = last_err();
+    cudaStreamSynchronize(st);
+    cudaFree(dgal);
+    return rc;
+}
+
+int launch_keys_export(const bfv_ctx *c, const bfv_keys *k, int8_t *sk, u64 *pk, u64 *gk, cudaStream_t st) {
+    if (sk && cudaMemcpyAsync(sk, k->sk, c->N, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return BFV_ERR_CUDA;
+    const unsigned npk = 2 * c->L, ngk = (unsigned)(k->ng * c->L * 2 * c->nqp);
+#define L_(LG)                                                                                           \
+    {                                                                                                    \
+        set_smem(k_intt_pairs<LG>, smem_full<LG>());                                                     \
+        if (pk) { k_intt_pairs<LG><<<npk, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->L, k->pk_eval, pk); count_launch(c); } \
+        if (gk) { k_intt_pairs<LG><<<ngk, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->nqp, k->gk_eval, gk); count_launch(c); } \
+    }
+    DISPATCH_LOGN(c, L_)
+#undef L_
+    return last_err();
+}
+
+int launch_encrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *pt, size_t count, u64 seed, uint32_t obj0, u64 *ct,
+                   void *ws, cudaStream_t st) {
+    int8_t *rnd = (int8_t *)ws;
+    const size_t total = count * c->N;
+    k_enc_sample<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(c->dcdt, c->cdt_len, seed, obj0, c->N, total, rnd);
+#define L_(LG)                                                                                                 \
+    {                                                                                                          \
+        set_smem(k_enc_main<LG>, smem_full<LG>());                                                             \
+        k_enc_main<LG><<<(unsigned)(count * 2 * c->L), nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->L, k->pk_eval, \
+                                                                                           rnd, pt, ct);       \
+    }
+    DISPATCH_LOGN(c, L_)
+#undef L_
+    count_launch(c, 2);
+    return last_err();
+}
+
+int launch_decrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *ct, size_t count, u64 *pt, void *ws, cudaStream_t st) {
+    u64 *x = (u64 *)ws;
+#define L_(LG)                                                                                              \
+    {                                                                                                       \
+        set_smem(k_dec_inner<LG>, smem_full<LG>());                                                         \
+        k_dec_inner<LG><<<(unsigned)(count * c->L), nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->L, k->sk_eval, \
+                                                                                        ct, x);             \
+    }
+    DISPATCH_LOGN(c, L_)
+#undef L_
+    const size_t total = count * c->N;
+    k_dec_round<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(c->dmods, c->ddec, x, c->N, total, pt);
+    count_launch(c, 2);
+    return last_err();
+}
+
+int launch_model_weights(const bfv_ctx *c, bfv_model *m, const u64 *w_pt, cudaStream_t st) {
+    const unsigned n = (unsigned)(m->nY * m->K * c->L);
+#define L_(LG)                                                                                           \
+    {                                                                                                    \
+        set_smem(k_model_weights<LG>, smem_full<LG>());                                                  \
+        k_model_weights<LG><<<n, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->L, c->nqp, w_pt, m->w_eval); \
+    }
+    DISPATCH_LOGN(c, L_)
+#undef L_
+    count_launch(c);
+    return last_err();
+}

@@ -1,0 +1,299 @@
+"""GPU parity: every stage of the CUDA path against the CPU oracle, bit for bit.
+
+Ciphertexts are compared in coefficient form (the boundary representation); decrypted
+scores are also compared with the closed form (x.W + b) mod t. At the full workload sizes
+the oracle computes sampled pairs, ciphertexts and coefficients one by one."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+if torch.cuda.is_available():
+    import paper_2204_05496_gb300 as bfv
+
+
+def dev(a):
+    """numpy (u)int64 array -> CUDA int64 tensor holding the same 64-bit words."""
+    a = np.ascontiguousarray(a)
+    if a.dtype == np.uint64:
+        a = a.view(np.int64)
+    return torch.from_numpy(a).cuda()
+
+
+def host(t):
+    return bfv.as_u64(t)
+
+
+# ----------------------------------------------------------------------------- tiny (N = 4096)
+
+@pytest.fixture(scope="module")
+def tiny():
+    w = synth.WORKLOADS["tiny-1"]
+    ctx = bfv.Context.from_shape(w.params)
+    keys = ctx.keygen(w.seed_keys)
+    P = oracle.Params.from_shape(w.params)
+    okeys = oracle.keygen(P, w.seed_keys)
+    return ctx, keys, P, okeys
+
+
+def test_parameters_match_oracle(tiny):
+    ctx, _, P, _ = tiny
+    assert ctx.primes == P.qs
+    assert ctx.omega == P.omega
+    assert ctx.delta_mod_q == [P.delta % q for q in P.q]
+    assert bfv.gaussian_table(16, 5) == P.cdt
+
+
+def test_keygen_parity(tiny):
+    ctx, keys, P, okeys = tiny
+    sk, pk, gk = ctx.keys_export(keys)
+    assert np.array_equal(sk.cpu().numpy(), okeys.sk)
+    assert np.array_equal(host(pk), okeys.pk)
+    assert np.array_equal(host(gk), okeys.gk_coeff)
+
+
+def test_encode_decode_parity(tiny):
+    ctx, _, P, _ = tiny
+    v = synth.slots(21, 5, P.N, P.t)
+    v[0, :7] = [-1, -P.t, 3 * P.t + 2, 0, P.t - 1, -(P.t // 2), 2 ** 40]   # any integers, taken mod t
+    pt = ctx.encode(dev(v))
+    assert np.array_equal(host(pt), oracle.encode(P, v))
+    got = ctx.decode(pt).cpu().numpy()
+    assert np.array_equal(got, np.mod(v, P.t))
+
+
+def test_encode_features_parity(tiny):
+    ctx, _, P, _ = tiny
+    X = synth.features(5, 3, 9000, 0.3)                     # f = 9000: K = 3, ragged last chunk
+    pt = ctx.encode_features(dev(X).to(torch.uint8))
+    assert pt.shape == (3, 3, P.N)
+    assert np.array_equal(host(pt), oracle.encode(P, oracle.pack_inputs(P, X).reshape(-1, P.N)).reshape(3, 3, P.N))
+    cols = ctx.encode_feature_columns(dev(X).to(torch.uint8))
+    want = np.zeros((9000, P.N), dtype=np.int64)
+    want[:, :3] = X.T
+    assert np.array_equal(host(cols)[:50], oracle.encode(P, want[:50]))
+    assert np.array_equal(host(cols)[-7:], oracle.encode(P, want[-7:]))
+
+
+def test_encrypt_parity(tiny):
+    ctx, keys, P, okeys = tiny
+    v = synth.slots(22, 6, P.N, P.t)
+    m = oracle.encode(P, v)
+    ct = ctx.encrypt(keys, dev(m), seed=777, obj0=40)
+    assert np.array_equal(host(ct), oracle.encrypt(P, okeys, m, seed=777, obj0=40))
+    assert ctx.encrypt(keys, dev(m[:0]), seed=1).numel() == 0                 # empty batch
+
+
+def test_decrypt_parity(tiny):
+    ctx, keys, P, okeys = tiny
+    v = synth.slots(23, 3, P.N, P.t)
+    ct = oracle.encrypt(P, okeys, oracle.encode(P, v), seed=5)
+    # plus a ciphertext of arbitrary residues: exact rounding must agree everywhere
+    rng = np.random.default_rng(3)
+    junk = np.stack([np.stack([rng.integers(0, q, P.N, dtype=np.uint64) for q in P.q]) for _ in range(2)])[None]
+    allct = np.concatenate([ct, junk])
+    pt = ctx.decrypt(keys, dev(allct))
+    assert np.array_equal(host(pt), oracle.decrypt(P, okeys.sk, allct))
+    assert np.array_equal(oracle.decode(P, host(pt)[:3]), v)
+
+
+@pytest.mark.parametrize("name", ["tiny-1", "tiny-16"])
+def test_packed_parity_tiny(name, tiny):
+    ctx, keys, P, okeys = tiny
+    w = synth.WORKLOADS[name]
+    X, W, b = synth.workload_inputs(w)
+    X_ct, _, Y = oracle.packed_pipeline(P, okeys, X, W, b, w.seed_enc)
+    model = ctx.model_prepare(W, b)
+    Yg = ctx.lr_scores_packed(keys, model, dev(X_ct))
+    assert np.array_equal(host(Yg), Y)
+    # ragged chunking of the pairs gives the same bits
+    Yc = ctx.lr_scores_packed(keys, model, dev(X_ct), pair_chunk=5)
+    assert np.array_equal(host(Yc), Y)
+    slots = ctx.decode(ctx.decrypt(keys, Yg)).cpu().numpy()
+    got = bfv.unpack_packed_scores(P.N, slots, X.shape[0], W.shape[1])
+    assert np.array_equal(got, oracle.expected_scores(X, W, b, P.t))
+
+
+def test_packed_pair_states_tiny(tiny):
+    ctx, keys, P, okeys = tiny
+    w = synth.WORKLOADS["tiny-16"]
+    X, W, b = synth.workload_inputs(w)
+    X_ct, W_pt, Y, pairs = oracle.packed_pipeline(P, okeys, X, W, b, w.seed_enc, return_pairs=True)
+    model = ctx.model_prepare(W, b)
+    nX = X.shape[0]
+    ws = torch.empty(ctx.packed_workspace(model, nX, 0), dtype=torch.uint8, device="cuda")
+    ctx.lr_scores_packed(keys, model, dev(X_ct), ws=ws)
+    for g in (0, 77, nX * W.shape[1] - 1):
+        got = ctx.packed_pair_from_workspace(model, nX, 0, ws, g)
+        assert np.array_equal(host(got), pairs[g])
+
+
+def test_end_to_end_on_gpu_tiny(tiny):
+    ctx, keys, P, okeys = tiny
+    w = synth.WORKLOADS["tiny-16"]
+    X, W, b = synth.workload_inputs(w)
+    pt = ctx.encode_features(dev(X).to(torch.uint8))
+    X_ct = ctx.encrypt(keys, pt.reshape(-1, P.N), seed=w.seed_enc).reshape(X.shape[0], -1, 2, P.L, P.N)
+    oX_ct, _, oY = oracle.packed_pipeline(P, okeys, X, W, b, w.seed_enc)
+    assert np.array_equal(host(X_ct), oX_ct)
+    model = ctx.model_prepare(W, b)
+    Y = ctx.lr_scores_packed(keys, model, X_ct)
+    assert np.array_equal(host(Y), oY)
+    scores = bfv.unpack_packed_scores(P.N, ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy(), X.shape[0], W.shape[1])
+    assert np.array_equal(scores, oracle.expected_scores(X, W, b, P.t))
+
+
+def test_packed_several_outputs_tiny(tiny):
+    # 520 individuals x 8 classes = 4160 pairs > N = 4096: two output ciphertexts, the second
+    # holding 64 pairs; closed form for every pair, bit-exact pairs sampled in the last chunk
+    ctx, keys, P, okeys = tiny
+    rng = np.random.default_rng(17)
+    X = (rng.random((520, 700)) < 0.05).astype(np.uint8)
+    W = rng.integers(-127, 128, (700, 8))
+    b = rng.integers(-127, 128, 8)
+    pt = ctx.encode_features(dev(X).to(torch.uint8))
+    X_ct = ctx.encrypt(keys, pt.reshape(-1, P.N), seed=9).reshape(520, 1, 2, P.L, P.N)
+    model = ctx.model_prepare(W, b)
+    chunk = 1500
+    ws = torch.empty(ctx.packed_workspace(model, 520, chunk), dtype=torch.uint8, device="cuda")
+    Y = ctx.lr_scores_packed(keys, model, X_ct, ws=ws, pair_chunk=chunk)
+    assert Y.shape[0] == 2
+    slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
+    assert np.array_equal(bfv.unpack_packed_scores(P.N, slots, 520, 8), oracle.expected_scores(X, W, b, P.t))
+    assert not slots.reshape(-1)[4160:].any()
+    W_pt = oracle.encode(P, oracle.pack_weights(P, W).reshape(-1, P.N)).reshape(8, 1, P.N)
+    xct = host(X_ct)
+    for g in (3000, 4100, 4159):
+        i, j = divmod(g, 8)
+        c = oracle.pair_rotsum(P, okeys, xct[i], W_pt[j])
+        want = oracle.pair_bias_mask(P, c, int(b[j]), g % P.N)
+        assert np.array_equal(host(ctx.packed_pair_from_workspace(model, 520, chunk, ws, g)), want)
+
+
+def test_standard_parity_tiny(tiny):
+    ctx, keys, P, okeys = tiny
+    w = synth.WORKLOADS["tiny-16"]
+    X, W, b = synth.workload_inputs(w)
+    cols = ctx.encode_feature_columns(dev(X).to(torch.uint8))
+    X_ct = ctx.encrypt(keys, cols, seed=w.seed_enc)
+    model = ctx.model_prepare(W, b)
+    Y = ctx.lr_scores_standard(model, X_ct, X.shape[0])
+    oY = oracle.lr_standard(P, host(X_ct), W, b)
+    assert np.array_equal(host(Y), oY)
+    slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
+    assert np.array_equal(slots[:, :X.shape[0]].T, oracle.expected_scores(X, W, b, P.t))
+    # the encryption of a few feature columns matches the oracle
+    want = np.zeros((3, P.N), dtype=np.int64)
+    want[:, :X.shape[0]] = X[:, [0, 500, 999]].T
+    oc = oracle.encrypt(P, okeys, oracle.encode(P, want[0:1]), seed=w.seed_enc, obj0=0)
+    assert np.array_equal(host(X_ct[0:1]), oc)
+    oc = oracle.encrypt(P, okeys, oracle.encode(P, want[2:3]), seed=w.seed_enc, obj0=999)
+    assert np.array_equal(host(X_ct[999:1000]), oc)
+
+
+def test_invalid_arguments_are_rejected(tiny):
+    ctx, keys, P, _ = tiny
+    with pytest.raises(bfv.BfvError):
+        bfv.Context(5000, 3, 36, 65537)                      # N not supported
+    model = ctx.model_prepare(np.ones((10, 2), dtype=np.int64), np.zeros(2, dtype=np.int64))
+    X_ct = torch.zeros((1, 1, 2, P.L, P.N), dtype=torch.int64, device="cuda")
+    tiny_ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(bfv.BfvError) as e:
+        bfv._call("bfv_lr_scores_packed", ctx.handle, keys.handle, model.handle, bfv._ptr(X_ct), 1,
+                  bfv._ptr(X_ct), bfv._ptr(tiny_ws), 16, 0, 0)
+    assert e.value.code == bfv.BFV_ERR_OVER_BUDGET
+    with pytest.raises(bfv.BfvError):
+        ctx.lr_scores_standard(model, X_ct[0, 0], P.N + 1)   # more individuals than slots
+
+
+# ----------------------------------------------------------------------------- paper scale (N = 16384, L = 7)
+
+@pytest.fixture(scope="module")
+def paper():
+    w = synth.WORKLOADS["single-40k"]
+    ctx = bfv.Context.from_shape(w.params)
+    keys = ctx.keygen(w.seed_keys)
+    P = oracle.Params.from_shape(w.params)
+    okeys = oracle.keygen(P, w.seed_keys)
+    return ctx, keys, P, okeys
+
+
+def test_paper_keys_match(paper):
+    ctx, keys, P, okeys = paper
+    sk, pk, gk = ctx.keys_export(keys)
+    assert ctx.primes == P.qs
+    assert np.array_equal(sk.cpu().numpy(), okeys.sk)
+    assert np.array_equal(host(pk), okeys.pk)
+    assert np.array_equal(host(gk), okeys.gk_coeff)
+
+
+def test_single_individual_packed_bit_exact(paper):
+    ctx, keys, P, okeys = paper
+    w = synth.WORKLOADS["single-40k"]
+    X, W, b = synth.workload_inputs(w)
+    pt = ctx.encode_features(dev(X).to(torch.uint8))
+    X_ct = ctx.encrypt(keys, pt.reshape(-1, P.N), seed=w.seed_enc).reshape(1, 3, 2, P.L, P.N)
+    oX_ct, _, oY = oracle.packed_pipeline(P, okeys, X, W, b, w.seed_enc)
+    assert np.array_equal(host(X_ct), oX_ct)
+    model = ctx.model_prepare(W, b)
+    Y = ctx.lr_scores_packed(keys, model, X_ct)
+    assert np.array_equal(host(Y), oY)
+    scores = bfv.unpack_packed_scores(P.N, ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy(), 1, 16)
+    assert np.array_equal(scores, oracle.expected_scores(X, W, b, P.t))
+
+
+def test_batch512_packed_full_size(paper):
+    """The benchmark's workload and launch configuration: 512 individuals x 40,000 features x 16
+    classes. Every score against the closed form; sampled pairs bit-exact against the oracle."""
+    ctx, keys, P, okeys = paper
+    w = synth.WORKLOADS["batch512-40k"]
+    X, W, b = synth.workload_inputs(w)
+    pt = ctx.encode_features(dev(X).to(torch.uint8))
+    X_ct = ctx.encrypt(keys, pt.reshape(-1, P.N), seed=w.seed_enc).reshape(512, 3, 2, P.L, P.N)
+    model = ctx.model_prepare(W, b)
+    ws = torch.empty(ctx.packed_workspace(model, 512, 0), dtype=torch.uint8, device="cuda")
+    Y = ctx.lr_scores_packed(keys, model, X_ct, ws=ws)
+    assert Y.shape[0] == 1
+    scores = bfv.unpack_packed_scores(P.N, ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy(), 512, 16)
+    assert np.array_equal(scores, oracle.expected_scores(X, W, b, P.t))
+    W_pt = oracle.encode(P, oracle.pack_weights(P, W).reshape(-1, P.N)).reshape(16, 3, P.N)
+    for g in (6144, 7001, 8191):                      # pairs of the last chunk of 2048
+        i, j = divmod(g, 16)
+        xo = oracle.encrypt(P, okeys, oracle.encode(P, oracle.pack_inputs(P, X[i:i + 1])[0]), seed=w.seed_enc,
+                            obj0=3 * i)
+        assert np.array_equal(host(X_ct[i]), xo)
+        c = oracle.pair_rotsum(P, okeys, xo, W_pt[j])
+        want = oracle.pair_bias_mask(P, c, int(b[j]), g % P.N)
+        assert np.array_equal(host(ctx.packed_pair_from_workspace(model, 512, 0, ws, g)), want)
+
+
+def test_single_individual_standard_full_size(paper):
+    """Standard product at 40,000 features (40,000 ciphertexts, 73 GB): closed form for the
+    decrypted scores, sampled output coefficients and sampled input ciphertexts bit-exact."""
+    ctx, keys, P, okeys = paper
+    w = synth.WORKLOADS["single-40k"]
+    X, W, b = synth.workload_inputs(w)
+    cols = ctx.encode_feature_columns(dev(X).to(torch.uint8))
+    X_ct = torch.empty((40000, 2, P.L, P.N), dtype=torch.int64, device="cuda")
+    ws = torch.empty(ctx.encrypt_workspace(4000), dtype=torch.uint8, device="cuda")
+    for f0 in range(0, 40000, 4000):
+        ctx.encrypt(keys, cols[f0:f0 + 4000], seed=w.seed_enc, obj0=f0, out=X_ct[f0:f0 + 4000], ws=ws)
+    model = ctx.model_prepare(W, b)
+    Y = ctx.lr_scores_standard(model, X_ct, 1)
+    slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
+    assert np.array_equal(slots[:, 0], oracle.expected_scores(X, W, b, P.t)[0])
+    for f in (0, 23456, 39999):
+        want = np.zeros((1, P.N), dtype=np.int64)
+        want[0, 0] = X[0, f]
+        assert np.array_equal(host(X_ct[f:f + 1]), oracle.encrypt(P, okeys, oracle.encode(P, want), seed=w.seed_enc, obj0=f))
+    Yh = host(Y)
+    for (j, c, l, k) in [(0, 0, 0, 0), (5, 1, 6, 16383), (15, 0, 3, 777)]:
+        xs = host(X_ct[:, c, l, k])
+        v = oracle.standard_coeff(W[:, j], xs, P.q[l])
+        if c == 0 and k == 0:
+            v = (v + P.delta % P.q[l] * (int(b[j]) % P.t)) % P.q[l]
+        assert int(Yh[j, c, l, k]) == v

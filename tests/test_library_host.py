@@ -1,0 +1,79 @@
+"""CPU-side checks of the CUDA library: it builds, loads, exports every function declared in
+include/bfv_lr.h, and its host-side parameter logic agrees with the oracle's independent
+computation. No GPU compute is called here."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import oracle
+import synth
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+@pytest.fixture(scope="module")
+def bfv():
+    import paper_2204_05496_gb300 as m
+    m.build()
+    return m
+
+
+def declared_functions():
+    src = open(os.path.join(ROOT, "include", "bfv_lr.h")).read()
+    return sorted(set(re.findall(r"^int\s+(bfv_\w+)\s*\(", src, flags=re.M)))
+
+
+def test_library_exports_every_declared_function(bfv):
+    names = declared_functions()
+    assert len(names) >= 20
+    lib = ctypes.CDLL(bfv.LIB_PATH)
+    for n in names:
+        assert hasattr(lib, n), n
+    assert set(names) == set(bfv.SIGNATURES)
+    assert bfv.lib().bfv_abi_version() == 1
+
+
+@pytest.mark.parametrize("shape", [synth.TINY, synth.PAPER16K])
+def test_host_prime_rule_matches_oracle(bfv, shape):
+    assert bfv.primes(shape.N, shape.L, shape.prime_bits, shape.t) == oracle.ntt_primes(shape.prime_bits, shape.N, shape.L + 1)
+
+
+@pytest.mark.parametrize("num,den", [(16, 5), (8, 5), (3, 1)])
+def test_host_gaussian_table_matches_oracle(bfv, num, den):
+    # the library computes exp() in 120-bit binary fixed point, the oracle with 90-digit decimals
+    assert bfv.gaussian_table(num, den) == oracle.gaussian_cdt(num, den)
+
+
+def test_bad_parameters_rejected_on_host(bfv):
+    p = bfv.Params(4096, 3, 36, 0, 65539, 16, 5)       # t = 65539 is not 1 mod 8192
+    out = (ctypes.c_uint64 * 8)()
+    assert bfv.lib().bfv_params_primes(ctypes.byref(p), ctypes.cast(out, ctypes.c_void_p)) == bfv.BFV_ERR_INVALID_ARG
+    p = bfv.Params(3000, 3, 36, 0, 65537, 16, 5)
+    assert bfv.lib().bfv_params_primes(ctypes.byref(p), ctypes.cast(out, ctypes.c_void_p)) == bfv.BFV_ERR_INVALID_ARG
+
+
+def test_setup_without_gpu_fails_loudly(bfv):
+    import torch
+    if torch.cuda.is_available():
+        pytest.skip("a GPU is present")
+    p = bfv.Params(4096, 3, 36, 0, 65537, 16, 5)
+    h = ctypes.c_void_p()
+    rc = bfv.lib().bfv_setup(ctypes.byref(p), ctypes.byref(h))
+    assert rc != bfv.BFV_OK and not h.value
+    with pytest.raises(RuntimeError):
+        bfv.Context(4096, 3, 36, 65537)
+
+
+def test_product_code_never_touches_the_oracle():
+    pkg = os.path.join(ROOT, "paper_2204_05496_gb300")
+    for dirpath, _, files in os.walk(pkg):
+        if "_build" in dirpath:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".cpp")):
+                src = open(os.path.join(dirpath, f)).read()
+                assert not re.search(r"\boracle\b", src), f
+    for f in ("bfv_lr.h",):
+        assert "oracle" not in open(os.path.join(ROOT, "include", f)).read()
