@@ -1,0 +1,557 @@
+#!/usr/bin/env python
+"""Benchmark: encrypted logistic-regression predictions per second on GB300.
+
+Workload (the headline configuration): BFV ring degree N = 16384, seven 54-bit ciphertext
+primes plus one 54-bit key-switching prime, t = 786433; 512 individuals x 40,000 binary
+features (Bernoulli 0.02) x 16 classes, int8-range integer weights and biases; synthetic,
+seeded inputs. One step = one pass of the whole private inference protocol over the batch
+(Section 4.2.2): pack+encode the features, encrypt them (1,536 ciphertexts), the packed
+product of Algorithm 1 (8,192 pairs, 14 key-switched rotations each), decrypt, decode.
+
+value     : predictions/s with the features resident in device memory (CUDA events per step,
+            L2 flushed between steps; max over ranks under torchrun).
+e2e       : the same through the C ABI with HOST buffers (bfv_lr_predict_packed_host:
+            pinned features copied in, scores copied out, inside the timed call).
+roofline  : the dominant kernel's algorithmic 64-bit modular multiplications per launch over
+            its live CUDA-event launch time, against the integer-pipe peak.
+Also reported: 1-individual latency (p50/p99), the server product alone, the standard
+per-element product at the same parameters, per-kernel time shares, and the CPU oracle on a
+bounded sample (cpu_baseline). `--impl reference` times the CPU oracle itself.
+"""
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "encrypted predictions/s @40k features, batch 512; 1-individual p50 latency"
+UNIT = "predictions/s"
+WORKLOAD = "batch512-40k"
+LATENCY_WORKLOAD = "single-40k"
+
+# Integer-pipe peak for 64-bit modular multiplication (derivation in the design doc): 152 SMs x
+# 64 32-bit multiply-adds per clock per SM x 2.07 GHz, 15 32-bit half-products per Shoup
+# product (7 for the high 64 bits of x*w', 4 + 4 for the low 64 bits of x*w and q^*q).
+SMS, IMAD_PER_CLK_SM, SM_MAX_HZ, IMAD_PER_MODMUL = 152, 64, 2.07e9, 15
+ALU_PEAK_GMODMUL = SMS * IMAD_PER_CLK_SM * SM_MAX_HZ / IMAD_PER_MODMUL / 1e9
+HBM_FALLBACK_GBS = 6800.0
+
+
+def parse_args(argv=None):
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", choices=["gb300", "reference"], default="gb300")
+    p.add_argument("--pair-chunk", type=int, default=0)
+    p.add_argument("--latency-reps", type=int, default=20)
+    p.add_argument("--no-standard", action="store_true")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--only-packed", action="store_true",
+                   help="profiling case: time only the packed product on --individuals of the batch")
+    p.add_argument("--individuals", type=int, default=512)
+    return p.parse_args(argv)
+
+
+# ----------------------------------------------------------------------------- host helpers
+
+def measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
+
+
+def modmuls_per_pair(kind, N, L, K):
+    """Algorithmic 64-bit modular multiplications per pair (one rotation step for the key
+    switching kinds). B = butterflies of one length-N NTT."""
+    B = (N // 2) * int(round(np.log2(N)))
+    return {
+        "ks_modup": L * L * B + 2 * L * (L + 1) * N,       # L^2 digit NTTs + key inner product
+        "ks_prep": L * B,                                   # inverse NTT of the L digits
+        "ks_moddown_p": 2 * B,                              # inverse NTT of the two P limbs
+        "ks_moddown": 2 * L * B + 2 * L * N,                # NTT of the corrections + P^-1 product
+        "mac": 2 * L * K * N,
+        "bias_mask": L * B + 2 * L * N,
+    }[kind]
+
+
+def source_hash(*paths):
+    h = hashlib.sha256()
+    for p in paths:
+        with open(os.path.join(ROOT, p), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic(kernel):
+    """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
+    path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.md")
+    try:
+        txt = open(path).read()
+    except OSError:
+        return None
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    h = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
+    if not m or not h:
+        return None
+    cur = source_hash("paper_2204_05496_gb300/csrc/k_packed.cu", "paper_2204_05496_gb300/csrc/bfv_device.cuh")
+    return float(m.group(1)) if h.group(1) == cur else None
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled every 200 ms during the timed region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, uuid=None):
+        self.uuid = uuid
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        fd, self.path = tempfile.mkstemp(prefix="clocks", suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.uuid:
+            cmd.insert(1, f"--id={self.uuid}")
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for n, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(n)
+        os.unlink(self.path)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def aggregate(per_rank_ms, units_per_rank):
+    """Whole-job throughput from per-rank step times: every rank processes its own batch;
+    the job takes as long as the slowest rank (max over ranks)."""
+    slow = max(per_rank_ms)
+    return units_per_rank * len(per_rank_ms) / (slow / 1e3), slow
+
+
+# ----------------------------------------------------------------------------- CPU oracle (baseline / reference)
+
+def oracle_sample(n_individuals, steps=1, warmup=0):
+    """The CPU oracle, as it stands, on `n_individuals` of the headline batch: encode, encrypt,
+    Algorithm 1, decrypt, decode. Returns (predictions/s, cores, seconds per step)."""
+    import oracle
+    w = synth.WORKLOADS[WORKLOAD]
+    X, W, b = synth.workload_inputs(w)
+    P = oracle.Params.from_shape(w.params)
+    keys = oracle.keygen(P, w.seed_keys)
+    W_pt = oracle.encode(P, oracle.pack_weights(P, W).reshape(-1, P.N)).reshape(W.shape[1], -1, P.N)
+    times = []
+    for s in range(warmup + steps):
+        i0 = (s * n_individuals) % X.shape[0]
+        Xs = X[i0:i0 + n_individuals]
+        t0 = time.perf_counter()
+        pt = oracle.encode(P, oracle.pack_inputs(P, Xs).reshape(-1, P.N))
+        ct = oracle.encrypt(P, keys, pt, w.seed_enc, obj0=3 * i0).reshape(len(Xs), -1, 2, P.L, P.N)
+        Y = oracle.lr_packed(P, keys, ct, W_pt, b)
+        slots = oracle.decode(P, oracle.decrypt(P, keys.sk, Y))
+        dt = time.perf_counter() - t0
+        got = oracle.unpack_packed_scores(P, slots, len(Xs), W.shape[1])
+        assert np.array_equal(got, oracle.expected_scores(Xs, W, b, P.t))
+        if s >= warmup:
+            times.append(dt)
+    sec = sum(times) / len(times)
+    return n_individuals / sec, P.nthreads, sec
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return 0
+    sample = 1
+    v, cores, sec = oracle_sample(sample, steps=args.steps, warmup=args.warmup)
+    line = {
+        "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "u64", "data": "synthetic",
+        "config": config_block(args, chunk=None),
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": f"{sample} individual (16 pairs) of the 512-individual batch per step"},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def config_block(args, chunk):
+    w = synth.WORKLOADS[WORKLOAD]
+    return {
+        "workload": (f"{WORKLOAD}: BFV N={w.params.N}, L={w.params.L} x {w.params.prime_bits}-bit primes + 1 "
+                     f"special prime, t={w.params.t}; {w.n_individuals} individuals x {w.n_features} "
+                     f"Bernoulli({w.p_feature}) binary features x {w.n_classes} classes, int8-range weights"),
+        "global_batch": w.n_individuals * max(1, args.gpus),
+        "individuals_per_gpu": w.n_individuals,
+        "features": w.n_features,
+        "classes": w.n_classes,
+        "pair_chunk": chunk,
+        "l2": "flushed (256 MB write) between timed steps; per-step working set ~15 GB >> 129 MB L2",
+        "parallelism": f"independent replicas x{max(1, args.gpus)}",
+    }
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+
+    rank, world = int(os.environ.get("RANK", "0")), int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    import paper_2204_05496_gb300 as bfv
+    bfv.build()
+
+    w = synth.WORKLOADS[WORKLOAD]
+    X, W, b = synth.workload_inputs(w)
+    nX, nY = X.shape[0], W.shape[1]
+    ctx = bfv.Context.from_shape(w.params)
+    keys = ctx.keygen(w.seed_keys)
+    model = ctx.model_prepare(W, b)
+    chunk = args.pair_chunk
+    Xd = torch.from_numpy(X).to(dev)
+    ws = torch.empty(ctx.predict_workspace(model, nX, chunk), dtype=torch.uint8, device=dev)
+    scores = torch.empty((nX, nY), dtype=torch.int64, device=dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    want = (X.astype(np.int64) @ W + b[None, :]) % w.params.t
+
+    def step(i):
+        ctx.predict_packed(keys, model, Xd, seed=w.seed_enc + i, out=scores, ws=ws, pair_chunk=chunk)
+
+    for i in range(args.warmup):
+        step(i)
+    torch.cuda.synchronize()
+    if not np.array_equal(scores.cpu().numpy(), want):
+        raise SystemExit("benchmarked path produced wrong scores")
+
+    uuid = None
+    try:
+        u = torch.cuda.get_device_properties(dev).uuid
+        uuid = f"GPU-{u}" if u and not str(u).startswith("GPU-") else str(u)
+    except Exception:
+        uuid = None
+    sampler = ClockSampler(uuid)
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    launches0 = ctx.launch_count()
+    sampler.start()
+    ctx.profile(True)
+    ctx.profile_read()
+    evs = []
+    t0 = time.perf_counter()
+    for i in range(args.steps):
+        flush.zero_()
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        step(args.warmup + i)
+        z.record()
+        evs.append((a, z))
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    ctx.profile(False)
+    kern = ctx.profile_read()
+    clocks = sampler.stop()
+    gpu_launches = ctx.launch_count() - launches0
+    step_ms = sum(a.elapsed_time(z) for a, z in evs) / args.steps
+    if world > 1:
+        t = torch.tensor([step_ms], device=dev)
+        allt = [torch.zeros_like(t) for _ in range(world)]
+        dist.all_gather(allt, t)
+        per_rank = [float(x.item()) for x in allt]
+        dist.barrier()
+    else:
+        per_rank = [step_ms]
+    value, slow_ms = aggregate(per_rank, nX)
+    if not np.array_equal(scores.cpu().numpy(), want):
+        raise SystemExit("benchmarked path produced wrong scores")
+
+    extras = {}
+    if rank == 0:
+        extras = gpu_extras(args, ctx, keys, model, X, W, b, ws, chunk, dev, kern, step_ms)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+    if rank != 0:
+        return 0
+
+    line = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": slow_ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded; stands in for iDASH/TCGA)",
+        "config": config_block(args, chunk),
+        "clocks": clocks,
+        "gpu_launches": gpu_launches,
+        "wall_s_timed_region": wall,
+    }
+    line.update(extras)
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def gpu_extras(args, ctx, keys, model, X, W, b, ws, chunk, dev, kern, step_ms):
+    import torch
+    w = synth.WORKLOADS[WORKLOAD]
+    N, L, K = w.params.N, w.params.L, model.K
+    nX, nY = X.shape[0], model.nY
+    out = {}
+
+    # per-kernel shares over the timed steps and the dominant kernel's roofline
+    total = sum(ms for _, ms in kern.values()) or 1.0
+    pairs = nX * nY
+    plan_chunk = chunk if chunk else min(pairs, 2048)
+    rot = int(round(np.log2(N)))
+    shares = {}
+    work = {}
+    for name, (n, ms) in kern.items():
+        if n == 0:
+            continue
+        d = {"launches": n, "ms_total": round(ms, 3), "share": round(ms / total, 4)}
+        if name in ("ks_modup", "ks_prep", "ks_moddown_p", "ks_moddown", "mac", "bias_mask"):
+            work[name] = modmuls_per_pair(name, N, L, K) * pairs * (rot if name.startswith("ks_") else 1) * args.steps
+            d["gmodmul_per_s"] = round(work[name] / (ms / 1e3) / 1e9, 1)
+        shares[name] = d
+    out["kernels"] = shares
+    top = max(shares, key=lambda k: shares[k]["ms_total"])
+    n, ms = kern[top]
+    if top in work:
+        per_launch = work[top] / n
+        achieved = per_launch / (ms / n / 1e3) / 1e9
+        out["roofline"] = {"kernel": top, "bound": "alu", "achieved": round(achieved, 1),
+                           "peak": round(ALU_PEAK_GMODMUL, 1), "unit": "Gmodmul/s",
+                           "frac": round(achieved / ALU_PEAK_GMODMUL, 4), "traffic": recorded_traffic(top),
+                           "work_per_launch": f"{per_launch:.4g} 64-bit modular multiplications "
+                                              f"({plan_chunk} pairs x one key switch)",
+                           "peak_basis": "152 SMs x 64 IMAD/clk x 2.07 GHz / 15 32-bit half-products per Shoup product"}
+
+    # server product alone (inputs already encrypted)
+    pt = ctx.encode_features(torch.from_numpy(X).to(dev))
+    X_ct = ctx.encrypt(keys, pt.reshape(-1, N), seed=w.seed_enc).reshape(nX, K, 2, L, N)
+    pws = torch.empty(ctx.packed_workspace(model, nX, chunk), dtype=torch.uint8, device=dev)
+    Y = ctx.lr_scores_packed(keys, model, X_ct, ws=pws, pair_chunk=chunk)
+    torch.cuda.synchronize()
+    reps = 2
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(reps):
+        ctx.lr_scores_packed(keys, model, X_ct, out=Y, ws=pws, pair_chunk=chunk)
+    z.record()
+    torch.cuda.synchronize()
+    sms = a.elapsed_time(z) / reps
+    out["server_only"] = {"ms": round(sms, 2), "predictions_per_s": round(nX / (sms / 1e3), 1)}
+    del pws, Y, X_ct, pt
+
+    # end to end through the C ABI with host buffers
+    Xh = torch.from_numpy(X).pin_memory()
+    sh = torch.empty((nX, nY), dtype=torch.int64).pin_memory()
+    e2e_t = []
+    for i in range(max(2, args.steps)):
+        t0 = time.perf_counter()
+        ctx.predict_packed_host(keys, model, Xh, seed=w.seed_enc + i, out=sh, ws=ws, pair_chunk=chunk)
+        e2e_t.append(time.perf_counter() - t0)
+    e2e_s = statistics.mean(e2e_t[1:]) if len(e2e_t) > 1 else e2e_t[0]
+    out["e2e"] = {"value": round(nX / e2e_s, 2), "unit": UNIT, "h2d_bytes_per_step": int(X.nbytes),
+                  "d2h_bytes_per_step": int(nX * nY * 8), "ms_per_step": round(e2e_s * 1e3, 2)}
+
+    # one individual: latency of the whole protocol (the metric's second half)
+    lw = synth.WORKLOADS[LATENCY_WORKLOAD]
+    X1, W1, b1 = synth.workload_inputs(lw)
+    k1 = ctx.keygen(lw.seed_keys)
+    m1 = ctx.model_prepare(W1, b1)
+    X1d = torch.from_numpy(X1).to(dev)
+    ws1 = torch.empty(ctx.predict_workspace(m1, 1, 0), dtype=torch.uint8, device=dev)
+    s1 = torch.empty((1, W1.shape[1]), dtype=torch.int64, device=dev)
+    lat = []
+    for i in range(3 + args.latency_reps):
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        ctx.predict_packed(k1, m1, X1d, seed=lw.seed_enc + i, out=s1, ws=ws1)
+        z.record()
+        torch.cuda.synchronize()
+        if i >= 3:
+            lat.append(a.elapsed_time(z))
+    want1 = (X1.astype(np.int64) @ W1 + b1[None, :]) % lw.params.t
+    assert np.array_equal(s1.cpu().numpy(), want1)
+    X1h = torch.from_numpy(X1).pin_memory()
+    s1h = torch.empty((1, W1.shape[1]), dtype=torch.int64).pin_memory()
+    lat_e2e = []
+    for i in range(3 + args.latency_reps):
+        t0 = time.perf_counter()
+        ctx.predict_packed_host(k1, m1, X1h, seed=lw.seed_enc + i, out=s1h, ws=ws1)
+        if i >= 3:
+            lat_e2e.append((time.perf_counter() - t0) * 1e3)
+    lat.sort()
+    lat_e2e.sort()
+    out["latency_1_individual"] = {
+        "p50_ms": round(lat[len(lat) // 2], 3), "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
+        "e2e_p50_ms": round(lat_e2e[len(lat_e2e) // 2], 3), "reps": len(lat),
+        "workload": f"{LATENCY_WORKLOAD}: 1 individual x {lw.n_features} features x {lw.n_classes} classes, same BFV parameters"}
+    del ws1
+
+    if not args.no_standard:
+        out["standard"] = standard_leg(args, ctx, keys, model, X, W, b, dev, step_ms, lat[len(lat) // 2])
+    if not args.no_cpu_baseline and int(os.environ.get("WORLD_SIZE", "1")) == 1:
+        v, cores, sec = oracle_sample(4)
+        out["cpu_baseline"] = {"value": round(v, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
+                               "sample": "4 individuals (64 pairs) of the 512-individual batch, whole protocol "
+                                         f"({sec:.1f} s)"}
+    return out
+
+
+def standard_leg(args, ctx, keys, model, X, W, b, dev, packed_step_ms, packed_lat_ms):
+    """The standard per-element product at the same parameters (Section 5.2.3): encode the
+    40,000 feature columns, encrypt them (73 GB), scalar-weighted sums, decrypt |Y| outputs."""
+    import torch
+    w = synth.WORKLOADS[WORKLOAD]
+    N, L = w.params.N, w.params.L
+    nX, f = X.shape
+    nY = model.nY
+    Xd = torch.from_numpy(X).to(dev)
+    X_ct = torch.empty((f, 2, L, N), dtype=torch.int64, device=dev)
+    blk = 4000
+    ews = torch.empty(ctx.encrypt_workspace(blk), dtype=torch.uint8, device=dev)
+    Y = torch.empty((nY, 2, L, N), dtype=torch.int64, device=dev)
+
+    def run(seed):
+        cols = ctx.encode_feature_columns(Xd)
+        for f0 in range(0, f, blk):
+            ctx.encrypt(keys, cols[f0:f0 + blk], seed=seed, obj0=f0, out=X_ct[f0:f0 + blk], ws=ews)
+        del cols
+        ctx.lr_scores_standard(model, X_ct, nX, out=Y)
+        return ctx.decode(ctx.decrypt(keys, Y))
+
+    slots = run(1)
+    torch.cuda.synchronize()
+    want = (X.astype(np.int64) @ W + b[None, :]) % w.params.t
+    if not np.array_equal(slots.cpu().numpy()[:, :nX].T, want):
+        raise SystemExit("standard product produced wrong scores")
+    ctx.profile(True)
+    ctx.profile_read()
+    times = []
+    for i in range(max(2, min(3, args.steps))):
+        a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        run(2 + i)
+        z.record()
+        torch.cuda.synchronize()
+        times.append(a.elapsed_time(z))
+    ctx.profile(False)
+    kern = ctx.profile_read()
+    ms = statistics.mean(times)
+    n, kms = kern["standard"]
+    bytes_per_launch = f * 2 * L * N * 8 + nY * 2 * L * N * 8
+    peaks = measured_peaks()
+    hbm = peaks.get("hbm_gbs", HBM_FALLBACK_GBS)
+    gbs = bytes_per_launch / (kms / n / 1e3) / 1e9
+    res = {
+        "ms_per_batch": round(ms, 2), "predictions_per_s_batch512": round(nX / (ms / 1e3), 2),
+        "latency_1_individual_ms": round(ms, 2),
+        "note": "cost is independent of the batch size up to N = 16384 individuals",
+        "product_kernel_ms": round(kms / n, 2),
+        "product_roofline": {"bound": "hbm", "achieved": round(gbs, 1), "peak": hbm, "unit": "GB/s",
+                             "frac": round(gbs / hbm, 4),
+                             "traffic_algorithmic_bytes": bytes_per_launch,
+                             "peak_basis": "measured" if "hbm_gbs" in peaks else "fallback"},
+        "packed_speedup_batch512": round(ms / packed_step_ms, 2),
+        "packed_speedup_1_individual": round(ms / packed_lat_ms, 1),
+        "encrypt_ms": round(kern["encrypt"][1] / max(1, len(times)), 2),
+    }
+    del X_ct, ews
+    torch.cuda.empty_cache()
+    return res
+
+
+def run_only_packed(args):
+    """Small profiling case: the packed product alone on the first --individuals of the batch
+    (same parameters, same kernels, fewer pairs), --warmup untimed then --steps timed calls."""
+    import torch
+    import paper_2204_05496_gb300 as bfv
+    bfv.build()
+    torch.cuda.set_device(0)
+    w = synth.WORKLOADS[WORKLOAD]
+    X, W, b = synth.workload_inputs(w)
+    X = X[:args.individuals]
+    N, L = w.params.N, w.params.L
+    ctx = bfv.Context.from_shape(w.params)
+    keys = ctx.keygen(w.seed_keys)
+    model = ctx.model_prepare(W, b)
+    pt = ctx.encode_features(torch.from_numpy(X).cuda())
+    X_ct = ctx.encrypt(keys, pt.reshape(-1, N), seed=w.seed_enc).reshape(len(X), model.K, 2, L, N)
+    ws = torch.empty(ctx.packed_workspace(model, len(X), args.pair_chunk), dtype=torch.uint8, device="cuda")
+    Y = ctx.lr_scores_packed(keys, model, X_ct, ws=ws, pair_chunk=args.pair_chunk)
+    for _ in range(args.warmup - 1):
+        ctx.lr_scores_packed(keys, model, X_ct, out=Y, ws=ws, pair_chunk=args.pair_chunk)
+    torch.cuda.synchronize()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        ctx.lr_scores_packed(keys, model, X_ct, out=Y, ws=ws, pair_chunk=args.pair_chunk)
+    z.record()
+    torch.cuda.synchronize()
+    slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
+    got = bfv.unpack_packed_scores(N, slots, len(X), W.shape[1])
+    ok = bool(np.array_equal(got, (X.astype(np.int64) @ W + b[None, :]) % w.params.t))
+    print(json.dumps({"case": "only-packed", "individuals": len(X), "pair_chunk": args.pair_chunk,
+                      "ms_per_call": a.elapsed_time(z) / args.steps, "correct": ok}), flush=True)
+    return 0 if ok else 1
+
+
+def main(argv=None):
+    args = parse_args(argv)
+    if args.impl == "reference":
+        return run_reference(args)
+    if args.only_packed:
+        return run_only_packed(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -165,6 +165,26 @@ int bfv_lr_scores_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *mo
 int bfv_lr_scores_standard(bfv_ctx *ctx, const bfv_model *model, const uint64_t *X_ct, size_t nX,
                            uint64_t *Y_ct, uintptr_t stream);
 
+/* ------------------------------------------------------------------ whole-protocol calls */
+
+/* One pass of the private inference protocol (Section 4.2.2, Fig. 2) over a batch, all on
+ * the device: bfv_encode_features -> bfv_encrypt (seed, object ids 0 .. nX*ceil(f/N)-1) ->
+ * bfv_lr_scores_packed -> bfv_decrypt -> bfv_decode, leaving score(i, j) = (x_i . W[:, j] +
+ * b_j) mod t at scores[i*nY + j]. X: uint8[nX][f] (device), scores: int64[nX][nY] (device).
+ * ws: at least bfv_lr_predict_packed_workspace(nX, pair_chunk) bytes. */
+int bfv_lr_predict_packed_workspace(const bfv_ctx *ctx, const bfv_model *model, size_t nX, size_t pair_chunk,
+                                    size_t *bytes);
+int bfv_lr_predict_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint8_t *X, size_t nX,
+                          uint64_t seed, int64_t *scores, void *ws, size_t ws_bytes, size_t pair_chunk,
+                          uintptr_t stream);
+
+/* The same with HOST buffers: copies X_host (uint8[nX][f]; pinned memory gives full copy speed)
+ * to the device inside the call, runs bfv_lr_predict_packed, copies the scores back to
+ * scores_host (int64[nX][nY]) and synchronises `stream`. Same workspace size. */
+int bfv_lr_predict_packed_host(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint8_t *X_host,
+                               size_t nX, uint64_t seed, int64_t *scores_host, void *ws, size_t ws_bytes,
+                               size_t pair_chunk, uintptr_t stream);
+
 /* ------------------------------------------------------------------ diagnostics */
 
 /* Copies pair g's ciphertext out of a packed-product workspace, in coefficient form
@@ -175,6 +195,27 @@ int bfv_lr_packed_pair_from_workspace(bfv_ctx *ctx, const bfv_model *model, size
 
 /* Number of kernel launches the library issued since bfv_setup (for launch accounting). */
 int bfv_launch_count(const bfv_ctx *ctx, uint64_t *count);
+
+/* Per-kernel timing with CUDA events recorded around every launch of the library's kernels on
+ * the launching stream (enable = 1 starts recording, 0 stops). bfv_profile_read synchronises
+ * the recorded events and returns, for kernel kind `kind` (BFV_K_*), the number of launches
+ * and their summed device time in milliseconds since the last read of that kind, then clears
+ * it. Recording adds two event records per launch. */
+#define BFV_K_NTT 0
+#define BFV_K_KS_PREP 1
+#define BFV_K_KS_MODUP 2
+#define BFV_K_KS_MODDOWN_P 3
+#define BFV_K_KS_MODDOWN 4
+#define BFV_K_MAC 5
+#define BFV_K_BIAS_MASK 6
+#define BFV_K_COMPRESS 7
+#define BFV_K_ENCRYPT 8
+#define BFV_K_DECRYPT 9
+#define BFV_K_ENCODE 10
+#define BFV_K_STANDARD 11
+#define BFV_K_COUNT 12
+int bfv_profile(bfv_ctx *ctx, int enable);
+int bfv_profile_read(bfv_ctx *ctx, int kind, uint64_t *launches, double *total_ms);
 
 #ifdef __cplusplus
 }

@@ -113,7 +113,16 @@ SIGNATURES = {
     "bfv_lr_scores_standard": [_vp, _vp, _vp, _sz, _vp, _up],
     "bfv_lr_packed_pair_from_workspace": [_vp, _vp, _sz, _sz, _vp, _sz, _vp, _up],
     "bfv_launch_count": [_vp, ctypes.POINTER(_u64)],
+    "bfv_lr_predict_packed_workspace": [_vp, _vp, _sz, _sz, ctypes.POINTER(_sz)],
+    "bfv_lr_predict_packed": [_vp, _vp, _vp, _vp, _sz, _u64, _vp, _vp, _sz, _sz, _up],
+    "bfv_lr_predict_packed_host": [_vp, _vp, _vp, _vp, _sz, _u64, _vp, _vp, _sz, _sz, _up],
+    "bfv_profile": [_vp, ctypes.c_int],
+    "bfv_profile_read": [_vp, ctypes.c_int, ctypes.POINTER(_u64), ctypes.POINTER(ctypes.c_double)],
 }
+
+# Kernel kinds of bfv_profile_read (BFV_K_* in include/bfv_lr.h).
+KERNEL_KINDS = ["ntt", "ks_prep", "ks_modup", "ks_moddown_p", "ks_moddown", "mac", "bias_mask", "compress",
+                "encrypt", "decrypt", "encode", "standard"]
 
 
 def lib():
@@ -329,6 +338,53 @@ class Context:
         _call("bfv_lr_scores_standard", self.handle, model.handle, _ptr(X_ct.contiguous()), nX, _ptr(Y),
               _stream(stream))
         return Y
+
+    def predict_workspace(self, model: Model, nX: int, pair_chunk: int = 0) -> int:
+        n = _sz()
+        _call("bfv_lr_predict_packed_workspace", self.handle, model.handle, nX, pair_chunk, ctypes.byref(n))
+        return n.value
+
+    def predict_packed(self, keys: Keys, model: Model, X, seed: int, out=None, ws=None, pair_chunk: int = 0,
+                       stream=None):
+        """Whole protocol on device buffers: X uint8[nX][f] -> scores int64[nX][nY] (mod t)."""
+        import torch
+        nX = X.shape[0]
+        scores = out if out is not None else torch.empty((nX, model.nY), dtype=torch.int64, device=X.device)
+        need = self.predict_workspace(model, nX, pair_chunk)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=X.device)
+        _call("bfv_lr_predict_packed", self.handle, keys.handle, model.handle, _ptr(X.contiguous()), nX, seed,
+              _ptr(scores), _ptr(ws), ws.numel(), pair_chunk, _stream(stream))
+        return scores
+
+    def predict_packed_host(self, keys: Keys, model: Model, X_host, seed: int, out=None, ws=None,
+                            pair_chunk: int = 0, stream=None):
+        """Whole protocol with HOST buffers (the copies happen inside the C call): X_host uint8
+        [nX][f] (numpy or pinned torch) -> scores int64[nX][nY] on the host."""
+        import torch
+        nX = X_host.shape[0]
+        if out is None:
+            out = np.empty((nX, model.nY), dtype=np.int64)
+        xp = X_host.data_ptr() if hasattr(X_host, "data_ptr") else X_host.ctypes.data
+        op = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
+        need = self.predict_workspace(model, nX, pair_chunk)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=f"cuda:{self.device}")
+        _call("bfv_lr_predict_packed_host", self.handle, keys.handle, model.handle, ctypes.c_void_p(xp), nX, seed,
+              ctypes.c_void_p(op), _ptr(ws), ws.numel(), pair_chunk, _stream(stream))
+        return out
+
+    def profile(self, enable: bool):
+        _call("bfv_profile", self.handle, 1 if enable else 0)
+
+    def profile_read(self) -> dict:
+        """{kernel kind: (launches, total ms)} since the last read."""
+        out = {}
+        for k, name in enumerate(KERNEL_KINDS):
+            n, ms = _u64(), ctypes.c_double()
+            _call("bfv_profile_read", self.handle, k, ctypes.byref(n), ctypes.byref(ms))
+            out[name] = (n.value, ms.value)
+        return out
 
     def packed_pair_from_workspace(self, model: Model, nX: int, pair_chunk: int, ws, g: int, stream=None):
         out = self._empty_u64(2, self.L, self.N)

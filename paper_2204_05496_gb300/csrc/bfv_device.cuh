@@ -34,8 +34,8 @@ struct ModTab {
     u64 phalf;              // floor(P/2) mod q
     u64 delta;              // floor(Q/t) mod q
     u64 r64, r64p;          // 2^64 mod q and companion
-    const u64 *fw, *fwp;    // forward twiddles psi^brev(k), k < N, and companions
-    const u64 *iw, *iwp;    // inverse twiddles psi^-brev(k) and companions
+    const ulonglong2 *fw;   // forward twiddles {psi^brev(k), Shoup companion}, k < N
+    const ulonglong2 *iw;   // inverse twiddles {psi^-brev(k), Shoup companion}
 };
 
 // ------------------------------------------------------------------ modular arithmetic
@@ -106,17 +106,17 @@ template <int M> struct PadSize { static constexpr int value = M + (M >> 4); };
 // Forward Cooley-Tukey stages s .. s+R-1 (global stage numbers) on a group of 2^R values
 // x[r] = a[base + r * t_last]; gblock is the global block index at stage s.
 template <int R>
-__device__ __forceinline__ void fwd_radix(u64 (&x)[1 << R], int s, int gblock, const u64 *__restrict__ fw,
-                                          const u64 *__restrict__ fwp, u64 q, u64 q2) {
+__device__ __forceinline__ void fwd_radix(u64 (&x)[1 << R], int s, int gblock, const ulonglong2 *__restrict__ fw,
+                                          u64 q, u64 q2) {
 #pragma unroll
     for (int u = 0; u < R; ++u) {
         const int half = 1 << (R - 1 - u);
 #pragma unroll
         for (int k = 0; k < (1 << u); ++k) {
             const int ti = (1 << (s + u)) + (gblock << u) + k;
-            const u64 w = __ldg(fw + ti), wp = __ldg(fwp + ti);
+            const ulonglong2 w = __ldg(fw + ti);
 #pragma unroll
-            for (int j = 0; j < half; ++j) ct_bfly(x[k * 2 * half + j], x[k * 2 * half + j + half], w, wp, q, q2);
+            for (int j = 0; j < half; ++j) ct_bfly(x[k * 2 * half + j], x[k * 2 * half + j + half], w.x, w.y, q, q2);
         }
     }
 }
@@ -126,8 +126,8 @@ __device__ __forceinline__ void fwd_radix(u64 (&x)[1 << R], int s, int gblock, c
 // transform is stage s0+R-1 and N^-1 is folded into it. (Indexing by r keeps x[] in
 // registers; the repeated twiddle loads of one stage hit the same address.)
 template <int R, bool LASTSTAGE>
-__device__ __forceinline__ void inv_radix(u64 (&x)[1 << R], int s0, int block, int N, const u64 *__restrict__ iw,
-                                          const u64 *__restrict__ iwp, u64 ni, u64 nip, u64 il, u64 ilp, u64 q,
+__device__ __forceinline__ void inv_radix(u64 (&x)[1 << R], int s0, int block, int N,
+                                          const ulonglong2 *__restrict__ iw, u64 ni, u64 nip, u64 il, u64 ilp, u64 q,
                                           u64 q2) {
 #pragma unroll
     for (int u = 0; u < R; ++u) {
@@ -138,7 +138,8 @@ __device__ __forceinline__ void inv_radix(u64 (&x)[1 << R], int s0, int block, i
                 gs_bfly_last(x[r], x[r + (1 << u)], ni, nip, il, ilp, q, q2);
             } else {
                 const int ti = (N >> (s0 + u + 1)) + (block << (R - 1 - u)) + (r >> (u + 1));
-                gs_bfly(x[r], x[r + (1 << u)], __ldg(iw + ti), __ldg(iwp + ti), q, q2);
+                const ulonglong2 w = __ldg(iw + ti);
+                gs_bfly(x[r], x[r + (1 << u)], w.x, w.y, q, q2);
             }
         }
     }
@@ -176,7 +177,7 @@ __device__ __forceinline__ void fwd_passes(u64 *sm, const ModTab &T, int C, int 
             if constexpr (P == 0) x[r] = load(base + r * TL);
             else x[r] = sm[padi(base + r * TL)];
         }
-        fwd_radix<R>(x, S + C, (hidx << S) + block, T.fw, T.fwp, q, q2);
+        fwd_radix<R>(x, S + C, (hidx << S) + block, T.fw, q, q2);
 #pragma unroll
         for (int r = 0; r < (1 << R); ++r) {
             if constexpr (P == NP - 1) store(base + r * TL, red1(red2(x[r], q2), q));
@@ -216,7 +217,7 @@ __device__ __forceinline__ void inv_passes(u64 *sm, const ModTab &T, Load &load,
             if constexpr (P == 0) x[r] = load(base + r * TL);
             else x[r] = sm[padi(base + r * TL)];
         }
-        inv_radix<R, P == NP - 1>(x, S, block, N, T.iw, T.iwp, T.ninv, T.ninvp, T.ilast, T.ilastp, q, q2);
+        inv_radix<R, P == NP - 1>(x, S, block, N, T.iw, T.ninv, T.ninvp, T.ilast, T.ilastp, q, q2);
 #pragma unroll
         for (int r = 0; r < (1 << R); ++r) {
             if constexpr (P == NP - 1) store(base + r * TL, red1(x[r], q));
@@ -284,6 +285,11 @@ __device__ __forceinline__ int gauss_of(u32 lo, u32 hi, u32 sgn, const u64 *cdt,
     for (int k = 0; k < n; ++k) mag += (r >= cdt[k]) ? 1 : 0;
     return (mag != 0 && (sgn & 1u)) ? -mag : mag;
 }
+
+// A constant operand and its Shoup companion, stored side by side.
+typedef ulonglong2 shoup_t;
+__device__ __forceinline__ shoup_t make_shoup(u64 w, u64 q) { return make_ulonglong2(w, shoup_companion(w, q)); }
+__device__ __forceinline__ u64 mul_shoup(u64 x, shoup_t w, u64 q) { return mul_shoup(x, w.x, w.y, q); }
 
 // Small signed integer lifted into [0, q).
 __device__ __forceinline__ u64 lift_small(int v, u64 q) { return v >= 0 ? (u64)v : q - (u64)(-v); }

@@ -4,6 +4,8 @@
 #include <cstdint>
 #include <vector>
 #include <atomic>
+#include <mutex>
+#include <utility>
 #include <cuda_runtime.h>
 
 #include "bfv_device.cuh"
@@ -19,6 +21,20 @@ struct DecConst {
     u64 invp[BFV_MAXP][BFV_MAXP];    // Shoup companions
     u64 qhalf[BFV_MAXW];             // floor(Q/2)
     u64 qshift[32][BFV_MAXW];        // Q << b for b < tbits
+};
+
+// Opt-in per-kernel CUDA-event timing (bfv_profile / bfv_profile_read).
+struct Profiler {
+    bool on = false;
+    std::mutex mu;
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending[BFV_K_COUNT];
+    std::vector<cudaEvent_t> pool;
+    cudaEvent_t get() {
+        cudaEvent_t e = nullptr;
+        if (!pool.empty()) { e = pool.back(); pool.pop_back(); }
+        else cudaEventCreate(&e);
+        return e;
+    }
 };
 
 struct bfv_ctx {
@@ -38,21 +54,22 @@ struct bfv_ctx {
     std::vector<u64> galois;         // rotate-and-sum Galois elements, in order
     std::vector<u64> delta_host;     // floor(Q/t) mod q_l
     std::atomic<uint64_t> launches{0};
+    mutable Profiler prof;
 };
 
 struct bfv_keys {
     const bfv_ctx *ctx = nullptr;
     int8_t *sk = nullptr;            // [N] ternary
-    u64 *sk_eval = nullptr;          // [nqp][2][N]: value, companion (evaluation layout)
-    u64 *pk_eval = nullptr;          // [2][L][2][N]: value, companion
-    u64 *gk_eval = nullptr;          // [ng][L digits][2 comps][nqp][2][N]: value, companion
+    shoup_t *sk_eval = nullptr;      // [nqp][N] {value, companion} (evaluation layout)
+    shoup_t *pk_eval = nullptr;      // [2][L][N]
+    shoup_t *gk_eval = nullptr;      // [ng][L digits][2 comps][nqp][N]
     int ng = 0;
 };
 
 struct bfv_model {
     const bfv_ctx *ctx = nullptr;
     size_t f = 0, nY = 0, K = 0;
-    u64 *w_eval = nullptr;           // [nY][K][L][2][N]: value, companion (packed product)
+    shoup_t *w_eval = nullptr;       // [nY][K][L][N] {value, companion} (packed product)
     int64_t *w_int = nullptr;        // [f][nY] integer weights (standard product)
     u64 *bias_delta = nullptr;       // [nY][L]: Delta [b_j]_t mod q_l
     int64_t wmax = 0;                // max |w| (bounds the standard product's accumulators)
@@ -62,6 +79,29 @@ struct bfv_model {
 inline void count_launch(const bfv_ctx *c, uint64_t n = 1) {
     const_cast<bfv_ctx *>(c)->launches.fetch_add(n, std::memory_order_relaxed);
 }
+
+// Records an event pair around the launches in its scope when profiling is on.
+struct ProfScope {
+    const bfv_ctx *c;
+    int kind;
+    cudaStream_t st;
+    cudaEvent_t a = nullptr;
+    ProfScope(const bfv_ctx *c_, int kind_, cudaStream_t st_) : c(c_), kind(kind_), st(st_) {
+        if (c->prof.on) {
+            std::lock_guard<std::mutex> g(c->prof.mu);
+            a = c->prof.get();
+            cudaEventRecord(a, st);
+        }
+    }
+    ~ProfScope() {
+        if (a) {
+            std::lock_guard<std::mutex> g(c->prof.mu);
+            cudaEvent_t b = c->prof.get();
+            cudaEventRecord(b, st);
+            c->prof.pending[kind].push_back({a, b});
+        }
+    }
+};
 
 #define BFV_CUDA_TRY(expr)                              \
     do {                                                \
@@ -87,7 +127,7 @@ int launch_model_weights(const bfv_ctx *c, bfv_model *m, const u64 *w_pt, cudaSt
 
 struct PackedPlan {
     size_t nX, nY, K, npairs, nout, chunk;
-    size_t off_xntt, off_yacc, off_state, off_digits, off_u, off_r, total;
+    size_t off_xntt, off_yacc, off_state, off_digits, off_s1, off_u, off_r, total;
 };
 PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t chunk);
 int launch_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const u64 *X_ct, size_t nX,

@@ -195,6 +195,9 @@ template <class T> int dalloc(T **p, size_t n) {
 
 void free_ctx(bfv_ctx *c) {
     if (!c) return;
+    for (auto &v : c->prof.pending)
+        for (auto &pr : v) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
+    for (auto e : c->prof.pool) cudaEventDestroy(e);
     cudaFree(c->dmods);
     cudaFree(c->dtw);
     cudaFree(c->dslot);
@@ -272,22 +275,22 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
             c->omega = psi;
         }
         const u64 psii = inv_h(psi, q);
-        u64 *fw = &tw[((size_t)j * 4 + 0) * N], *fwp = &tw[((size_t)j * 4 + 1) * N];
-        u64 *iw = &tw[((size_t)j * 4 + 2) * N], *iwp = &tw[((size_t)j * 4 + 3) * N];
+        // [j][fw pairs (2N words)][iw pairs (2N words)], each pair {w, w'}
+        u64 *fwv = &tw[(size_t)j * 4 * N], *iwv = &tw[(size_t)j * 4 * N + 2 * N];
         std::vector<u64> pw(N), ipw(N);
         pw[0] = ipw[0] = 1;
         for (u64 i = 1; i < N; ++i) { pw[i] = mulmod_h(pw[i - 1], psi, q); ipw[i] = mulmod_h(ipw[i - 1], psii, q); }
         for (u64 k = 0; k < N; ++k) {
             const u64 b = brev_h(k, c->logN);
-            fw[k] = pw[b]; fwp[k] = shoup_h(fw[k], q);
-            iw[k] = ipw[b]; iwp[k] = shoup_h(iw[k], q);
+            fwv[2 * k] = pw[b]; fwv[2 * k + 1] = shoup_h(pw[b], q);
+            iwv[2 * k] = ipw[b]; iwv[2 * k + 1] = shoup_h(ipw[b], q);
         }
         ModTab &T = c->hmods[j];
         T.q = q;
         T.q2 = 2 * q;
         T.ninv = inv_h(N % q, q);
         T.ninvp = shoup_h(T.ninv, q);
-        T.ilast = mulmod_h(iw[1], T.ninv, q);
+        T.ilast = mulmod_h(iwv[2], T.ninv, q);
         T.ilastp = shoup_h(T.ilast, q);
         T.bits = ilog2_h(q + 1);
         T.mu = (u64)(((u128)1 << (2 * T.bits)) / q);
@@ -303,7 +306,8 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
         T.r64 = (u64)(((u128)1 << 64) % q);
         T.r64p = shoup_h(T.r64, q);
         const u64 *base = c->dtw + (size_t)j * 4 * N;
-        T.fw = base; T.fwp = base + N; T.iw = base + 2 * N; T.iwp = base + 3 * N;
+        T.fw = (const ulonglong2 *)base;
+        T.iw = (const ulonglong2 *)(base + 2 * N);
     }
     if (cudaMemcpy(c->dtw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) { free_ctx(c); return BFV_ERR_CUDA; }
     if ((rc = dalloc(&c->dmods, nmod))) { free_ctx(c); return rc; }
@@ -396,8 +400,8 @@ int bfv_keygen(bfv_ctx *ctx, uint64_t seed, uintptr_t stream, bfv_keys **out) {
     k->ng = (int)ctx->galois.size();
     const size_t N = ctx->N, L = ctx->L, nqp = ctx->nqp;
     int rc = BFV_OK;
-    if ((rc = dalloc(&k->sk, N)) || (rc = dalloc(&k->sk_eval, nqp * 2 * N)) || (rc = dalloc(&k->pk_eval, 2 * L * 2 * N)) ||
-        (rc = dalloc(&k->gk_eval, (size_t)k->ng * L * 2 * nqp * 2 * N))) {
+    if ((rc = dalloc(&k->sk, N)) || (rc = dalloc(&k->sk_eval, nqp * N)) || (rc = dalloc(&k->pk_eval, 2 * L * N)) ||
+        (rc = dalloc(&k->gk_eval, (size_t)k->ng * L * 2 * nqp * N))) {
         bfv_keys_free(k);
         return rc;
     }
@@ -500,7 +504,7 @@ int bfv_model_prepare(bfv_ctx *ctx, const int64_t *W, const int64_t *b, size_t f
     int rc;
     int64_t *dslots = nullptr;
     u64 *dpt = nullptr;
-    if ((rc = dalloc(&m->w_eval, nY * K * L * 2 * N)) || (rc = dalloc(&m->w_int, f * nY)) ||
+    if ((rc = dalloc(&m->w_eval, nY * K * L * N)) || (rc = dalloc(&m->w_int, f * nY)) ||
         (rc = dalloc(&m->bias_delta, nY * L)) || (rc = dalloc(&dslots, nY * K * N)) || (rc = dalloc(&dpt, nY * K * N))) {
         cudaFree(dslots);
         cudaFree(dpt);
@@ -582,6 +586,110 @@ int bfv_lr_packed_pair_from_workspace(bfv_ctx *ctx, const bfv_model *model, size
     int rc = launch_pair_export(ctx, plan, ws, g - last_chunk_start, (u64 *)ct_out, S(stream));
     if (rc) return rc;
     return cudaStreamSynchronize(S(stream)) == cudaSuccess ? BFV_OK : BFV_ERR_CUDA;
+}
+
+// ------------------------------------------------------------------ whole-protocol calls
+
+namespace {
+struct PredictPlan {
+    PackedPlan packed;
+    size_t off_x, off_pt, off_ct, off_encws, off_packed, off_y, off_decws, off_ptout, off_slots, total;
+};
+PredictPlan predict_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t chunk) {
+    PredictPlan p{};
+    p.packed = packed_plan(c, m, nX, chunk);
+    const size_t N = c->N, L = c->L, K = m->K, nout = p.packed.nout, ctb = 2 * L * N * 8;
+    size_t off = 0;
+    p.off_x = off; off += align256(nX * m->f);
+    p.off_pt = off; off += align256(nX * K * N * 8);
+    p.off_ct = off; off += align256(nX * K * ctb);
+    p.off_encws = off; off += align256(nX * K * 3 * N);
+    p.off_packed = off; off += align256(p.packed.total);
+    p.off_y = off; off += align256(nout * ctb);
+    p.off_decws = off; off += align256(nout * L * N * 8);
+    p.off_ptout = off; off += align256(nout * N * 8);
+    p.off_slots = off; off += align256(nout * N * 8);
+    p.total = off;
+    return p;
+}
+int run_predict(bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const uint8_t *X, size_t nX, u64 seed,
+                const PredictPlan &pl, char *ws, cudaStream_t st) {
+    u64 *pt = (u64 *)(ws + pl.off_pt), *ct = (u64 *)(ws + pl.off_ct), *Y = (u64 *)(ws + pl.off_y);
+    u64 *ptout = (u64 *)(ws + pl.off_ptout);
+    int64_t *slots = (int64_t *)(ws + pl.off_slots);
+    int rc;
+    if ((rc = launch_encode_features(c, X, nX, m->f, pt, st))) return rc;
+    if ((rc = launch_encrypt(c, k, pt, nX * m->K, seed, 0, ct, ws + pl.off_encws, st))) return rc;
+    if ((rc = launch_packed(c, k, m, ct, nX, Y, ws + pl.off_packed, pl.packed, st))) return rc;
+    if ((rc = launch_decrypt(c, k, Y, pl.packed.nout, ptout, ws + pl.off_decws, st))) return rc;
+    return launch_decode(c, ptout, pl.packed.nout, slots, st);
+}
+}  // namespace
+
+int bfv_lr_predict_packed_workspace(const bfv_ctx *ctx, const bfv_model *model, size_t nX, size_t pair_chunk,
+                                    size_t *bytes) {
+    if (!ctx || !model || model->ctx != ctx || !bytes || nX == 0) return BFV_ERR_INVALID_ARG;
+    *bytes = predict_plan(ctx, model, nX, pair_chunk).total;
+    return BFV_OK;
+}
+
+int bfv_lr_predict_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint8_t *X, size_t nX,
+                          uint64_t seed, int64_t *scores, void *ws, size_t ws_bytes, size_t pair_chunk,
+                          uintptr_t stream) {
+    if (!ctx || !keys || !model || keys->ctx != ctx || model->ctx != ctx) return BFV_ERR_INVALID_ARG;
+    if (nX == 0) return BFV_OK;
+    if (!X || !scores || !ws) return BFV_ERR_INVALID_ARG;
+    PredictPlan pl = predict_plan(ctx, model, nX, pair_chunk);
+    if (ws_bytes < pl.total) return BFV_ERR_OVER_BUDGET;
+    int rc = run_predict(ctx, keys, model, X, nX, seed, pl, (char *)ws, S(stream));
+    if (rc) return rc;
+    return cudaMemcpyAsync(scores, (char *)ws + pl.off_slots, nX * model->nY * 8, cudaMemcpyDeviceToDevice,
+                           S(stream)) == cudaSuccess ? BFV_OK : BFV_ERR_CUDA;
+}
+
+int bfv_lr_predict_packed_host(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint8_t *X_host,
+                               size_t nX, uint64_t seed, int64_t *scores_host, void *ws, size_t ws_bytes,
+                               size_t pair_chunk, uintptr_t stream) {
+    if (!ctx || !keys || !model || keys->ctx != ctx || model->ctx != ctx) return BFV_ERR_INVALID_ARG;
+    if (nX == 0) return BFV_OK;
+    if (!X_host || !scores_host || !ws) return BFV_ERR_INVALID_ARG;
+    PredictPlan pl = predict_plan(ctx, model, nX, pair_chunk);
+    if (ws_bytes < pl.total) return BFV_ERR_OVER_BUDGET;
+    char *w = (char *)ws;
+    cudaStream_t st = S(stream);
+    if (cudaMemcpyAsync(w + pl.off_x, X_host, nX * model->f, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return BFV_ERR_CUDA;
+    int rc = run_predict(ctx, keys, model, (const uint8_t *)(w + pl.off_x), nX, seed, pl, w, st);
+    if (rc) return rc;
+    if (cudaMemcpyAsync(scores_host, w + pl.off_slots, nX * model->nY * 8, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+        return BFV_ERR_CUDA;
+    return cudaStreamSynchronize(st) == cudaSuccess ? BFV_OK : BFV_ERR_CUDA;
+}
+
+int bfv_profile(bfv_ctx *ctx, int enable) {
+    if (!ctx) return BFV_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(ctx->prof.mu);
+    ctx->prof.on = enable != 0;
+    return BFV_OK;
+}
+
+int bfv_profile_read(bfv_ctx *ctx, int kind, uint64_t *launches, double *total_ms) {
+    if (!ctx || kind < 0 || kind >= BFV_K_COUNT || !launches || !total_ms) return BFV_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(ctx->prof.mu);
+    double ms = 0;
+    int rc = BFV_OK;
+    for (auto &pr : ctx->prof.pending[kind]) {
+        float x = 0;
+        if (cudaEventSynchronize(pr.second) != cudaSuccess || cudaEventElapsedTime(&x, pr.first, pr.second) != cudaSuccess)
+            rc = BFV_ERR_CUDA;
+        ms += x;
+        ctx->prof.pool.push_back(pr.first);
+        ctx->prof.pool.push_back(pr.second);
+    }
+    *launches = ctx->prof.pending[kind].size();
+    *total_ms = ms;
+    ctx->prof.pending[kind].clear();
+    return rc;
 }
 
 int bfv_launch_count(const bfv_ctx *ctx, uint64_t *count) {

@@ -29,7 +29,7 @@ template <class K> void set_smem(K kern, size_t bytes) {
 // ------------------------------------------------------------------ MAC (lines 5-13)
 // C[g][c][l][p] = sum_k Xe[i][k][c][l][p] * We[j][k][l][p]; grid.x = (g, c, l), grid.y = tile.
 __global__ void __launch_bounds__(256) k_mac(const ModTab *__restrict__ mods, int N, int L, int K, int nY, size_t g0,
-                                             const u64 *__restrict__ Xe, const u64 *__restrict__ We, u64 *C) {
+                                             const u64 *__restrict__ Xe, const shoup_t *__restrict__ We, u64 *C) {
     const size_t x = blockIdx.x;
     const int l = (int)(x % L), c = (int)((x / L) % 2);
     const size_t gl = x / (2 * L), g = g0 + gl;
@@ -44,8 +44,8 @@ __global__ void __launch_bounds__(256) k_mac(const ModTab *__restrict__ mods, in
         u64 acc = 0;
         for (int k = 0; k < K; ++k) {
             const u64 xv = Xe[(i * K + k) * ctw + ((size_t)c * L + l) * N + p];
-            const u64 *w = We + (((j * K + k) * L + l) * 2) * (size_t)N;
-            acc = red2(acc + mul_shoup(xv, w[p], w[N + p], q), q2);
+            const shoup_t w = __ldg(We + ((j * K + k) * L + l) * (size_t)N + p);
+            acc = red2(acc + mul_shoup(xv, w, q), q2);
         }
         C[gl * ctw + ((size_t)c * L + l) * N + p] = red1(acc, q);
     }
@@ -53,10 +53,11 @@ __global__ void __launch_bounds__(256) k_mac(const ModTab *__restrict__ mods, in
 
 // ------------------------------------------------------------------ key switching
 
-// grid.x = (g, c, l). c = 1: digit D[g][l] = INTT(sigma(C1[g][l])); c = 0: C0 += sigma(C0).
+// grid.x = (g, c, l). c = 1: digit D[g][l] = INTT(sigma(C1[g][l])), and S1[g][l] = sigma(C1[g][l])
+// in evaluation form; c = 0: C0 += sigma(C0).
 template <int LOGN>
 __global__ void __launch_bounds__(nt_for(LOGN)) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 gal, u64 *C,
-                                                           u64 *D) {
+                                                           u64 *D, u64 *S1) {
     extern __shared__ u64 sm[];
     constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
     const int l = blockIdx.x % L, c = (blockIdx.x / L) % 2;
@@ -64,8 +65,9 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_ks_prep(const ModTab *__restri
     const ModTab T = mods[l];
     u64 *limb = C + ((g * 2 + c) * L + l) * (size_t)N;
     if (c == 1) {
-        u64 *dst = D + (g * L + l) * (size_t)N;
-        ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return limb[auto_src(p, gal, LOGN)]; },
+        u64 *dst = D + (g * L + l) * (size_t)N, *s1 = S1 + (g * L + l) * (size_t)N;
+        ntt_inverse<LOGN, NT>(sm, T,
+                              [&](int p) { const u64 v = limb[auto_src(p, gal, LOGN)]; s1[p] = v; return v; },
                               [&](int p, u64 v) { dst[p] = v; });
     } else {
         for (int p = threadIdx.x; p < N; p += NT) sm[p] = limb[p];
@@ -74,12 +76,38 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_ks_prep(const ModTab *__restri
     }
 }
 
+// acc_c[p] += v(p) * key_c[p] for this thread's points p = tid + e NT, four at a time with
+// all loads issued first.
+template <int H, int NT, class Val>
+__device__ __forceinline__ void key_mac(u64 *acc0, u64 *acc1, const shoup_t *__restrict__ k0,
+                                        const shoup_t *__restrict__ k1, u64 q, u64 q2, Val val) {
+    static_assert(H % (4 * NT) == 0, "points per thread must be a multiple of 4");
+#pragma unroll 1
+    for (int p0 = threadIdx.x; p0 < H; p0 += 4 * NT) {
+        u64 v[4];
+        shoup_t a[4], b[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int p = p0 + e * NT;
+            a[e] = __ldg(k0 + p);
+            b[e] = __ldg(k1 + p);
+            v[e] = val(p);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int p = p0 + e * NT;
+            acc0[p] = red2(acc0[p] + mul_shoup(v[e], a[e], q), q2);
+            acc1[p] = red2(acc1[p] + mul_shoup(v[e], b[e], q), q2);
+        }
+    }
+}
+
 // grid.x = (g, j, h): U[g][c][j][h N/2 + p] = sum_i NTT_j(D[g][i] mod q_j)[h N/2 + p] * key[i][c][j].
-// The digit of index j itself is sigma(C1[g][j]) in evaluation form already.
+// The digit of index j itself is sigma(C1[g][j]) in evaluation form already (S1).
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN - 1)) k_ks_modup(const ModTab *__restrict__ mods, int L, u32 gal,
-                                                                const u64 *__restrict__ C, const u64 *__restrict__ D,
-                                                                const u64 *__restrict__ key, u64 *U) {
+__global__ void __launch_bounds__(nt_for(LOGN - 1)) k_ks_modup(const ModTab *__restrict__ mods, int L,
+                                                                const u64 *__restrict__ S1, const u64 *__restrict__ D,
+                                                                const shoup_t *__restrict__ key, u64 *U) {
     extern __shared__ u64 sm[];
     constexpr int N = 1 << LOGN, H = N / 2, NT = nt_for(LOGN - 1);
     u64 *acc0 = sm + PadSize<H>::value, *acc1 = acc0 + H;
@@ -88,41 +116,31 @@ __global__ void __launch_bounds__(nt_for(LOGN - 1)) k_ks_modup(const ModTab *__r
     const size_t g = blockIdx.x / (2 * nqp);
     const ModTab T = mods[j];
     const u64 q = T.q, q2 = T.q2;
-    const u64 w1 = T.fw[1], w1p = T.fwp[1];
+    const shoup_t w1 = T.fw[1];
     for (int p = threadIdx.x; p < H; p += NT) { acc0[p] = 0; acc1[p] = 0; }
-    const size_t keystride = (size_t)nqp * 2 * N;     // one (digit, component) block
+    const size_t keystride = (size_t)nqp * N;     // one (digit, component) block
 #pragma unroll 1
     for (int i = 0; i < L; ++i) {
-        const u64 *k0 = key + ((size_t)i * 2 + 0) * keystride + (size_t)j * 2 * N + (size_t)h * H;
-        const u64 *k1 = key + ((size_t)i * 2 + 1) * keystride + (size_t)j * 2 * N + (size_t)h * H;
+        const shoup_t *k0 = key + ((size_t)i * 2 + 0) * keystride + (size_t)j * N + (size_t)h * H;
+        const shoup_t *k1 = key + ((size_t)i * 2 + 1) * keystride + (size_t)j * N + (size_t)h * H;
         if (i == j) {
-            const u64 *c1 = C + ((g * 2 + 1) * L + j) * (size_t)N;
-            __syncthreads();
-            for (int p = threadIdx.x; p < H; p += NT) {
-                const u64 v = c1[auto_src(h * H + p, gal, LOGN)];
-                acc0[p] = red2(acc0[p] + mul_shoup(v, k0[p], k0[N + p], q), q2);
-                acc1[p] = red2(acc1[p] + mul_shoup(v, k1[p], k1[N + p], q), q2);
-            }
+            const u64 *s1 = S1 + (g * L + j) * (size_t)N + (size_t)h * H;
+            key_mac<H, NT>(acc0, acc1, k0, k1, q, q2, [&](int p) { return s1[p]; });
         } else {
             const u64 *d = D + (g * L + i) * (size_t)N;
             ntt_forward<LOGN - 1, NT>(
                 sm, T, 1, h,
                 [&](int p) {
                     const u64 a = red1(d[p], q), b = red1(d[p + H], q);
-                    const u64 t = mul_shoup(b, w1, w1p, q);
+                    const u64 t = mul_shoup(b, w1, q);
                     return h == 0 ? a + t : a - t + q2;
                 },
                 [&](int p, u64 v) { sm[padi(p)] = v; });
             __syncthreads();
-            for (int p = threadIdx.x; p < H; p += NT) {
-                const u64 v = sm[padi(p)];
-                acc0[p] = red2(acc0[p] + mul_shoup(v, k0[p], k0[N + p], q), q2);
-                acc1[p] = red2(acc1[p] + mul_shoup(v, k1[p], k1[N + p], q), q2);
-            }
+            key_mac<H, NT>(acc0, acc1, k0, k1, q, q2, [&](int p) { return sm[padi(p)]; });
             __syncthreads();
         }
     }
-    __syncthreads();
     u64 *u0 = U + ((g * 2 + 0) * nqp + j) * (size_t)N + (size_t)h * H;
     u64 *u1 = U + ((g * 2 + 1) * nqp + j) * (size_t)N + (size_t)h * H;
     for (int p = threadIdx.x; p < H; p += NT) { u0[p] = red1(acc0[p], q); u1[p] = red1(acc1[p], q); }
@@ -160,9 +178,18 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_ks_moddown(const ModTab *__res
     __syncthreads();
     const u64 *u = U + ((g * 2 + c) * nqp + l) * (size_t)N;
     u64 *dst = C + ((g * 2 + c) * L + l) * (size_t)N;
-    for (int p = threadIdx.x; p < N; p += NT) {
-        const u64 v = red1(mul_shoup(u[p] + sm[padi(p)], T.pinv, T.pinvp, T.q), T.q);
-        dst[p] = add_mod(dst[p], v, T.q);
+    static_assert(N % (4 * NT) == 0, "points per thread must be a multiple of 4");
+#pragma unroll 1
+    for (int p0 = threadIdx.x; p0 < N; p0 += 4 * NT) {
+        u64 a[4], b[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) { a[e] = u[p0 + e * NT]; b[e] = dst[p0 + e * NT]; }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int p = p0 + e * NT;
+            const u64 v = red1(mul_shoup(a[e] + sm[padi(p)], T.pinv, T.pinvp, T.q), T.q);
+            dst[p] = add_mod(b[e], v, T.q);
+        }
     }
 }
 
@@ -246,6 +273,7 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const u6
     const size_t ctw = 2 * (size_t)L * N;
     u64 *Xe = (u64 *)(ws + pl.off_xntt), *Yacc = (u64 *)(ws + pl.off_yacc), *C = (u64 *)(ws + pl.off_state);
     u64 *D = (u64 *)(ws + pl.off_digits), *U = (u64 *)(ws + pl.off_u), *R = (u64 *)(ws + pl.off_r);
+    u64 *S1 = (u64 *)(ws + pl.off_s1);
     const size_t full = pad_bytes<N>(), half = pad_bytes<N / 2>() + 2 * sizeof(u64) * (N / 2);
     set_smem(k_ks_prep<LOGN>, full);
     set_smem(k_ks_modup<LOGN>, half);
@@ -256,26 +284,33 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const u6
     int rc = launch_ntt_limbs(c, X_ct, Xe, pl.nX * pl.K, true, st);
     if (rc) return rc;
     if (cudaMemsetAsync(Yacc, 0, pl.nout * ctw * sizeof(u64), st) != cudaSuccess) return BFV_ERR_CUDA;
-    const size_t keyblock = (size_t)L * 2 * nqp * 2 * N;   // one Galois element
+    const size_t keyblock = (size_t)L * 2 * nqp * N;   // one Galois element
     for (size_t g0 = 0; g0 < pl.npairs; g0 += pl.chunk) {
         const size_t ng = std::min(pl.chunk, pl.npairs - g0);
+        { ProfScope pr(c, BFV_K_MAC, st);
         k_mac<<<dim3((unsigned)(ng * 2 * L), (unsigned)((N + 1023) / 1024)), 256, 0, st>>>(
-            c->dmods, N, L, (int)pl.K, (int)pl.nY, g0, Xe, m->w_eval, C);
+            c->dmods, N, L, (int)pl.K, (int)pl.nY, g0, Xe, m->w_eval, C); }
         count_launch(c);
         for (int s = 0; s < k->ng; ++s) {
             const u32 gal = (u32)c->galois[s];
-            const u64 *key = k->gk_eval + (size_t)s * keyblock;
-            k_ks_prep<LOGN><<<(unsigned)(ng * 2 * L), nt_for(LOGN), full, st>>>(c->dmods, L, gal, C, D);
-            k_ks_modup<LOGN><<<(unsigned)(ng * nqp * 2), nt_for(LOGN - 1), half, st>>>(c->dmods, L, gal, C, D, key, U);
-            k_ks_moddown_p<LOGN><<<(unsigned)(ng * 2), nt_for(LOGN), full, st>>>(c->dmods, L, U, R);
-            k_ks_moddown<LOGN><<<(unsigned)(ng * 2 * L), nt_for(LOGN), full, st>>>(c->dmods, L, U, R, C);
+            const shoup_t *key = k->gk_eval + (size_t)s * keyblock;
+            { ProfScope pr(c, BFV_K_KS_PREP, st);
+              k_ks_prep<LOGN><<<(unsigned)(ng * 2 * L), nt_for(LOGN), full, st>>>(c->dmods, L, gal, C, D, S1); }
+            { ProfScope pr(c, BFV_K_KS_MODUP, st);
+              k_ks_modup<LOGN><<<(unsigned)(ng * nqp * 2), nt_for(LOGN - 1), half, st>>>(c->dmods, L, S1, D, key, U); }
+            { ProfScope pr(c, BFV_K_KS_MODDOWN_P, st);
+              k_ks_moddown_p<LOGN><<<(unsigned)(ng * 2), nt_for(LOGN), full, st>>>(c->dmods, L, U, R); }
+            { ProfScope pr(c, BFV_K_KS_MODDOWN, st);
+              k_ks_moddown<LOGN><<<(unsigned)(ng * 2 * L), nt_for(LOGN), full, st>>>(c->dmods, L, U, R, C); }
             count_launch(c, 4);
         }
+        { ProfScope pr(c, BFV_K_BIAS_MASK, st);
         k_bias_mask<LOGN><<<(unsigned)(ng * L), nt_for(LOGN), full, st>>>(c->dmods, L, nqp, (int)pl.nY, g0, c->dmaskpow,
-                                                                         m->bias_delta, C);
+                                                                         m->bias_delta, C); }
         count_launch(c);
         for (size_t o = g0 / N; o <= (g0 + ng - 1) / N; ++o) {
             const size_t ga = std::max(g0, o * N), gb = std::min(g0 + ng, (o + 1) * N);
+            ProfScope pr(c, BFV_K_COMPRESS, st);
             k_compress<<<(unsigned)((ctw + 255) / 256), 256, 0, st>>>(c->dmods, N, L, ga, gb, g0, C, Yacc + o * ctw);
             count_launch(c);
         }
@@ -303,6 +338,7 @@ PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t c
     p.off_yacc = off; off += al256(p.nout * ctb);
     p.off_state = off; off += al256(p.chunk * ctb);
     p.off_digits = off; off += al256(p.chunk * L * N * sizeof(u64));
+    p.off_s1 = off; off += al256(p.chunk * L * N * sizeof(u64));
     p.off_u = off; off += al256(p.chunk * 2 * nqp * N * sizeof(u64));
     p.off_r = off; off += al256(p.chunk * 2 * N * sizeof(u64));
     p.total = off;

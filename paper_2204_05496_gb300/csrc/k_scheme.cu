@@ -36,18 +36,18 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_ntt_limbs(const ModTab *__rest
         ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return src[p]; }, [&](int p, u64 v) { dst[p] = v; });
 }
 
-// Inverse transform of value arrays stored as [limb][2][N] (value, companion); limb x uses
-// modulus x % M; output [limb][N].
+// Inverse transform of evaluation-form {value, companion} arrays [limb][N]; limb x uses
+// modulus x % M; output [limb][N] coefficients.
 template <int LOGN>
 __global__ void __launch_bounds__(nt_for(LOGN)) k_intt_pairs(const ModTab *__restrict__ mods, int M,
-                                                              const u64 *__restrict__ in, u64 *out) {
+                                                              const shoup_t *__restrict__ in, u64 *out) {
     extern __shared__ u64 sm[];
     constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
     const size_t x = blockIdx.x;
     const ModTab T = mods[x % M];
-    const u64 *src = in + x * 2 * N;
+    const shoup_t *src = in + x * N;
     u64 *dst = out + x * N;
-    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return src[p]; }, [&](int p, u64 v) { dst[p] = v; });
+    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return src[p].x; }, [&](int p, u64 v) { dst[p] = v; });
 }
 
 // ------------------------------------------------------------------ encode / decode (mod t)
@@ -132,53 +132,50 @@ __global__ void k_keygen_sk(u64 seed, int N, int8_t *sk) {
     sk[k] = (int8_t)ternary_of(w[0]);
 }
 
-// Evaluation form of s for every modulus of QP: out [nqp][2][N] (value, companion).
+// Evaluation form of s for every modulus of QP: out [nqp][N] {value, companion}.
 template <int LOGN>
 __global__ void __launch_bounds__(nt_for(LOGN)) k_keygen_sk_eval(const ModTab *__restrict__ mods,
-                                                                  const int8_t *__restrict__ sk, u64 *out) {
+                                                                  const int8_t *__restrict__ sk, shoup_t *out) {
     extern __shared__ u64 sm[];
     constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
     const int j = blockIdx.x;
     const ModTab T = mods[j];
-    u64 *dst = out + (size_t)j * 2 * N;
+    shoup_t *dst = out + (size_t)j * N;
     ntt_forward<LOGN, NT>(sm, T, 0, 0, [&](int p) { return lift_small(sk[p], T.q); },
-                          [&](int p, u64 v) { dst[p] = v; dst[N + p] = shoup_companion(v, T.q); });
+                          [&](int p, u64 v) { dst[p] = make_shoup(v, T.q); });
 }
 
-// Public key limb l: pk1 = a (uniform), pk0 = -(a s + e); out [2][L][2][N].
+// Public key limb l: pk1 = a (uniform), pk0 = -(a s + e); out [2][L][N] {value, companion}.
 template <int LOGN>
 __global__ void __launch_bounds__(nt_for(LOGN)) k_keygen_pk(const ModTab *__restrict__ mods, const u64 *__restrict__ cdt,
-                                                             int cdt_len, u64 seed, int L, const u64 *__restrict__ sk_eval,
-                                                             u64 *pk) {
+                                                             int cdt_len, u64 seed, int L, const shoup_t *__restrict__ sk_eval,
+                                                             shoup_t *pk) {
     extern __shared__ u64 sm[];
     constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
     const int l = blockIdx.x;
     const ModTab T = mods[l];
-    u64 *pk0 = pk + (size_t)l * 2 * N, *pk1 = pk + ((size_t)L + l) * 2 * N;
-    const u64 *s = sk_eval + (size_t)l * 2 * N;
+    shoup_t *pk0 = pk + (size_t)l * N, *pk1 = pk + ((size_t)L + l) * N;
+    const shoup_t *s = sk_eval + (size_t)l * N;
     ntt_forward<LOGN, NT>(
         sm, T, 0, 0,
         [&](int p) { u32 w[16]; chacha20_block(seed, (u32)p, kPkA, 0, (u32)l, w); return uniform_of(w, T); },
         [&](int p, u64 v) {
-            pk1[p] = v; pk1[N + p] = shoup_companion(v, T.q);
-            pk0[p] = red1(mul_shoup(v, s[p], s[N + p], T.q), T.q);   // a s, finished below
+            pk1[p] = make_shoup(v, T.q);
+            pk0[p].x = red1(mul_shoup(v, s[p], T.q), T.q);   // a s, finished below
         });
     __syncthreads();
     ntt_forward<LOGN, NT>(
         sm, T, 0, 0,
         [&](int p) { u32 w[16]; chacha20_block(seed, (u32)p, kPkE, 0, 0, w); return lift_small(gauss_of(w[0], w[1], w[2], cdt, cdt_len), T.q); },
-        [&](int p, u64 v) {
-            const u64 r = sub_mod(0, add_mod(pk0[p], v, T.q), T.q);
-            pk0[p] = r; pk0[N + p] = shoup_companion(r, T.q);
-        });
+        [&](int p, u64 v) { pk0[p] = make_shoup(sub_mod(0, add_mod(pk0[p].x, v, T.q), T.q), T.q); });
 }
 
 // Galois key (element gi, digit i, limb j of QP):
-//   k1 = a, k0 = -a s + e + [i == j] [P]_{q_j} sigma_g(s); out [ng][L][2][nqp][2][N].
+//   k1 = a, k0 = -a s + e + [i == j] [P]_{q_j} sigma_g(s); out [ng][L][2][nqp][N] {value, companion}.
 template <int LOGN>
 __global__ void __launch_bounds__(nt_for(LOGN)) k_keygen_galois(const ModTab *__restrict__ mods, const u64 *__restrict__ cdt,
                                                                  int cdt_len, u64 seed, int L, const u64 *__restrict__ gal,
-                                                                 const u64 *__restrict__ sk_eval, u64 *gk) {
+                                                                 const shoup_t *__restrict__ sk_eval, shoup_t *gk) {
     extern __shared__ u64 sm[];
     constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
     const int nqp = L + 1;
@@ -186,15 +183,15 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_keygen_galois(const ModTab *__
     const ModTab T = mods[j];
     const u32 obj = (u32)gi * 256u + (u32)i;
     const u32 g = (u32)gal[gi];
-    u64 *k0 = gk + ((((size_t)gi * L + i) * 2 + 0) * nqp + j) * 2 * N;
-    u64 *k1 = gk + ((((size_t)gi * L + i) * 2 + 1) * nqp + j) * 2 * N;
-    const u64 *s = sk_eval + (size_t)j * 2 * N;
+    shoup_t *k0 = gk + ((((size_t)gi * L + i) * 2 + 0) * nqp + j) * N;
+    shoup_t *k1 = gk + ((((size_t)gi * L + i) * 2 + 1) * nqp + j) * N;
+    const shoup_t *s = sk_eval + (size_t)j * N;
     ntt_forward<LOGN, NT>(
         sm, T, 0, 0,
         [&](int p) { u32 w[16]; chacha20_block(seed, (u32)p, kGkA, obj, (u32)j, w); return uniform_of(w, T); },
         [&](int p, u64 v) {
-            k1[p] = v; k1[N + p] = shoup_companion(v, T.q);
-            k0[p] = red1(mul_shoup(v, s[p], s[N + p], T.q), T.q);
+            k1[p] = make_shoup(v, T.q);
+            k0[p].x = red1(mul_shoup(v, s[p], T.q), T.q);
         });
     __syncthreads();
     const u64 pmod = mods[L].q % T.q;
@@ -202,9 +199,9 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_keygen_galois(const ModTab *__
         sm, T, 0, 0,
         [&](int p) { u32 w[16]; chacha20_block(seed, (u32)p, kGkE, obj, 0, w); return lift_small(gauss_of(w[0], w[1], w[2], cdt, cdt_len), T.q); },
         [&](int p, u64 v) {
-            u64 r = sub_mod(v, k0[p], T.q);
-            if (i == j) r = add_mod(r, mul_barrett(pmod, s[auto_src(p, g, LOGN)], T.q, T.mu, T.bits), T.q);
-            k0[p] = r; k0[N + p] = shoup_companion(r, T.q);
+            u64 r = sub_mod(v, k0[p].x, T.q);
+            if (i == j) r = add_mod(r, mul_barrett(pmod, s[auto_src(p, g, LOGN)].x, T.q, T.mu, T.bits), T.q);
+            k0[p] = make_shoup(r, T.q);
         });
 }
 
@@ -228,7 +225,7 @@ __global__ void k_enc_sample(const u64 *__restrict__ cdt, int cdt_len, u64 seed,
 // CTA (c, comp, l): comp 0 -> pk0 u + e1 + Delta m, comp 1 -> pk1 u + e2 (limb l).
 template <int LOGN>
 __global__ void __launch_bounds__(nt_for(LOGN)) k_enc_main(const ModTab *__restrict__ mods, int L,
-                                                            const u64 *__restrict__ pk, const int8_t *__restrict__ rnd,
+                                                            const shoup_t *__restrict__ pk, const int8_t *__restrict__ rnd,
                                                             const u64 *__restrict__ pt, u64 *ct) {
     extern __shared__ u64 sm[];
     constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
@@ -236,11 +233,11 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_enc_main(const ModTab *__restr
     const size_t c = blockIdx.x / (2 * L);
     const ModTab T = mods[l];
     const int8_t *u = rnd + c * 3 * N, *e = rnd + c * 3 * N + (size_t)(1 + comp) * N;
-    const u64 *key = pk + ((size_t)comp * L + l) * 2 * N;
+    const shoup_t *key = pk + ((size_t)comp * L + l) * N;
     const u64 *m = pt + c * N;
     u64 *out = ct + ((c * 2 + comp) * L + l) * (size_t)N;
     ntt_forward<LOGN, NT>(sm, T, 0, 0, [&](int p) { return lift_small(u[p], T.q); },
-                          [&](int p, u64 v) { sm[padi(p)] = mul_shoup(v, key[p], key[N + p], T.q); });
+                          [&](int p, u64 v) { sm[padi(p)] = mul_shoup(v, key[p], T.q); });
     __syncthreads();
     ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return sm[padi(p)]; }, [&](int p, u64 v) {
         u64 r = add_mod(v, lift_small(e[p], T.q), T.q);
@@ -254,7 +251,7 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_enc_main(const ModTab *__restr
 // CTA (c, l): x_l = [c0 + c1 s]_{q_l} -> ws [count][L][N].
 template <int LOGN>
 __global__ void __launch_bounds__(nt_for(LOGN)) k_dec_inner(const ModTab *__restrict__ mods, int L,
-                                                             const u64 *__restrict__ sk_eval, const u64 *__restrict__ ct,
+                                                             const shoup_t *__restrict__ sk_eval, const u64 *__restrict__ ct,
                                                              u64 *x) {
     extern __shared__ u64 sm[];
     constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
@@ -262,9 +259,9 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_dec_inner(const ModTab *__rest
     const size_t c = blockIdx.x / L;
     const ModTab T = mods[l];
     const u64 *c0 = ct + (c * 2 * L + l) * (size_t)N, *c1 = ct + ((c * 2 + 1) * L + l) * (size_t)N;
-    const u64 *s = sk_eval + (size_t)l * 2 * N;
+    const shoup_t *s = sk_eval + (size_t)l * N;
     ntt_forward<LOGN, NT>(sm, T, 0, 0, [&](int p) { return c1[p]; },
-                          [&](int p, u64 v) { sm[padi(p)] = mul_shoup(v, s[p], s[N + p], T.q); });
+                          [&](int p, u64 v) { sm[padi(p)] = mul_shoup(v, s[p], T.q); });
     __syncthreads();
     u64 *dst = x + (c * L + l) * (size_t)N;
     ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return sm[padi(p)]; },
@@ -335,10 +332,10 @@ __global__ void k_dec_round(const ModTab *__restrict__ mods, const DecConst *__r
 }
 
 // ------------------------------------------------------------------ model weights
-// plaintext (j, k) mod t -> centred lift into q_l -> evaluation form; out [nY*K][L][2][N].
+// plaintext (j, k) mod t -> centred lift into q_l -> evaluation form; out [nY*K][L][N] {value, companion}.
 template <int LOGN>
 __global__ void __launch_bounds__(nt_for(LOGN)) k_model_weights(const ModTab *__restrict__ mods, int L, int tmod,
-                                                                 const u64 *__restrict__ pt, u64 *out) {
+                                                                 const u64 *__restrict__ pt, shoup_t *out) {
     extern __shared__ u64 sm[];
     constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
     const int l = blockIdx.x % L;
@@ -346,10 +343,10 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_model_weights(const ModTab *__
     const ModTab T = mods[l];
     const u64 t = mods[tmod].q, th = (t - 1) / 2;
     const u64 *src = pt + jk * N;
-    u64 *dst = out + (jk * L + l) * 2 * (size_t)N;
+    shoup_t *dst = out + (jk * L + l) * (size_t)N;
     ntt_forward<LOGN, NT>(sm, T, 0, 0,
                           [&](int p) { const u64 v = src[p]; return v <= th ? v : T.q - (t - v); },
-                          [&](int p, u64 v) { dst[p] = v; dst[N + p] = shoup_companion(v, T.q); });
+                          [&](int p, u64 v) { dst[p] = make_shoup(v, T.q); });
 }
 
 // ------------------------------------------------------------------ dispatch helper
@@ -369,6 +366,7 @@ int last_err() { return cudaGetLastError() == cudaSuccess ? BFV_OK : BFV_ERR_CUD
 // ====================================================================== launchers
 
 int launch_ntt_limbs(const bfv_ctx *c, const u64 *in, u64 *out, size_t nct, bool forward, cudaStream_t st) {
+    ProfScope prof_(c, BFV_K_NTT, st);
     const size_t nl = nct * 2 * c->L;
     if (!nl) return BFV_OK;
 #define L_(LG)                                                                                          \
@@ -384,6 +382,7 @@ int launch_ntt_limbs(const bfv_ctx *c, const u64 *in, u64 *out, size_t nct, bool
 }
 
 int launch_encode(const bfv_ctx *c, const int64_t *slots, size_t count, u64 *pt, cudaStream_t st) {
+    ProfScope prof_(c, BFV_K_ENCODE, st);
 #define L_(LG)                                                                                                  \
     {                                                                                                           \
         set_smem(k_encode<LG>, smem_full<LG>());                                                                \
@@ -396,6 +395,7 @@ int launch_encode(const bfv_ctx *c, const int64_t *slots, size_t count, u64 *pt,
 }
 
 int launch_decode(const bfv_ctx *c, const u64 *pt, size_t count, int64_t *slots, cudaStream_t st) {
+    ProfScope prof_(c, BFV_K_ENCODE, st);
 #define L_(LG)                                                                                                  \
     {                                                                                                           \
         set_smem(k_decode<LG>, smem_full<LG>());                                                                \
@@ -408,6 +408,7 @@ int launch_decode(const bfv_ctx *c, const u64 *pt, size_t count, int64_t *slots,
 }
 
 int launch_encode_features(const bfv_ctx *c, const uint8_t *X, size_t nX, size_t f, u64 *pt, cudaStream_t st) {
+    ProfScope prof_(c, BFV_K_ENCODE, st);
     const int K = (int)((f + c->N - 1) / c->N);
 #define L_(LG)                                                                                                 \
     {                                                                                                          \
@@ -422,6 +423,7 @@ int launch_encode_features(const bfv_ctx *c, const uint8_t *X, size_t nX, size_t
 }
 
 int launch_encode_columns(const bfv_ctx *c, const uint8_t *X, size_t nX, size_t f, u64 *pt, cudaStream_t st) {
+    ProfScope prof_(c, BFV_K_ENCODE, st);
 #define L_(LG)                                                                                                  \
     {                                                                                                           \
         set_smem(k_encode_columns<LG>, smem_full<LG>());                                                        \
@@ -480,6 +482,7 @@ int launch_keys_export(const bfv_ctx *c, const bfv_keys *k, int8_t *sk, u64 *pk,
 
 int launch_encrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *pt, size_t count, u64 seed, uint32_t obj0, u64 *ct,
                    void *ws, cudaStream_t st) {
+    ProfScope prof_(c, BFV_K_ENCRYPT, st);
     int8_t *rnd = (int8_t *)ws;
     const size_t total = count * c->N;
     k_enc_sample<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(c->dcdt, c->cdt_len, seed, obj0, c->N, total, rnd);
@@ -496,6 +499,7 @@ int launch_encrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *pt, size_t co
 }
 
 int launch_decrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *ct, size_t count, u64 *pt, void *ws, cudaStream_t st) {
+    ProfScope prof_(c, BFV_K_DECRYPT, st);
     u64 *x = (u64 *)ws;
 #define L_(LG)                                                                                              \
     {                                                                                                       \

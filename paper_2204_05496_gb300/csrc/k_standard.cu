@@ -80,6 +80,7 @@ __global__ void __launch_bounds__(256) k_standard(const ModTab *__restrict__ mod
 }  // namespace
 
 int launch_standard(const bfv_ctx *c, const bfv_model *m, const u64 *X_ct, u64 *Y_ct, cudaStream_t st) {
+    ProfScope prof_(c, BFV_K_STANDARD, st);
     const size_t ctw = 2 * (size_t)c->L * c->N;
     const unsigned blocks = (unsigned)((ctw + 255) / 256);
     for (int j0 = 0; j0 < (int)m->nY; j0 += 16) {
