@@ -62,6 +62,9 @@ def parse_args(argv=None):
     p.add_argument("--only-packed", action="store_true",
                    help="profiling case: time only the packed product on --individuals of the batch")
     p.add_argument("--individuals", type=int, default=512)
+    p.add_argument("--only-standard", action="store_true",
+                   help="profiling case: time only the standard product on the first --features features")
+    p.add_argument("--features", type=int, default=40000)
     return p.parse_args(argv)
 
 
@@ -459,13 +462,14 @@ def standard_leg(args, ctx, keys, model, X, W, b, dev, packed_step_ms, packed_la
     blk = 4000
     ews = torch.empty(ctx.encrypt_workspace(blk), dtype=torch.uint8, device=dev)
     Y = torch.empty((nY, 2, L, N), dtype=torch.int64, device=dev)
+    sws = torch.empty(ctx.standard_workspace(model), dtype=torch.uint8, device=dev)
 
     def run(seed):
         cols = ctx.encode_feature_columns(Xd)
         for f0 in range(0, f, blk):
             ctx.encrypt(keys, cols[f0:f0 + blk], seed=seed, obj0=f0, out=X_ct[f0:f0 + blk], ws=ews)
         del cols
-        ctx.lr_scores_standard(model, X_ct, nX, out=Y)
+        ctx.lr_scores_standard(model, X_ct, nX, out=Y, ws=sws)
         return ctx.decode(ctx.decrypt(keys, Y))
 
     slots = run(1)
@@ -504,7 +508,9 @@ def standard_leg(args, ctx, keys, model, X, W, b, dev, packed_step_ms, packed_la
         "packed_speedup_1_individual": round(ms / packed_lat_ms, 1),
         "encrypt_ms": round(kern["encrypt"][1] / max(1, len(times)), 2),
     }
-    del X_ct, ews
+    if ctx.check_error():
+        raise SystemExit("a bounded wait in the standard product ran out")
+    del X_ct, ews, sws
     torch.cuda.empty_cache()
     return res
 
@@ -544,12 +550,50 @@ def run_only_packed(args):
     return 0 if ok else 1
 
 
+def run_only_standard(args):
+    """Small profiling case: the standard product alone on the first --features features of the
+    batch (same parameters and kernels), --warmup untimed then --steps timed calls."""
+    import torch
+    import paper_2204_05496_gb300 as bfv
+    bfv.build()
+    torch.cuda.set_device(0)
+    w = synth.WORKLOADS[WORKLOAD]
+    X, W, b = synth.workload_inputs(w)
+    X, W = X[:, :args.features], W[:args.features]
+    N, L = w.params.N, w.params.L
+    ctx = bfv.Context.from_shape(w.params)
+    keys = ctx.keygen(w.seed_keys)
+    model = ctx.model_prepare(W, b)
+    X_ct = ctx.encrypt(keys, ctx.encode_feature_columns(torch.from_numpy(X).cuda()), seed=w.seed_enc)
+    sws = torch.empty(ctx.standard_workspace(model), dtype=torch.uint8, device="cuda")
+    Y = ctx.lr_scores_standard(model, X_ct, len(X), ws=sws)
+    for _ in range(args.warmup - 1):
+        ctx.lr_scores_standard(model, X_ct, len(X), out=Y, ws=sws)
+    torch.cuda.synchronize()
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    for _ in range(args.steps):
+        ctx.lr_scores_standard(model, X_ct, len(X), out=Y, ws=sws)
+    z.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(z) / args.steps
+    slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
+    ok = bool(np.array_equal(slots[:, :len(X)].T, (X.astype(np.int64) @ W + b[None, :]) % w.params.t))
+    ok = ok and ctx.check_error() == 0
+    gb = args.features * 2 * L * N * 8 / 1e9
+    print(json.dumps({"case": "only-standard", "features": args.features, "ms_per_call": ms,
+                      "gb_per_s": gb / (ms / 1e3), "correct": ok}), flush=True)
+    return 0 if ok else 1
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.impl == "reference":
         return run_reference(args)
     if args.only_packed:
         return run_only_packed(args)
+    if args.only_standard:
+        return run_only_standard(args)
     return run_gpu(args)
 
 

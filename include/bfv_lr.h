@@ -161,9 +161,25 @@ int bfv_lr_scores_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *mo
 
 /* Standard product (Section 5.2.3): ciphertext f of X_ct holds feature f of individual i in
  * slot i (nX <= N); output j = sum_f w[f][j] X_ct[f] + Delta [b_j]_t, weights as integer
- * scalars. X_ct: uint64[f][2][L][N]; Y_ct: uint64[nY][2][L][N]. Needs no workspace. */
+ * scalars (|w| < 2^31 and |w| f 2^ceil(bits/2) < 2^63, else BFV_ERR_BAD_PARAMS).
+ * X_ct: uint64[f][2][L][N]; Y_ct: uint64[nY][2][L][N]. ws: device workspace of at least
+ * bfv_lr_scores_standard_workspace() bytes (per-split partial sums). A bounded wait inside
+ * the streaming kernel that runs out sets the context's error word (see bfv_check_error). */
+int bfv_lr_scores_standard_workspace(const bfv_ctx *ctx, const bfv_model *model, size_t *bytes);
 int bfv_lr_scores_standard(bfv_ctx *ctx, const bfv_model *model, const uint64_t *X_ct, size_t nX,
-                           uint64_t *Y_ct, uintptr_t stream);
+                           uint64_t *Y_ct, void *ws, size_t ws_bytes, uintptr_t stream);
+
+/* Synchronises the device, returns the context's device error word in *flags (bit 0: a
+ * bounded wait in a kernel ran out) and clears it. Returns BFV_ERR_TIMEOUT if it was set. */
+int bfv_check_error(bfv_ctx *ctx, int *flags);
+
+/* Failure injection for tests (host-side switch, no fault): with what =
+ * BFV_INJECT_STREAM_STALL and value = n > 0 (a multiple of 16), the first pipeline stage of
+ * every standard-product CTA waits for n bytes that are never sent, so its bounded wait runs
+ * out after a short poll limit, the CTA drains its copies, sets the error word and returns
+ * (the output is then invalid). value = 0 turns it off. */
+#define BFV_INJECT_STREAM_STALL 1
+int bfv_debug_inject(bfv_ctx *ctx, int what, int value);
 
 /* ------------------------------------------------------------------ whole-protocol calls */
 

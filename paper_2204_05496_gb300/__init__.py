@@ -110,7 +110,10 @@ SIGNATURES = {
     "bfv_model_free": [_vp],
     "bfv_lr_scores_packed_workspace": [_vp, _vp, _sz, _sz, ctypes.POINTER(_sz)],
     "bfv_lr_scores_packed": [_vp, _vp, _vp, _vp, _sz, _vp, _vp, _sz, _sz, _up],
-    "bfv_lr_scores_standard": [_vp, _vp, _vp, _sz, _vp, _up],
+    "bfv_lr_scores_standard_workspace": [_vp, _vp, ctypes.POINTER(_sz)],
+    "bfv_lr_scores_standard": [_vp, _vp, _vp, _sz, _vp, _vp, _sz, _up],
+    "bfv_check_error": [_vp, ctypes.POINTER(ctypes.c_int)],
+    "bfv_debug_inject": [_vp, ctypes.c_int, ctypes.c_int],
     "bfv_lr_packed_pair_from_workspace": [_vp, _vp, _sz, _sz, _vp, _sz, _vp, _up],
     "bfv_launch_count": [_vp, ctypes.POINTER(_u64)],
     "bfv_lr_predict_packed_workspace": [_vp, _vp, _sz, _sz, ctypes.POINTER(_sz)],
@@ -333,11 +336,28 @@ class Context:
               _ptr(ws), ws.numel(), pair_chunk, _stream(stream))
         return Y
 
-    def lr_scores_standard(self, model: Model, X_ct, nX: int, out=None, stream=None):
+    def standard_workspace(self, model: Model) -> int:
+        n = _sz()
+        _call("bfv_lr_scores_standard_workspace", self.handle, model.handle, ctypes.byref(n))
+        return n.value
+
+    def lr_scores_standard(self, model: Model, X_ct, nX: int, out=None, ws=None, stream=None):
+        import torch
         Y = out if out is not None else self._empty_u64(model.nY, 2, self.L, self.N)
-        _call("bfv_lr_scores_standard", self.handle, model.handle, _ptr(X_ct.contiguous()), nX, _ptr(Y),
-              _stream(stream))
+        need = self.standard_workspace(model)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(max(need, 1), dtype=torch.uint8, device=X_ct.device)
+        _call("bfv_lr_scores_standard", self.handle, model.handle, _ptr(X_ct.contiguous()), nX, _ptr(Y), _ptr(ws),
+              ws.numel(), _stream(stream))
         return Y
+
+    def check_error(self) -> int:
+        """Device error word (bit 0: a bounded wait ran out); clears it. Raises BfvError on timeout."""
+        f = ctypes.c_int()
+        rc = lib().bfv_check_error(self.handle, ctypes.byref(f))
+        if rc not in (BFV_OK, BFV_ERR_TIMEOUT):
+            raise BfvError("bfv_check_error", rc)
+        return f.value
 
     def predict_workspace(self, model: Model, nX: int, pair_chunk: int = 0) -> int:
         n = _sz()

@@ -53,6 +53,9 @@ struct bfv_ctx {
     DecConst *ddec = nullptr;        // decryption constants
     std::vector<u64> galois;         // rotate-and-sum Galois elements, in order
     std::vector<u64> delta_host;     // floor(Q/t) mod q_l
+    int sms = 0;                     // streaming multiprocessors of the device
+    int *derr = nullptr;             // device error word (bounded waits that ran out set bit 0)
+    int inject_extra_tx = 0;         // failure injection: bytes a streaming stage waits for in vain
     std::atomic<uint64_t> launches{0};
     mutable Profiler prof;
 };
@@ -70,7 +73,7 @@ struct bfv_model {
     const bfv_ctx *ctx = nullptr;
     size_t f = 0, nY = 0, K = 0;
     shoup_t *w_eval = nullptr;       // [nY][K][L][N] {value, companion} (packed product)
-    int64_t *w_int = nullptr;        // [f][nY] integer weights (standard product)
+    int *w16 = nullptr;              // [ceil(nY/16)][f][16] int32 weights, zero-padded (standard product)
     u64 *bias_delta = nullptr;       // [nY][L]: Delta [b_j]_t mod q_l
     int64_t wmax = 0;                // max |w| (bounds the standard product's accumulators)
 };
@@ -134,7 +137,14 @@ int launch_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const
                   u64 *Y_ct, void *ws, const PackedPlan &plan, cudaStream_t st);
 int launch_pair_export(const bfv_ctx *c, const PackedPlan &plan, const void *ws, size_t slot_in_chunk, u64 *ct_out,
                        cudaStream_t st);
-int launch_standard(const bfv_ctx *c, const bfv_model *m, const u64 *X_ct, u64 *Y_ct, cudaStream_t st);
+struct StandardPlan {
+    size_t ntiles, splits, fper, ngroups, bytes;
+    int split_bits;
+};
+StandardPlan standard_plan(const bfv_ctx *c, const bfv_model *m);
+size_t standard_smem_bytes();
+int launch_standard(const bfv_ctx *c, const bfv_model *m, const u64 *X_ct, u64 *Y_ct, void *ws, const StandardPlan &pl,
+                    cudaStream_t st);
 
 // Threads per CTA for a transform of 2^logm points.
 constexpr int nt_for(int logm) { return logm >= 14 ? 512 : (logm == 13 ? 512 : (logm == 12 ? 256 : 128)); }

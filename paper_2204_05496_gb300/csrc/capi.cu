@@ -204,6 +204,7 @@ void free_ctx(bfv_ctx *c) {
     cudaFree(c->dmaskpow);
     cudaFree(c->dcdt);
     cudaFree(c->ddec);
+    cudaFree(c->derr);
     delete c;
 }
 
@@ -240,6 +241,7 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
     bfv_ctx *c = new (std::nothrow) bfv_ctx();
     if (!c) return BFV_ERR_OOM;
     if (cudaGetDevice(&c->device) != cudaSuccess) { delete c; return BFV_ERR_CUDA; }
+    if (cudaDeviceGetAttribute(&c->sms, cudaDevAttrMultiProcessorCount, c->device) != cudaSuccess) { delete c; return BFV_ERR_CUDA; }
     c->N = (int)p->N;
     c->logN = ilog2_h(p->N);
     c->L = (int)p->L;
@@ -366,6 +368,8 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
         for (size_t i = 0; i < s.size() && (int)i < BFV_MAXW; ++i) dc.qshift[b][i] = s[i];
     }
     if ((rc = dalloc(&c->ddec, 1))) { free_ctx(c); return rc; }
+    if ((rc = dalloc(&c->derr, 1))) { free_ctx(c); return rc; }
+    cudaMemset(c->derr, 0, sizeof(int));
     cudaMemcpy(c->ddec, &dc, sizeof dc, cudaMemcpyHostToDevice);
 
     // rotate-and-sum Galois elements: 2N-1, then 3^(N/4), ..., 3^1 mod 2N
@@ -504,7 +508,8 @@ int bfv_model_prepare(bfv_ctx *ctx, const int64_t *W, const int64_t *b, size_t f
     int rc;
     int64_t *dslots = nullptr;
     u64 *dpt = nullptr;
-    if ((rc = dalloc(&m->w_eval, nY * K * L * N)) || (rc = dalloc(&m->w_int, f * nY)) ||
+    const size_t ngroups = (nY + 15) / 16;
+    if ((rc = dalloc(&m->w_eval, nY * K * L * N)) || (rc = dalloc(&m->w16, ngroups * f * 16)) ||
         (rc = dalloc(&m->bias_delta, nY * L)) || (rc = dalloc(&dslots, nY * K * N)) || (rc = dalloc(&dpt, nY * K * N))) {
         cudaFree(dslots);
         cudaFree(dpt);
@@ -515,6 +520,11 @@ int bfv_model_prepare(bfv_ctx *ctx, const int64_t *W, const int64_t *b, size_t f
         const int64_t a = W[x] < 0 ? -W[x] : W[x];
         if (a > m->wmax) m->wmax = a;
     }
+    // 16-wide int32 weight rows for the standard product (valid when |w| < 2^31)
+    std::vector<int> w16(ngroups * f * 16, 0);
+    if (m->wmax < (1ll << 31))
+        for (size_t r = 0; r < f; ++r)
+            for (size_t j = 0; j < nY; ++j) w16[((j / 16) * f + r) * 16 + j % 16] = (int)W[r * nY + j];
     // transposed, packed weights: slot s of plaintext (j, k) = W[k N + s][j]
     std::vector<int64_t> slots(nY * K * N, 0);
     for (size_t j = 0; j < nY; ++j)
@@ -528,7 +538,7 @@ int bfv_model_prepare(bfv_ctx *ctx, const int64_t *W, const int64_t *b, size_t f
     cudaStream_t st = S(stream);
     rc = BFV_OK;
     if (cudaMemcpyAsync(dslots, slots.data(), slots.size() * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-        cudaMemcpyAsync(m->w_int, W, f * nY * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(m->w16, w16.data(), w16.size() * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(m->bias_delta, bd.data(), bd.size() * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
         rc = BFV_ERR_CUDA;
     if (!rc) rc = launch_encode(ctx, dslots, nY * K, dpt, st);
@@ -544,7 +554,7 @@ int bfv_model_prepare(bfv_ctx *ctx, const int64_t *W, const int64_t *b, size_t f
 int bfv_model_free(bfv_model *m) {
     if (!m) return BFV_ERR_INVALID_ARG;
     cudaFree(m->w_eval);
-    cudaFree(m->w_int);
+    cudaFree(m->w16);
     cudaFree(m->bias_delta);
     delete m;
     return BFV_OK;
@@ -567,13 +577,39 @@ int bfv_lr_scores_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *mo
     return launch_packed(ctx, keys, model, (const u64 *)X_ct, nX, (u64 *)Y_ct, ws, plan, S(stream));
 }
 
+int bfv_lr_scores_standard_workspace(const bfv_ctx *ctx, const bfv_model *model, size_t *bytes) {
+    if (!ctx || !model || model->ctx != ctx || !bytes) return BFV_ERR_INVALID_ARG;
+    *bytes = align256(standard_plan(ctx, model).bytes);
+    return BFV_OK;
+}
+
 int bfv_lr_scores_standard(bfv_ctx *ctx, const bfv_model *model, const uint64_t *X_ct, size_t nX, uint64_t *Y_ct,
-                           uintptr_t stream) {
+                           void *ws, size_t ws_bytes, uintptr_t stream) {
     if (!ctx || !model || model->ctx != ctx || nX > (size_t)ctx->N) return BFV_ERR_INVALID_ARG;
-    if (!X_ct || !Y_ct) return BFV_ERR_INVALID_ARG;
-    // signed 64-bit accumulators of w * (28-bit halves) stay exact while |w| f < 2^35
-    if (model->wmax >= (1ll << 31) || (double)model->wmax * (double)model->f >= 34359738368.0) return BFV_ERR_BAD_PARAMS;
-    return launch_standard(ctx, model, (const u64 *)X_ct, (u64 *)Y_ct, S(stream));
+    if (!X_ct || !Y_ct || !ws) return BFV_ERR_INVALID_ARG;
+    StandardPlan pl = standard_plan(ctx, model);
+    if (ws_bytes < pl.bytes) return BFV_ERR_OVER_BUDGET;
+    // signed 64-bit accumulators of w * (split halves) stay exact while |w| f 2^max(s, bits-s) < 2^63
+    const int wide = std::max(pl.split_bits, ctx->bits - pl.split_bits);
+    if (model->wmax >= (1ll << 31) || (long double)model->wmax * model->f * (long double)(1ull << wide) >= 9.2e18L)
+        return BFV_ERR_BAD_PARAMS;
+    return launch_standard(ctx, model, (const u64 *)X_ct, (u64 *)Y_ct, ws, pl, S(stream));
+}
+
+int bfv_debug_inject(bfv_ctx *ctx, int what, int value) {
+    if (!ctx) return BFV_ERR_INVALID_ARG;
+    if (what != BFV_INJECT_STREAM_STALL || value < 0 || value % 16) return BFV_ERR_INVALID_ARG;
+    ctx->inject_extra_tx = value;
+    return BFV_OK;
+}
+
+int bfv_check_error(bfv_ctx *ctx, int *flags) {
+    if (!ctx || !flags) return BFV_ERR_INVALID_ARG;
+    int v = 0;
+    if (cudaMemcpy(&v, ctx->derr, sizeof(int), cudaMemcpyDeviceToHost) != cudaSuccess) return BFV_ERR_CUDA;
+    if (v && cudaMemset(ctx->derr, 0, sizeof(int)) != cudaSuccess) return BFV_ERR_CUDA;
+    *flags = v;
+    return v ? BFV_ERR_TIMEOUT : BFV_OK;
 }
 
 int bfv_lr_packed_pair_from_workspace(bfv_ctx *ctx, const bfv_model *model, size_t nX, size_t pair_chunk,

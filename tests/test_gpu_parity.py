@@ -195,6 +195,30 @@ def test_standard_parity_tiny(tiny):
     assert np.array_equal(host(X_ct[999:1000]), oc)
 
 
+def test_stream_stall_reports_timeout_and_context_recovers(tiny):
+    # failure injection on the host side: the first pipeline stage waits for 16 bytes that are
+    # never sent; the bounded wait runs out, the kernel sets the error word and returns
+    ctx, keys, P, okeys = tiny
+    rng = np.random.default_rng(5)
+    X = (rng.random((4, 200)) < 0.3).astype(np.uint8)
+    W = rng.integers(-127, 128, (200, 3))
+    b = rng.integers(-127, 128, 3)
+    model = ctx.model_prepare(W, b)
+    X_ct = ctx.encrypt(keys, ctx.encode_feature_columns(dev(X).to(torch.uint8)), seed=3)
+    assert ctx.check_error() == 0
+    bfv._call("bfv_debug_inject", ctx.handle, 1, 16)
+    try:
+        ctx.lr_scores_standard(model, X_ct, 4)
+        assert ctx.check_error() & 1
+    finally:
+        bfv._call("bfv_debug_inject", ctx.handle, 1, 0)
+    Y = ctx.lr_scores_standard(model, X_ct, 4)
+    assert ctx.check_error() == 0
+    slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
+    assert np.array_equal(slots[:, :4].T, oracle.expected_scores(X, W, b, P.t))
+    assert np.array_equal(host(Y), oracle.lr_standard(P, host(X_ct), W, b))
+
+
 def test_invalid_arguments_are_rejected(tiny):
     ctx, keys, P, _ = tiny
     with pytest.raises(bfv.BfvError):
