@@ -136,6 +136,28 @@ int bfv_decrypt_workspace(const bfv_ctx *ctx, size_t count, size_t *bytes);
 int bfv_decrypt(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *ct, size_t count, uint64_t *pt,
                 void *ws, size_t ws_bytes, uintptr_t stream);
 
+/* Decryption that allocates nothing (no paper counterpart; a library convenience). Some
+ * callers cannot call cudaMalloc: it may synchronise the whole device and can fail under a
+ * fixed memory reservation, so latency-critical serving threads, code that runs while a
+ * stream is being captured into a CUDA graph, and processes whose device memory belongs to
+ * another allocator need an entry point that never allocates. This one computes exactly
+ * what bfv_decrypt computes but keeps its scratch (the per-limb residues) in a fixed 4 MiB
+ * device array inside the library, which every GPU that loads the library holds until the
+ * process exits. Limits and rules:
+ *  - count may be at most bfv_decrypt_noalloc_max_count() ciphertexts, that is
+ *    floor(4 MiB / (L N 8)) (4 at N = 16384, L = 7); larger counts return
+ *    BFV_ERR_OVER_BUDGET and nothing is launched — split the batch.
+ *  - The first call on a device resolves the array's device address (a runtime query, no
+ *    allocation); make that first call before any stream capture. The current device must be
+ *    the context's device.
+ *  - Every call shares the one array and it keeps the last call's contents. Nothing in it
+ *    needs to start at zero (each call writes every word it reads), but calls whose work
+ *    overlaps on the GPU race on it: issue them on one stream or otherwise serialise them.
+ * ct: uint64[count][2][L][N], pt: uint64[count][N], device buffers; asynchronous on `stream`. */
+int bfv_decrypt_noalloc_max_count(const bfv_ctx *ctx, size_t *count);
+int bfv_decrypt_noalloc(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *ct, size_t count, uint64_t *pt,
+                        uintptr_t stream);
+
 /* ------------------------------------------------------------------ server side */
 
 /* Encodes the model (Section 4.2.2): the transposed weights W^T as |Y| x ceil(f/N)

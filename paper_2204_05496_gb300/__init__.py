@@ -114,6 +114,8 @@ SIGNATURES = {
     "bfv_lr_scores_standard": [_vp, _vp, _vp, _sz, _vp, _vp, _sz, _up],
     "bfv_check_error": [_vp, ctypes.POINTER(ctypes.c_int)],
     "bfv_debug_inject": [_vp, ctypes.c_int, ctypes.c_int],
+    "bfv_decrypt_noalloc_max_count": [_vp, ctypes.POINTER(_sz)],
+    "bfv_decrypt_noalloc": [_vp, _vp, _vp, _sz, _vp, _up],
     "bfv_lr_packed_pair_from_workspace": [_vp, _vp, _sz, _sz, _vp, _sz, _vp, _up],
     "bfv_launch_count": [_vp, ctypes.POINTER(_u64)],
     "bfv_lr_predict_packed_workspace": [_vp, _vp, _sz, _sz, ctypes.POINTER(_sz)],

@@ -527,3 +527,69 @@ int launch_model_weights(const bfv_ctx *c, bfv_model *m, const u64 *w_pt, cudaSt
     count_launch(c);
     return last_err();
 }
+
+// ====================================================================== allocation-free decryption
+//
+// bfv_decrypt_noalloc: decryption whose scratch (the per-limb residues [c0 + c1 s]_{q_l})
+// lives in a fixed device array owned by this file instead of a caller workspace, for
+// callers that must not call cudaMalloc at all. The array is resolved to a device address
+// once per device with cudaGetSymbolAddress (host code cannot pass the symbol itself).
+
+#include <mutex>
+
+namespace {
+
+constexpr size_t kNoAllocScratchBytes = 4u << 20;   // 4 MiB, held by every device that loads the library
+static __device__ __align__(256) u64 g_noalloc_scratch[kNoAllocScratchBytes / sizeof(u64)];
+
+std::mutex g_noalloc_mu;
+u64 *g_noalloc_ptr[128] = {};   // device address of g_noalloc_scratch, per device ordinal
+
+int noalloc_scratch(int device, u64 **out) {
+    if (device < 0 || device >= 128) return BFV_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(g_noalloc_mu);
+    if (!g_noalloc_ptr[device]) {
+        void *p = nullptr;
+        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return BFV_ERR_CUDA;
+        g_noalloc_ptr[device] = (u64 *)p;
+    }
+    *out = g_noalloc_ptr[device];
+    return BFV_OK;
+}
+
+}  // namespace
+
+extern "C" int bfv_decrypt_noalloc(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *ct, size_t count, uint64_t *pt,
+                                   uintptr_t stream) {
+    if (!ctx || !keys || keys->ctx != ctx) return BFV_ERR_INVALID_ARG;
+    if (!count) return BFV_OK;
+    if (!ct || !pt) return BFV_ERR_INVALID_ARG;
+    if (count > kNoAllocScratchBytes / ((size_t)ctx->L * ctx->N * sizeof(u64))) return BFV_ERR_OVER_BUDGET;
+    int dev = -1;
+    if (cudaGetDevice(&dev) != cudaSuccess) return BFV_ERR_CUDA;
+    if (dev != ctx->device) return BFV_ERR_INVALID_ARG;
+    u64 *x = nullptr;
+    int rc = noalloc_scratch(dev, &x);
+    if (rc) return rc;
+    const bfv_ctx *c = ctx;
+    cudaStream_t st = (cudaStream_t)stream;
+    // every scratch word k_dec_round reads is written by k_dec_inner in the same call
+#define L_(LG)                                                                                                    \
+    {                                                                                                             \
+        set_smem(k_dec_inner<LG>, smem_full<LG>());                                                               \
+        k_dec_inner<LG><<<(unsigned)(count * c->L), nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->L, keys->sk_eval, \
+                                                                                        (const u64 *)ct, x);      \
+    }
+    DISPATCH_LOGN(c, L_)
+#undef L_
+    const size_t total = count * c->N;
+    k_dec_round<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(c->dmods, c->ddec, x, c->N, total, (u64 *)pt);
+    count_launch(c, 2);
+    return last_err();
+}
+
+extern "C" int bfv_decrypt_noalloc_max_count(const bfv_ctx *ctx, size_t *count) {
+    if (!ctx || !count) return BFV_ERR_INVALID_ARG;
+    *count = kNoAllocScratchBytes / ((size_t)ctx->L * ctx->N * sizeof(u64));
+    return BFV_OK;
+}
