@@ -74,6 +74,7 @@ struct bfv_model {
     size_t f = 0, nY = 0, K = 0;
     shoup_t *w_eval = nullptr;       // [nY][K][L][N] {value, companion} (packed product)
     int *w16 = nullptr;              // [ceil(nY/16)][f][16] int32 weights, zero-padded (standard product)
+    int *w4 = nullptr;               // [ceil(nY/16)][ceil(f/4)][16] four int8 weights per int32 (|w| <= 127)
     u64 *bias_delta = nullptr;       // [nY][L]: Delta [b_j]_t mod q_l
     int64_t wmax = 0;                // max |w| (bounds the standard product's accumulators)
 };
@@ -130,7 +131,7 @@ int launch_model_weights(const bfv_ctx *c, bfv_model *m, const u64 *w_pt, cudaSt
 
 struct PackedPlan {
     size_t nX, nY, K, npairs, nout, chunk;
-    size_t off_xntt, off_yacc, off_state, off_digits, off_s1, off_u, off_r, total;
+    size_t off_xntt, off_yacc, off_state, off_digits, off_u, off_r, total;
 };
 PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t chunk);
 int launch_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const u64 *X_ct, size_t nX,
@@ -140,6 +141,7 @@ int launch_pair_export(const bfv_ctx *c, const PackedPlan &plan, const void *ws,
 struct StandardPlan {
     size_t ntiles, splits, fper, ngroups, bytes;
     int split_bits;
+    bool int8;                       // byte-plane dp4a kernel (|w| <= 127)
 };
 StandardPlan standard_plan(const bfv_ctx *c, const bfv_model *m);
 size_t standard_smem_bytes();

@@ -509,7 +509,9 @@ int bfv_model_prepare(bfv_ctx *ctx, const int64_t *W, const int64_t *b, size_t f
     int64_t *dslots = nullptr;
     u64 *dpt = nullptr;
     const size_t ngroups = (nY + 15) / 16;
+    const size_t f4 = (f + 3) / 4;
     if ((rc = dalloc(&m->w_eval, nY * K * L * N)) || (rc = dalloc(&m->w16, ngroups * f * 16)) ||
+        (rc = dalloc(&m->w4, ngroups * f4 * 16)) ||
         (rc = dalloc(&m->bias_delta, nY * L)) || (rc = dalloc(&dslots, nY * K * N)) || (rc = dalloc(&dpt, nY * K * N))) {
         cudaFree(dslots);
         cudaFree(dpt);
@@ -525,6 +527,14 @@ int bfv_model_prepare(bfv_ctx *ctx, const int64_t *W, const int64_t *b, size_t f
     if (m->wmax < (1ll << 31))
         for (size_t r = 0; r < f; ++r)
             for (size_t j = 0; j < nY; ++j) w16[((j / 16) * f + r) * 16 + j % 16] = (int)W[r * nY + j];
+    // four consecutive features' int8 weights per int32 (byte u = feature 4i + u), per class
+    std::vector<int> w4(ngroups * f4 * 16, 0);
+    if (m->wmax <= 127)
+        for (size_t r = 0; r < f; ++r)
+            for (size_t j = 0; j < nY; ++j) {
+                const uint32_t byte = (uint32_t)(uint8_t)(int8_t)W[r * nY + j];
+                w4[((j / 16) * f4 + r / 4) * 16 + j % 16] |= (int)(byte << (8 * (r % 4)));
+            }
     // transposed, packed weights: slot s of plaintext (j, k) = W[k N + s][j]
     std::vector<int64_t> slots(nY * K * N, 0);
     for (size_t j = 0; j < nY; ++j)
@@ -539,6 +549,7 @@ int bfv_model_prepare(bfv_ctx *ctx, const int64_t *W, const int64_t *b, size_t f
     rc = BFV_OK;
     if (cudaMemcpyAsync(dslots, slots.data(), slots.size() * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(m->w16, w16.data(), w16.size() * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(m->w4, w4.data(), w4.size() * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(m->bias_delta, bd.data(), bd.size() * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
         rc = BFV_ERR_CUDA;
     if (!rc) rc = launch_encode(ctx, dslots, nY * K, dpt, st);
@@ -555,6 +566,7 @@ int bfv_model_free(bfv_model *m) {
     if (!m) return BFV_ERR_INVALID_ARG;
     cudaFree(m->w_eval);
     cudaFree(m->w16);
+    cudaFree(m->w4);
     cudaFree(m->bias_delta);
     delete m;
     return BFV_OK;

@@ -53,11 +53,10 @@ __global__ void __launch_bounds__(256) k_mac(const ModTab *__restrict__ mods, in
 
 // ------------------------------------------------------------------ key switching
 
-// grid.x = (g, c, l). c = 1: digit D[g][l] = INTT(sigma(C1[g][l])), and S1[g][l] = sigma(C1[g][l])
-// in evaluation form; c = 0: C0 += sigma(C0).
+// grid.x = (g, c, l). c = 1: digit D[g][l] = INTT(sigma(C1[g][l])); c = 0: C0 += sigma(C0).
 template <int LOGN>
 __global__ void __launch_bounds__(nt_for(LOGN)) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 gal, u64 *C,
-                                                           u64 *D, u64 *S1) {
+                                                           u64 *D) {
     extern __shared__ u64 sm[];
     constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
     const int l = blockIdx.x % L, c = (blockIdx.x / L) % 2;
@@ -65,9 +64,8 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_ks_prep(const ModTab *__restri
     const ModTab T = mods[l];
     u64 *limb = C + ((g * 2 + c) * L + l) * (size_t)N;
     if (c == 1) {
-        u64 *dst = D + (g * L + l) * (size_t)N, *s1 = S1 + (g * L + l) * (size_t)N;
-        ntt_inverse<LOGN, NT>(sm, T,
-                              [&](int p) { const u64 v = limb[auto_src(p, gal, LOGN)]; s1[p] = v; return v; },
+        u64 *dst = D + (g * L + l) * (size_t)N;
+        ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return limb[auto_src(p, gal, LOGN)]; },
                               [&](int p, u64 v) { dst[p] = v; });
     } else {
         for (int p = threadIdx.x; p < N; p += NT) sm[p] = limb[p];
@@ -103,10 +101,10 @@ __device__ __forceinline__ void key_mac(u64 *acc0, u64 *acc1, const shoup_t *__r
 }
 
 // grid.x = (g, j, h): U[g][c][j][h N/2 + p] = sum_i NTT_j(D[g][i] mod q_j)[h N/2 + p] * key[i][c][j].
-// The digit of index j itself is sigma(C1[g][j]) in evaluation form already (S1).
+// The digit of index j itself is sigma(C1[g][j]) in evaluation form already (a permuted read).
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN - 1)) k_ks_modup(const ModTab *__restrict__ mods, int L,
-                                                                const u64 *__restrict__ S1, const u64 *__restrict__ D,
+__global__ void __launch_bounds__(nt_for(LOGN - 1)) k_ks_modup(const ModTab *__restrict__ mods, int L, u32 gal,
+                                                                const u64 *__restrict__ C, const u64 *__restrict__ D,
                                                                 const shoup_t *__restrict__ key, u64 *U) {
     extern __shared__ u64 sm[];
     constexpr int N = 1 << LOGN, H = N / 2, NT = nt_for(LOGN - 1);
@@ -124,8 +122,8 @@ __global__ void __launch_bounds__(nt_for(LOGN - 1)) k_ks_modup(const ModTab *__r
         const shoup_t *k0 = key + ((size_t)i * 2 + 0) * keystride + (size_t)j * N + (size_t)h * H;
         const shoup_t *k1 = key + ((size_t)i * 2 + 1) * keystride + (size_t)j * N + (size_t)h * H;
         if (i == j) {
-            const u64 *s1 = S1 + (g * L + j) * (size_t)N + (size_t)h * H;
-            key_mac<H, NT>(acc0, acc1, k0, k1, q, q2, [&](int p) { return s1[p]; });
+            const u64 *c1 = C + ((g * 2 + 1) * L + j) * (size_t)N;
+            key_mac<H, NT>(acc0, acc1, k0, k1, q, q2, [&](int p) { return c1[auto_src(h * H + p, gal, LOGN)]; });
         } else {
             const u64 *d = D + (g * L + i) * (size_t)N;
             ntt_forward<LOGN - 1, NT>(
@@ -273,7 +271,6 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const u6
     const size_t ctw = 2 * (size_t)L * N;
     u64 *Xe = (u64 *)(ws + pl.off_xntt), *Yacc = (u64 *)(ws + pl.off_yacc), *C = (u64 *)(ws + pl.off_state);
     u64 *D = (u64 *)(ws + pl.off_digits), *U = (u64 *)(ws + pl.off_u), *R = (u64 *)(ws + pl.off_r);
-    u64 *S1 = (u64 *)(ws + pl.off_s1);
     const size_t full = pad_bytes<N>(), half = pad_bytes<N / 2>() + 2 * sizeof(u64) * (N / 2);
     set_smem(k_ks_prep<LOGN>, full);
     set_smem(k_ks_modup<LOGN>, half);
@@ -295,9 +292,9 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const u6
             const u32 gal = (u32)c->galois[s];
             const shoup_t *key = k->gk_eval + (size_t)s * keyblock;
             { ProfScope pr(c, BFV_K_KS_PREP, st);
-              k_ks_prep<LOGN><<<(unsigned)(ng * 2 * L), nt_for(LOGN), full, st>>>(c->dmods, L, gal, C, D, S1); }
+              k_ks_prep<LOGN><<<(unsigned)(ng * 2 * L), nt_for(LOGN), full, st>>>(c->dmods, L, gal, C, D); }
             { ProfScope pr(c, BFV_K_KS_MODUP, st);
-              k_ks_modup<LOGN><<<(unsigned)(ng * nqp * 2), nt_for(LOGN - 1), half, st>>>(c->dmods, L, S1, D, key, U); }
+              k_ks_modup<LOGN><<<(unsigned)(ng * nqp * 2), nt_for(LOGN - 1), half, st>>>(c->dmods, L, gal, C, D, key, U); }
             { ProfScope pr(c, BFV_K_KS_MODDOWN_P, st);
               k_ks_moddown_p<LOGN><<<(unsigned)(ng * 2), nt_for(LOGN), full, st>>>(c->dmods, L, U, R); }
             { ProfScope pr(c, BFV_K_KS_MODDOWN, st);
@@ -338,7 +335,6 @@ PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t c
     p.off_yacc = off; off += al256(p.nout * ctb);
     p.off_state = off; off += al256(p.chunk * ctb);
     p.off_digits = off; off += al256(p.chunk * L * N * sizeof(u64));
-    p.off_s1 = off; off += al256(p.chunk * L * N * sizeof(u64));
     p.off_u = off; off += al256(p.chunk * 2 * nqp * N * sizeof(u64));
     p.off_r = off; off += al256(p.chunk * 2 * N * sizeof(u64));
     p.total = off;

@@ -100,6 +100,146 @@ __global__ void __launch_bounds__(kE, 2) k_standard_stream(const int *__restrict
     for (int j = 0; j < kNY; ++j) out[(size_t)j * ctw] = make_longlong2(lo[j], hi[j]);
 }
 
+// ------------------------------------------------------------------ int8 weights: byte planes + dp4a
+//
+// For |w| <= 127 the product is formed byte by byte: x = sum_k 2^(8k) x_k, and for four
+// features at a time the bytes x_k of the four residues are packed into one 32-bit word
+// (PRMT) and dotted with the four features' int8 weights by one dp4a (4 multiply-adds per
+// instruction). Each thread keeps one int32 accumulator per (class, byte plane) for 8 of
+// the 16 classes (two threads per ciphertext word); an accumulator grows by at most
+// 4 * 255 * 127 per dp4a, so a split may hold up to 65,536 features. The planes are folded
+// into (lo, hi) = (sum_{k<4} 2^(8k) acc_k, sum_{k>=4} 2^(8(k-4)) acc_k), i.e. split at 32 bits.
+
+constexpr int kE8 = 128;                  // ciphertext words per CTA tile (two threads per word)
+constexpr int kS8 = 4;                    // stages in flight
+
+struct Std8Smem {
+    u64 x[kS8][kF][kE8];
+    int w[kS8][kF / 4][kNY];               // four features' int8 weights per int32, per class
+    u64 full[kS8];                         // copies of a stage landed
+    u64 empty[kS8];                        // every warp is done with a stage
+};
+
+__device__ __forceinline__ int dp4a_us(u32 a, int b, int c) {
+    int d;
+    asm("dp4a.u32.s32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+    return d;
+}
+__device__ __forceinline__ u32 prmt(u32 a, u32 b, u32 sel) {
+    u32 d;
+    asm("prmt.b32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(sel));
+    return d;
+}
+// Byte planes 4q .. 4q+3 of four 32-bit halves a0..a3: plane k holds byte k of a0, a1, a2, a3.
+__device__ __forceinline__ void planes4(u32 a0, u32 a1, u32 a2, u32 a3, u32 (&p)[4]) {
+    const u32 t01 = prmt(a0, a1, 0x5140u), t23 = prmt(a2, a3, 0x5140u);   // bytes 0, 1
+    const u32 u01 = prmt(a0, a1, 0x7362u), u23 = prmt(a2, a3, 0x7362u);   // bytes 2, 3
+    p[0] = prmt(t01, t23, 0x5410u);
+    p[1] = prmt(t01, t23, 0x7632u);
+    p[2] = prmt(u01, u23, 0x5410u);
+    p[3] = prmt(u01, u23, 0x7632u);
+}
+
+template <int NP>
+__global__ void __launch_bounds__(2 * kE8 + 32, 2) k_standard_dp4a(const int *__restrict__ W4, const u64 *__restrict__ X,
+                                                                   size_t ctw, size_t F, size_t fper,
+                                                                   longlong2 *partial, int *err, u32 extra_tx,
+                                                                   long long wait_limit) {
+    extern __shared__ __align__(128) unsigned char raw[];
+    Std8Smem &s = *reinterpret_cast<Std8Smem *>(raw);
+    constexpr int kConsumers = 2 * kE8;                 // warps 0..7 compute, warp 8 copies
+    const size_t ntiles = ctw / kE8;
+    const size_t tile = blockIdx.x % ntiles, split = blockIdx.x / ntiles;
+    const size_t e0 = tile * kE8;
+    const size_t fa = split * fper, fb = std::min(F, fa + fper);
+    const int nst = fa < fb ? (int)((fb - fa + kF - 1) / kF) : 0;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        for (int i = 0; i < kS8; ++i) {
+            mbar_init(&s.full[i], 1);
+            mbar_init(&s.empty[i], kConsumers / 32);
+        }
+        mbar_init_fence();
+    }
+    __syncthreads();
+    bool failed = false;
+    if (tid >= kConsumers) {
+        // producer warp: lane 0 streams the stages, refilling a slot once every consumer warp let go
+        if (tid == kConsumers) {
+            int st = 0;
+            for (; st < nst; ++st) {
+                const int slot = st % kS8;
+                if (st >= kS8 && !mbar_wait(&s.empty[slot], (u32)(((st - kS8) / kS8) & 1), wait_limit)) {
+                    failed = true;
+                    break;
+                }
+                const size_t f0 = fa + (size_t)st * kF;
+                const int nf = (int)std::min((size_t)kF, fb - f0);
+                const int ng = (nf + 3) / 4;
+                mbar_expect_tx(&s.full[slot], (u32)nf * (kE8 * 8) + (u32)ng * kNY * 4 + (st == 0 ? extra_tx : 0u));
+                for (int ff = 0; ff < nf; ++ff)
+                    bulk_g2s(&s.x[slot][ff][0], X + (f0 + ff) * ctw + e0, kE8 * 8, &s.full[slot]);
+                bulk_g2s(&s.w[slot][0][0], W4 + (f0 / 4) * kNY, (u32)ng * kNY * 4, &s.full[slot]);
+            }
+            // drain: the last stages issued may still be landing
+            for (int k = st > kS8 ? st - kS8 : 0; k < st; ++k) mbar_wait(&s.full[k % kS8], (u32)((k / kS8) & 1), wait_limit);
+        }
+    } else {
+        const int ew = tid % kE8, jh = tid / kE8;          // word, class half
+        int acc[8][NP];
+#pragma unroll
+        for (int j = 0; j < 8; ++j)
+#pragma unroll
+            for (int k = 0; k < NP; ++k) acc[j][k] = 0;
+        for (int st = 0; st < nst; ++st) {
+            const int slot = st % kS8;
+            if (!mbar_wait(&s.full[slot], (u32)((st / kS8) & 1), wait_limit)) {
+                failed = true;
+                break;
+            }
+            const size_t f0 = fa + (size_t)st * kF;
+            const int nf = (int)std::min((size_t)kF, fb - f0);
+            for (int g4 = 0; g4 < (nf + 3) / 4; ++g4) {
+                u64 x[4];
+#pragma unroll
+                for (int u = 0; u < 4; ++u) x[u] = (g4 * 4 + u < nf) ? s.x[slot][g4 * 4 + u][ew] : 0ull;
+                u32 pl[8];
+                {
+                    u32 lo4[4], hi4[4];
+                    planes4((u32)x[0], (u32)x[1], (u32)x[2], (u32)x[3], lo4);
+                    planes4((u32)(x[0] >> 32), (u32)(x[1] >> 32), (u32)(x[2] >> 32), (u32)(x[3] >> 32), hi4);
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) { pl[k] = lo4[k]; pl[4 + k] = hi4[k]; }
+                }
+                const int4 *wv = reinterpret_cast<const int4 *>(&s.w[slot][g4][jh * 8]);
+                const int4 wa = wv[0], wb = wv[1];
+                const int ws[8] = {wa.x, wa.y, wa.z, wa.w, wb.x, wb.y, wb.z, wb.w};
+#pragma unroll
+                for (int j = 0; j < 8; ++j)
+#pragma unroll
+                    for (int k = 0; k < NP; ++k) acc[j][k] = dp4a_us(pl[k], ws[j], acc[j][k]);
+            }
+            __syncwarp();
+            if ((tid & 31) == 0) mbar_arrive(&s.empty[slot]);
+        }
+        if (!failed) {
+            longlong2 *out = partial + (split * kNY + jh * 8) * ctw + e0 + ew;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                long long lo = 0, hi = 0;
+#pragma unroll
+                for (int k = 0; k < NP; ++k) {
+                    if (k < 4) lo += (long long)acc[j][k] * (1ll << (8 * k));
+                    else hi += (long long)acc[j][k] * (1ll << (8 * (k - 4)));
+                }
+                out[(size_t)j * ctw] = make_longlong2(lo, hi);
+            }
+        }
+    }
+    // a bounded wait ran out somewhere: report it (the output of this launch is invalid)
+    if (__syncthreads_or(failed) && tid == 0) atomicOr(err, 1);
+}
+
 // Y[j0 + j][e] = (sum over splits of hi 2^s + lo) mod q + Delta [b]_t at coefficient 0 of c0.
 __global__ void __launch_bounds__(256) k_standard_finalize(const ModTab *__restrict__ mods, int N, int L, size_t ctw,
                                                            int splits, int nj, int j0, int split_bits,
@@ -131,14 +271,16 @@ __global__ void __launch_bounds__(256) k_standard_finalize(const ModTab *__restr
 StandardPlan standard_plan(const bfv_ctx *c, const bfv_model *m) {
     StandardPlan p{};
     const size_t ctw = 2 * (size_t)c->L * c->N;
-    p.ntiles = ctw / kE;
+    p.int8 = m->wmax <= 127 && c->bits <= 64;
+    p.ntiles = ctw / (p.int8 ? kE8 : kE);
     const size_t target = (size_t)c->sms * 2 * 6;    // about six waves of two CTAs per SM
     size_t splits = std::max<size_t>(1, (target + p.ntiles - 1) / p.ntiles);
     splits = std::min<size_t>(splits, std::max<size_t>(1, (m->f + 4 * kF - 1) / (4 * kF)));
+    if (p.int8) splits = std::max<size_t>(splits, (m->f + 65535) / 65536);   // int32 plane accumulators
     p.fper = ((m->f + splits - 1) / splits + kF - 1) / kF * kF;
     p.splits = (m->f + p.fper - 1) / p.fper;
     p.ngroups = (m->nY + kNY - 1) / kNY;
-    p.split_bits = (c->bits + 1) / 2;
+    p.split_bits = p.int8 ? 32 : (c->bits + 1) / 2;
     p.bytes = p.splits * kNY * ctw * sizeof(longlong2);
     return p;
 }
@@ -151,11 +293,33 @@ int launch_standard(const bfv_ctx *c, const bfv_model *m, const u64 *X_ct, u64 *
     const size_t ctw = 2 * (size_t)c->L * c->N;
     cudaFuncSetAttribute(k_standard_stream, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(StdSmem));
     longlong2 *partial = (longlong2 *)ws;
+    const int np = (c->bits + 7) / 8;
+    const long long limit = c->inject_extra_tx ? (1ll << 12) : kWaitLimit;
     for (size_t gi = 0; gi < pl.ngroups; ++gi) {
         const int j0 = (int)(gi * kNY), nj = (int)std::min<size_t>(kNY, m->nY - j0);
-        k_standard_stream<<<(unsigned)(pl.ntiles * pl.splits), kE, sizeof(StdSmem), st>>>(
-            m->w16 + gi * m->f * kNY, X_ct, ctw, m->f, pl.fper, pl.split_bits, partial, c->derr,
-            (u32)c->inject_extra_tx, c->inject_extra_tx ? (1ll << 12) : kWaitLimit);
+        const unsigned grid = (unsigned)(pl.ntiles * pl.splits);
+        if (pl.int8) {
+            const int *w4 = m->w4 + gi * ((m->f + 3) / 4) * kNY;
+#define STD8(NP)                                                                                                   \
+    {                                                                                                              \
+        cudaFuncSetAttribute(k_standard_dp4a<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(Std8Smem)); \
+        k_standard_dp4a<NP><<<grid, 2 * kE8 + 32, sizeof(Std8Smem), st>>>(w4, X_ct, ctw, m->f, pl.fper, partial,    \
+                                                                        c->derr,                                  \
+                                                                        (u32)c->inject_extra_tx, limit);          \
+    }
+            switch (np) {
+                case 4: STD8(4); break;
+                case 5: STD8(5); break;
+                case 6: STD8(6); break;
+                case 7: STD8(7); break;
+                default: STD8(8); break;
+            }
+#undef STD8
+        } else {
+            k_standard_stream<<<grid, kE, sizeof(StdSmem), st>>>(m->w16 + gi * m->f * kNY, X_ct, ctw, m->f, pl.fper,
+                                                                pl.split_bits, partial, c->derr,
+                                                                (u32)c->inject_extra_tx, limit);
+        }
         const size_t n = (size_t)nj * ctw;
         k_standard_finalize<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(c->dmods, c->N, c->L, ctw, (int)pl.splits, nj, j0,
                                                                          pl.split_bits, partial, m->bias_delta, Y_ct);

@@ -195,6 +195,22 @@ def test_standard_parity_tiny(tiny):
     assert np.array_equal(host(X_ct[999:1000]), oc)
 
 
+def test_standard_wide_weights_parity(tiny):
+    # weights outside the int8 range take the 32 x 32 -> 64 multiply-add kernel
+    ctx, keys, P, okeys = tiny
+    rng = np.random.default_rng(6)
+    X = (rng.random((9, 300)) < 0.3).astype(np.uint8)
+    W = rng.integers(-3000, 3001, (300, 19))                   # 19 classes: two class groups
+    b = rng.integers(-3000, 3001, 19)
+    model = ctx.model_prepare(W, b)
+    X_ct = ctx.encrypt(keys, ctx.encode_feature_columns(dev(X).to(torch.uint8)), seed=4)
+    Y = ctx.lr_scores_standard(model, X_ct, 9)
+    assert ctx.check_error() == 0
+    assert np.array_equal(host(Y), oracle.lr_standard(P, host(X_ct), W, b))
+    slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
+    assert np.array_equal(slots[:, :9].T, oracle.expected_scores(X, W, b, P.t))
+
+
 def test_stream_stall_reports_timeout_and_context_recovers(tiny):
     # failure injection on the host side: the first pipeline stage waits for 16 bytes that are
     # never sent; the bounded wait runs out, the kernel sets the error word and returns
