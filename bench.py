@@ -59,6 +59,7 @@ def parse_args(argv=None):
     p.add_argument("--latency-reps", type=int, default=20)
     p.add_argument("--no-standard", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--sweep", action="store_true", help="also time the server product at several pair chunks")
     p.add_argument("--only-packed", action="store_true",
                    help="profiling case: time only the packed product on --individuals of the batch")
     p.add_argument("--individuals", type=int, default=512)
@@ -390,7 +391,31 @@ def gpu_extras(args, ctx, keys, model, X, W, b, ws, chunk, dev, kern, step_ms):
     torch.cuda.synchronize()
     sms = a.elapsed_time(z) / reps
     out["server_only"] = {"ms": round(sms, 2), "predictions_per_s": round(nX / (sms / 1e3), 1)}
-    del pws, Y, X_ct, pt
+    # the same product replayed from a CUDA graph (one host call per product)
+    ctx.lr_scores_packed_graph(keys, model, X_ct, out=Y, ws=pws, pair_chunk=chunk)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(reps):
+        ctx.lr_scores_packed_graph(keys, model, X_ct, out=Y, ws=pws, pair_chunk=chunk)
+    z.record()
+    torch.cuda.synchronize()
+    out["server_only"]["graph_ms"] = round(a.elapsed_time(z) / reps, 2)
+    if args.sweep:
+        del pws
+        sweep = {}
+        for ch in (512, 1024, 2048, 4096, 8192):
+            sw = torch.empty(ctx.packed_workspace(model, nX, ch), dtype=torch.uint8, device=dev)
+            ctx.lr_scores_packed(keys, model, X_ct, out=Y, ws=sw, pair_chunk=ch)
+            a.record()
+            ctx.lr_scores_packed(keys, model, X_ct, out=Y, ws=sw, pair_chunk=ch)
+            z.record()
+            torch.cuda.synchronize()
+            sweep[ch] = round(a.elapsed_time(z), 1)
+            del sw
+        out["server_only"]["chunk_sweep_ms"] = sweep
+    else:
+        del pws
+    del Y, X_ct, pt
 
     # end to end through the C ABI with host buffers
     Xh = torch.from_numpy(X).pin_memory()
@@ -421,6 +446,24 @@ def gpu_extras(args, ctx, keys, model, X, W, b, ws, chunk, dev, kern, step_ms):
         torch.cuda.synchronize()
         if i >= 3:
             lat.append(a.elapsed_time(z))
+    # the server product alone for one individual, launched directly and from a graph
+    pt1 = ctx.encode_features(X1d)
+    X1_ct = ctx.encrypt(k1, pt1.reshape(-1, lw.params.N), seed=lw.seed_enc).reshape(1, m1.K, 2, lw.params.L, lw.params.N)
+    pw1 = torch.empty(ctx.packed_workspace(m1, 1, 0), dtype=torch.uint8, device=dev)
+    Y1 = ctx.lr_scores_packed(k1, m1, X1_ct, ws=pw1)
+    srv = {}
+    for name, fn in (("direct", ctx.lr_scores_packed), ("graph", ctx.lr_scores_packed_graph)):
+        fn(k1, m1, X1_ct, out=Y1, ws=pw1)
+        ts = []
+        for _ in range(10):
+            a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn(k1, m1, X1_ct, out=Y1, ws=pw1)
+            z.record()
+            torch.cuda.synchronize()
+            ts.append(a.elapsed_time(z))
+        srv[name] = round(sorted(ts)[len(ts) // 2], 3)
+    del pw1, Y1, X1_ct, pt1
     want1 = (X1.astype(np.int64) @ W1 + b1[None, :]) % lw.params.t
     assert np.array_equal(s1.cpu().numpy(), want1)
     X1h = torch.from_numpy(X1).pin_memory()
@@ -436,6 +479,7 @@ def gpu_extras(args, ctx, keys, model, X, W, b, ws, chunk, dev, kern, step_ms):
     out["latency_1_individual"] = {
         "p50_ms": round(lat[len(lat) // 2], 3), "p99_ms": round(lat[min(len(lat) - 1, int(0.99 * len(lat)))], 3),
         "e2e_p50_ms": round(lat_e2e[len(lat_e2e) // 2], 3), "reps": len(lat),
+        "server_product_p50_ms": srv,
         "workload": f"{LATENCY_WORKLOAD}: 1 individual x {lw.n_features} features x {lw.n_classes} classes, same BFV parameters"}
     del ws1
 

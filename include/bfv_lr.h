@@ -181,6 +181,25 @@ int bfv_lr_scores_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *mo
                          size_t nX, uint64_t *Y_ct, void *ws, size_t ws_bytes, size_t pair_chunk,
                          uintptr_t stream);
 
+/* The same product replayed from a CUDA graph: the first call with a given set of arguments
+ * (handles, pointers, sizes, chunk, stream) captures every launch of bfv_lr_scores_packed
+ * into a graph and later calls launch the instantiated graph, so the host issues one call
+ * per product. Same results and workspace as bfv_lr_scores_packed. While per-kernel
+ * profiling is on (bfv_profile) it launches directly instead. Not thread-safe against
+ * concurrent calls on the same stream; the first call must not run inside another capture. */
+int bfv_lr_scores_packed_graph(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint64_t *X_ct,
+                               size_t nX, uint64_t *Y_ct, void *ws, size_t ws_bytes, size_t pair_chunk,
+                               uintptr_t stream);
+
+/* Autotuner for the packed product's pair chunk (how many pairs are in flight at once):
+ * runs the product on the caller's inputs for chunk sizes 128 .. 16384 that fit in ws_bytes,
+ * times each with CUDA events after a warm-up run, and records the fastest for this number
+ * of pairs in the context; later calls and workspace queries with pair_chunk = 0 use it
+ * (size workspaces after tuning). Y_ct receives the product. Synchronises `stream`. */
+int bfv_autotune_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint64_t *X_ct, size_t nX,
+                        uint64_t *Y_ct, void *ws, size_t ws_bytes, uintptr_t stream, size_t *best_chunk,
+                        double *best_ms);
+
 /* Standard product (Section 5.2.3): ciphertext f of X_ct holds feature f of individual i in
  * slot i (nX <= N); output j = sum_f w[f][j] X_ct[f] + Delta [b_j]_t, weights as integer
  * scalars (|w| < 2^31 and |w| f 2^ceil(bits/2) < 2^63, else BFV_ERR_BAD_PARAMS).

@@ -115,6 +115,9 @@ SIGNATURES = {
     "bfv_check_error": [_vp, ctypes.POINTER(ctypes.c_int)],
     "bfv_debug_inject": [_vp, ctypes.c_int, ctypes.c_int],
     "bfv_decrypt_noalloc_max_count": [_vp, ctypes.POINTER(_sz)],
+    "bfv_lr_scores_packed_graph": [_vp, _vp, _vp, _vp, _sz, _vp, _vp, _sz, _sz, _up],
+    "bfv_autotune_packed": [_vp, _vp, _vp, _vp, _sz, _vp, _vp, _sz, _up, ctypes.POINTER(_sz),
+                            ctypes.POINTER(ctypes.c_double)],
     "bfv_decrypt_noalloc": [_vp, _vp, _vp, _sz, _vp, _up],
     "bfv_lr_packed_pair_from_workspace": [_vp, _vp, _sz, _sz, _vp, _sz, _vp, _up],
     "bfv_launch_count": [_vp, ctypes.POINTER(_u64)],
@@ -342,6 +345,31 @@ class Context:
         n = _sz()
         _call("bfv_lr_scores_standard_workspace", self.handle, model.handle, ctypes.byref(n))
         return n.value
+
+    def lr_scores_packed_graph(self, keys: Keys, model: Model, X_ct, out=None, ws=None, pair_chunk: int = 0,
+                               stream=None):
+        """lr_scores_packed replayed from a cached CUDA graph (one host call per product)."""
+        import torch
+        nX = X_ct.shape[0]
+        nout = -(-nX * model.nY // self.N)
+        Y = out if out is not None else self._empty_u64(nout, 2, self.L, self.N)
+        need = self.packed_workspace(model, nX, pair_chunk)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=X_ct.device)
+        _call("bfv_lr_scores_packed_graph", self.handle, keys.handle, model.handle, _ptr(X_ct.contiguous()), nX,
+              _ptr(Y), _ptr(ws), ws.numel(), pair_chunk, _stream(stream))
+        return Y
+
+    def autotune_packed(self, keys: Keys, model: Model, X_ct, ws, out=None, stream=None):
+        """Times pair-chunk sizes that fit in `ws` and makes the fastest the default for this
+        number of pairs. Returns (chunk, ms)."""
+        nX = X_ct.shape[0]
+        nout = -(-nX * model.nY // self.N)
+        Y = out if out is not None else self._empty_u64(nout, 2, self.L, self.N)
+        ch, ms = _sz(), ctypes.c_double()
+        _call("bfv_autotune_packed", self.handle, keys.handle, model.handle, _ptr(X_ct.contiguous()), nX, _ptr(Y),
+              _ptr(ws), ws.numel(), _stream(stream), ctypes.byref(ch), ctypes.byref(ms))
+        return ch.value, ms.value
 
     def lr_scores_standard(self, model: Model, X_ct, nX: int, out=None, ws=None, stream=None):
         import torch

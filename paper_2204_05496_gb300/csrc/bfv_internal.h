@@ -4,7 +4,9 @@
 #include <cstdint>
 #include <vector>
 #include <atomic>
+#include <map>
 #include <mutex>
+#include <tuple>
 #include <utility>
 #include <cuda_runtime.h>
 
@@ -56,6 +58,12 @@ struct bfv_ctx {
     int sms = 0;                     // streaming multiprocessors of the device
     int *derr = nullptr;             // device error word (bounded waits that ran out set bit 0)
     int inject_extra_tx = 0;         // failure injection: bytes a streaming stage waits for in vain
+    std::map<size_t, size_t> tuned_chunk;   // pairs -> pair chunk chosen by bfv_autotune_packed
+    // CUDA graphs of whole packed products, keyed by every argument of the call
+    typedef std::tuple<const void *, const void *, const void *, size_t, void *, void *, size_t, cudaStream_t> GraphKey;
+    std::map<GraphKey, std::pair<cudaGraphExec_t, uint64_t>> graphs;   // exec, kernel launches it holds
+    std::mutex graph_mu;
+    cudaStream_t capture_stream = nullptr;   // graphs are captured here, then launched on the caller's stream
     std::atomic<uint64_t> launches{0};
     mutable Profiler prof;
 };

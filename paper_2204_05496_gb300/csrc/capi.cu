@@ -198,6 +198,8 @@ void free_ctx(bfv_ctx *c) {
     for (auto &v : c->prof.pending)
         for (auto &pr : v) { cudaEventDestroy(pr.first); cudaEventDestroy(pr.second); }
     for (auto e : c->prof.pool) cudaEventDestroy(e);
+    for (auto &kv : c->graphs) cudaGraphExecDestroy(kv.second.first);
+    if (c->capture_stream) cudaStreamDestroy(c->capture_stream);
     cudaFree(c->dmods);
     cudaFree(c->dtw);
     cudaFree(c->dslot);
@@ -587,6 +589,87 @@ int bfv_lr_scores_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *mo
     PackedPlan plan = packed_plan(ctx, model, nX, pair_chunk);
     if (ws_bytes < plan.total) return BFV_ERR_OVER_BUDGET;
     return launch_packed(ctx, keys, model, (const u64 *)X_ct, nX, (u64 *)Y_ct, ws, plan, S(stream));
+}
+
+int bfv_lr_scores_packed_graph(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint64_t *X_ct,
+                               size_t nX, uint64_t *Y_ct, void *ws, size_t ws_bytes, size_t pair_chunk,
+                               uintptr_t stream) {
+    if (!ctx || !keys || !model || keys->ctx != ctx || model->ctx != ctx) return BFV_ERR_INVALID_ARG;
+    if (nX == 0) return BFV_OK;
+    if (!X_ct || !Y_ct || !ws) return BFV_ERR_INVALID_ARG;
+    PackedPlan plan = packed_plan(ctx, model, nX, pair_chunk);
+    if (ws_bytes < plan.total) return BFV_ERR_OVER_BUDGET;
+    cudaStream_t st = S(stream);
+    if (ctx->prof.on)   // per-launch event timing needs direct launches
+        return launch_packed(ctx, keys, model, (const u64 *)X_ct, nX, (u64 *)Y_ct, ws, plan, st);
+    bfv_ctx::GraphKey key(keys, model, X_ct, nX, Y_ct, ws, plan.chunk, st);
+    std::lock_guard<std::mutex> g(ctx->graph_mu);
+    auto it = ctx->graphs.find(key);
+    if (it == ctx->graphs.end()) {
+        if (ctx->graphs.size() >= 64) {   // bounded cache: drop everything and start over
+            for (auto &kv : ctx->graphs) cudaGraphExecDestroy(kv.second.first);
+            ctx->graphs.clear();
+        }
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        // capture on a context-owned stream (the caller's may be the uncapturable legacy stream)
+        if (!ctx->capture_stream &&
+            cudaStreamCreateWithFlags(&ctx->capture_stream, cudaStreamNonBlocking) != cudaSuccess)
+            return BFV_ERR_CUDA;
+        cudaStream_t cs = ctx->capture_stream;
+        const uint64_t before = ctx->launches.load();
+        if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BFV_ERR_CUDA;
+        int rc = launch_packed(ctx, keys, model, (const u64 *)X_ct, nX, (u64 *)Y_ct, ws, plan, cs);
+        const uint64_t held = ctx->launches.load() - before;
+        ctx->launches.fetch_sub(held);     // counted when the graph runs
+        cudaError_t e = cudaStreamEndCapture(cs, &graph);
+        if (rc || e != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return rc ? rc : BFV_ERR_CUDA; }
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return BFV_ERR_CUDA;
+        it = ctx->graphs.emplace(key, std::make_pair(exec, held)).first;
+    }
+    if (cudaGraphLaunch(it->second.first, st) != cudaSuccess) return BFV_ERR_CUDA;
+    count_launch(ctx, it->second.second);
+    return BFV_OK;
+}
+
+int bfv_autotune_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint64_t *X_ct, size_t nX,
+                        uint64_t *Y_ct, void *ws, size_t ws_bytes, uintptr_t stream, size_t *best_chunk,
+                        double *best_ms) {
+    if (!ctx || !keys || !model || keys->ctx != ctx || model->ctx != ctx || !best_chunk) return BFV_ERR_INVALID_ARG;
+    if (nX == 0 || !X_ct || !Y_ct || !ws) return BFV_ERR_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    const size_t npairs = nX * model->nY;
+    const size_t cands[] = {128, 256, 512, 1024, 2048, 4096, 8192, 16384};
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return BFV_ERR_CUDA;
+    size_t best = 0, last = 0;
+    float best_t = 0;
+    int rc = BFV_OK;
+    for (size_t ch : cands) {
+        const size_t eff = std::min(ch, npairs);
+        if (eff == last) continue;               // larger candidates all mean "every pair at once"
+        last = eff;
+        PackedPlan plan = packed_plan(ctx, model, nX, eff);
+        if (plan.total > ws_bytes) break;
+        if ((rc = launch_packed(ctx, keys, model, (const u64 *)X_ct, nX, (u64 *)Y_ct, ws, plan, st))) break;  // warm-up
+        cudaEventRecord(a, st);
+        if ((rc = launch_packed(ctx, keys, model, (const u64 *)X_ct, nX, (u64 *)Y_ct, ws, plan, st))) break;
+        cudaEventRecord(b, st);
+        if (cudaEventSynchronize(b) != cudaSuccess) { rc = BFV_ERR_CUDA; break; }
+        float t = 0;
+        cudaEventElapsedTime(&t, a, b);
+        if (!best || t < best_t) { best = eff; best_t = t; }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc) return rc;
+    if (!best) return BFV_ERR_OVER_BUDGET;
+    ctx->tuned_chunk[npairs] = best;
+    *best_chunk = best;
+    if (best_ms) *best_ms = best_t;
+    return BFV_OK;
 }
 
 int bfv_lr_scores_standard_workspace(const bfv_ctx *ctx, const bfv_model *model, size_t *bytes) {

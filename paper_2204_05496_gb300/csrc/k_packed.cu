@@ -328,7 +328,11 @@ PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t c
     p.K = m->K;
     p.npairs = nX * m->nY;
     p.nout = (p.npairs + N - 1) / N;
-    p.chunk = chunk ? std::min(chunk, p.npairs) : std::min<size_t>(p.npairs, 2048);
+    if (!chunk) {
+        auto it = c->tuned_chunk.find(p.npairs);
+        chunk = it != c->tuned_chunk.end() ? it->second : 2048;
+    }
+    p.chunk = std::min(chunk, p.npairs);
     const size_t ctb = 2 * L * N * sizeof(u64);
     size_t off = 0;
     p.off_xntt = off; off += al256(nX * p.K * ctb);

@@ -118,6 +118,29 @@ def test_packed_parity_tiny(name, tiny):
     assert np.array_equal(got, oracle.expected_scores(X, W, b, P.t))
 
 
+def test_packed_graph_replay_and_autotune_tiny(tiny):
+    ctx, keys, P, okeys = tiny
+    w = synth.WORKLOADS["tiny-16"]
+    X, W, b = synth.workload_inputs(w)
+    X_ct, _, Y = oracle.packed_pipeline(P, okeys, X, W, b, w.seed_enc)
+    model = ctx.model_prepare(W, b)
+    Xd = dev(X_ct)
+    ws = torch.empty(ctx.packed_workspace(model, 16, 0), dtype=torch.uint8, device="cuda")
+    out = ctx.lr_scores_packed_graph(keys, model, Xd, ws=ws)          # captures
+    n0 = ctx.launch_count()
+    out.zero_()
+    ctx.lr_scores_packed_graph(keys, model, Xd, out=out, ws=ws)      # a new key (out differs) ...
+    ctx.lr_scores_packed_graph(keys, model, Xd, out=out, ws=ws)      # ... and its replay
+    torch.cuda.synchronize()
+    assert np.array_equal(host(out), Y)
+    assert ctx.launch_count() > n0
+    big = torch.empty(ctx.packed_workspace(model, 16, 128), dtype=torch.uint8, device="cuda")
+    chunk, ms = ctx.autotune_packed(keys, model, Xd, big)
+    assert chunk == 128 and ms > 0                                   # 128 pairs: one chunk holds all
+    Yt = ctx.lr_scores_packed(keys, model, Xd, ws=big)               # chunk 0 -> the tuned chunk
+    assert np.array_equal(host(Yt), Y)
+
+
 def test_packed_pair_states_tiny(tiny):
     ctx, keys, P, okeys = tiny
     w = synth.WORKLOADS["tiny-16"]
