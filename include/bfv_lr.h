@@ -181,6 +181,19 @@ int bfv_lr_scores_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *mo
                          size_t nX, uint64_t *Y_ct, void *ws, size_t ws_bytes, size_t pair_chunk,
                          uintptr_t stream);
 
+/* Several independent requests in one fused product (continuous batching): request r has
+ * nXs[r] individuals with input ciphertexts X_cts[r] (uint64[nXs[r]][ceil(f/N)][2][L][N],
+ * device) and receives its own outputs Y_cts[r] (uint64[ceil(nXs[r] |Y| / N)][2][L][N]),
+ * laid out exactly as bfv_lr_scores_packed would for that request alone — the pairs of all
+ * requests share every kernel launch, and each request's output is bit-identical to its
+ * single-request result. 1 <= nreq <= 64; X_cts, nXs and Y_cts are HOST arrays of length
+ * nreq. ws: at least bfv_lr_scores_packed_multi_workspace() bytes. */
+int bfv_lr_scores_packed_multi_workspace(const bfv_ctx *ctx, const bfv_model *model, int nreq, const size_t *nXs,
+                                         size_t pair_chunk, size_t *bytes);
+int bfv_lr_scores_packed_multi(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, int nreq,
+                               const uint64_t *const *X_cts, const size_t *nXs, uint64_t *const *Y_cts, void *ws,
+                               size_t ws_bytes, size_t pair_chunk, uintptr_t stream);
+
 /* The same product replayed from a CUDA graph: the first call with a given set of arguments
  * (handles, pointers, sizes, chunk, stream) captures every launch of bfv_lr_scores_packed
  * into a graph and later calls launch the instantiated graph, so the host issues one call

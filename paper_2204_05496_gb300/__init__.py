@@ -115,6 +115,8 @@ SIGNATURES = {
     "bfv_check_error": [_vp, ctypes.POINTER(ctypes.c_int)],
     "bfv_debug_inject": [_vp, ctypes.c_int, ctypes.c_int],
     "bfv_decrypt_noalloc_max_count": [_vp, ctypes.POINTER(_sz)],
+    "bfv_lr_scores_packed_multi_workspace": [_vp, _vp, ctypes.c_int, _vp, _sz, ctypes.POINTER(_sz)],
+    "bfv_lr_scores_packed_multi": [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _sz, _sz, _up],
     "bfv_lr_scores_packed_graph": [_vp, _vp, _vp, _vp, _sz, _vp, _vp, _sz, _sz, _up],
     "bfv_autotune_packed": [_vp, _vp, _vp, _vp, _sz, _vp, _vp, _sz, _up, ctypes.POINTER(_sz),
                             ctypes.POINTER(ctypes.c_double)],
@@ -345,6 +347,32 @@ class Context:
         n = _sz()
         _call("bfv_lr_scores_standard_workspace", self.handle, model.handle, ctypes.byref(n))
         return n.value
+
+    def multi_workspace(self, model: Model, nXs, pair_chunk: int = 0) -> int:
+        arr = (ctypes.c_size_t * len(nXs))(*nXs)
+        n = _sz()
+        _call("bfv_lr_scores_packed_multi_workspace", self.handle, model.handle, len(nXs), ctypes.cast(arr, _vp),
+              pair_chunk, ctypes.byref(n))
+        return n.value
+
+    def lr_scores_packed_multi(self, keys: Keys, model: Model, X_cts, outs=None, ws=None, pair_chunk: int = 0,
+                               stream=None):
+        """Several requests (a list of input-ciphertext tensors) in one fused packed product; returns
+        one output tensor per request, each identical to its single-request result."""
+        import torch
+        nXs = [x.shape[0] for x in X_cts]
+        if outs is None:
+            outs = [self._empty_u64(-(-n * model.nY // self.N), 2, self.L, self.N) for n in nXs]
+        need = self.multi_workspace(model, nXs, pair_chunk)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=f"cuda:{self.device}")
+        xs = [x.contiguous() for x in X_cts]
+        xp = (ctypes.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
+        yp = (ctypes.c_void_p * len(outs))(*[y.data_ptr() for y in outs])
+        na = (ctypes.c_size_t * len(nXs))(*nXs)
+        _call("bfv_lr_scores_packed_multi", self.handle, keys.handle, model.handle, len(xs), ctypes.cast(xp, _vp),
+              ctypes.cast(na, _vp), ctypes.cast(yp, _vp), _ptr(ws), ws.numel(), pair_chunk, _stream(stream))
+        return outs
 
     def lr_scores_packed_graph(self, keys: Keys, model: Model, X_ct, out=None, ws=None, pair_chunk: int = 0,
                                stream=None):

@@ -137,11 +137,26 @@ int launch_decrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *ct, size_t co
                    cudaStream_t st);
 int launch_model_weights(const bfv_ctx *c, bfv_model *m, const u64 *w_pt, cudaStream_t st);
 
+// Requests fused into one packed product, passed to kernels by value.
+constexpr int kMaxReq = 64;
+struct ReqTable {
+    int n;
+    int pad_;
+    u64 pair_start[kMaxReq + 1];     // first global pair of each request; [n] = number of pairs
+    u32 xct[kMaxReq];                // first input ciphertext of each request in the fused input
+};
+
 struct PackedPlan {
     size_t nX, nY, K, npairs, nout, chunk;
     size_t off_xntt, off_yacc, off_state, off_digits, off_u, off_r, total;
+    int nreq;
+    ReqTable rt;
+    size_t nXs[kMaxReq], ycts[kMaxReq], nouts[kMaxReq];   // per request: individuals, first output, outputs
 };
 PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t chunk);
+PackedPlan packed_plan_multi(const bfv_ctx *c, const bfv_model *m, int nreq, const size_t *nXs, size_t chunk);
+int launch_packed_multi(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, int nreq, const u64 *const *X_ct,
+                        u64 *const *Y_ct, void *ws, const PackedPlan &plan, cudaStream_t st);
 int launch_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const u64 *X_ct, size_t nX,
                   u64 *Y_ct, void *ws, const PackedPlan &plan, cudaStream_t st);
 int launch_pair_export(const bfv_ctx *c, const PackedPlan &plan, const void *ws, size_t slot_in_chunk, u64 *ct_out,

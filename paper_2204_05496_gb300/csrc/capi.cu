@@ -591,6 +591,28 @@ int bfv_lr_scores_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *mo
     return launch_packed(ctx, keys, model, (const u64 *)X_ct, nX, (u64 *)Y_ct, ws, plan, S(stream));
 }
 
+int bfv_lr_scores_packed_multi_workspace(const bfv_ctx *ctx, const bfv_model *model, int nreq, const size_t *nXs,
+                                         size_t pair_chunk, size_t *bytes) {
+    if (!ctx || !model || model->ctx != ctx || !bytes || !nXs || nreq < 1 || nreq > kMaxReq) return BFV_ERR_INVALID_ARG;
+    for (int r = 0; r < nreq; ++r)
+        if (!nXs[r]) return BFV_ERR_INVALID_ARG;
+    *bytes = packed_plan_multi(ctx, model, nreq, nXs, pair_chunk).total;
+    return BFV_OK;
+}
+
+int bfv_lr_scores_packed_multi(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, int nreq,
+                               const uint64_t *const *X_cts, const size_t *nXs, uint64_t *const *Y_cts, void *ws,
+                               size_t ws_bytes, size_t pair_chunk, uintptr_t stream) {
+    if (!ctx || !keys || !model || keys->ctx != ctx || model->ctx != ctx) return BFV_ERR_INVALID_ARG;
+    if (nreq < 1 || nreq > kMaxReq || !X_cts || !nXs || !Y_cts || !ws) return BFV_ERR_INVALID_ARG;
+    for (int r = 0; r < nreq; ++r)
+        if (!nXs[r] || !X_cts[r] || !Y_cts[r]) return BFV_ERR_INVALID_ARG;
+    PackedPlan plan = packed_plan_multi(ctx, model, nreq, nXs, pair_chunk);
+    if (ws_bytes < plan.total) return BFV_ERR_OVER_BUDGET;
+    return launch_packed_multi(ctx, keys, model, nreq, (const u64 *const *)X_cts, (u64 *const *)Y_cts, ws, plan,
+                               S(stream));
+}
+
 int bfv_lr_scores_packed_graph(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint64_t *X_ct,
                                size_t nX, uint64_t *Y_ct, void *ws, size_t ws_bytes, size_t pair_chunk,
                                uintptr_t stream) {

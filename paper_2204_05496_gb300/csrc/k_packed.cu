@@ -26,14 +26,25 @@ template <class K> void set_smem(K kern, size_t bytes) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
+// Pair p of a fused product belongs to request r with pair_start[r] <= p < pair_start[r+1];
+// g = p - pair_start[r] is the pair index inside its request (i = g / |Y|, j = g mod |Y|).
+__device__ __forceinline__ int req_of(const ReqTable &rt, size_t p) {
+    int r = 0;
+    while (r + 1 < rt.n && rt.pair_start[r + 1] <= p) ++r;
+    return r;
+}
+
 // ------------------------------------------------------------------ MAC (lines 5-13)
 // C[g][c][l][p] = sum_k Xe[i][k][c][l][p] * We[j][k][l][p]; grid.x = (g, c, l), grid.y = tile.
 __global__ void __launch_bounds__(256) k_mac(const ModTab *__restrict__ mods, int N, int L, int K, int nY, size_t g0,
-                                             const u64 *__restrict__ Xe, const shoup_t *__restrict__ We, u64 *C) {
+                                             const ReqTable rt, const u64 *__restrict__ Xe,
+                                             const shoup_t *__restrict__ We, u64 *C) {
     const size_t x = blockIdx.x;
     const int l = (int)(x % L), c = (int)((x / L) % 2);
-    const size_t gl = x / (2 * L), g = g0 + gl;
-    const size_t i = g / nY, j = g % nY;
+    const size_t gl = x / (2 * L), gp = g0 + gl;
+    const int r = req_of(rt, gp);
+    const size_t g = gp - rt.pair_start[r];
+    const size_t i = rt.xct[r] / K + g / nY, j = g % nY;
     const u64 q = mods[l].q, q2 = 2 * q;
     const size_t ctw = 2 * (size_t)L * N;
     const int p0 = blockIdx.y * 1024 + threadIdx.x;
@@ -196,12 +207,13 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_ks_moddown(const ModTab *__res
 // (g0+g) mod N), whose coefficient k is N^-1 omega^(-e k) mod t, e the slot's exponent.
 template <int LOGN>
 __global__ void __launch_bounds__(nt_for(LOGN)) k_bias_mask(const ModTab *__restrict__ mods, int L, int tmod, int nY,
-                                                             size_t g0, const u32 *__restrict__ maskpow,
+                                                             size_t g0, const ReqTable rt, const u32 *__restrict__ maskpow,
                                                              const u64 *__restrict__ bias_delta, u64 *C) {
     extern __shared__ u64 sm[];
     constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
     const int l = blockIdx.x % L;
-    const size_t gl = blockIdx.x / L, g = g0 + gl;
+    const size_t gl = blockIdx.x / L, gp = g0 + gl;
+    const size_t g = gp - rt.pair_start[req_of(rt, gp)];
     const int j = (int)(g % nY), s = (int)(g % N);
     const ModTab T = mods[l];
     const u64 t = mods[tmod].q, th = (t - 1) / 2;
@@ -264,8 +276,8 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_intt_copy(const ModTab *__rest
 int last_err() { return cudaGetLastError() == cudaSuccess ? BFV_OK : BFV_ERR_CUDA; }
 
 template <int LOGN>
-int run_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const u64 *X_ct, u64 *Y_ct, char *ws,
-               const PackedPlan &pl, cudaStream_t st) {
+int run_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, int nreq, const u64 *const *X_ct,
+               u64 *const *Y_ct, char *ws, const PackedPlan &pl, cudaStream_t st) {
     constexpr int N = 1 << LOGN;
     const int L = c->L, nqp = c->nqp;
     const size_t ctw = 2 * (size_t)L * N;
@@ -278,15 +290,16 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const u6
     set_smem(k_ks_moddown<LOGN>, full);
     set_smem(k_bias_mask<LOGN>, full);
 
-    int rc = launch_ntt_limbs(c, X_ct, Xe, pl.nX * pl.K, true, st);
-    if (rc) return rc;
+    int rc;
+    for (int r = 0; r < nreq; ++r)
+        if ((rc = launch_ntt_limbs(c, X_ct[r], Xe + (size_t)pl.rt.xct[r] * ctw, pl.nXs[r] * pl.K, true, st))) return rc;
     if (cudaMemsetAsync(Yacc, 0, pl.nout * ctw * sizeof(u64), st) != cudaSuccess) return BFV_ERR_CUDA;
     const size_t keyblock = (size_t)L * 2 * nqp * N;   // one Galois element
     for (size_t g0 = 0; g0 < pl.npairs; g0 += pl.chunk) {
         const size_t ng = std::min(pl.chunk, pl.npairs - g0);
         { ProfScope pr(c, BFV_K_MAC, st);
         k_mac<<<dim3((unsigned)(ng * 2 * L), (unsigned)((N + 1023) / 1024)), 256, 0, st>>>(
-            c->dmods, N, L, (int)pl.K, (int)pl.nY, g0, Xe, m->w_eval, C); }
+            c->dmods, N, L, (int)pl.K, (int)pl.nY, g0, pl.rt, Xe, m->w_eval, C); }
         count_launch(c);
         for (int s = 0; s < k->ng; ++s) {
             const u32 gal = (u32)c->galois[s];
@@ -302,40 +315,64 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const u6
             count_launch(c, 4);
         }
         { ProfScope pr(c, BFV_K_BIAS_MASK, st);
-        k_bias_mask<LOGN><<<(unsigned)(ng * L), nt_for(LOGN), full, st>>>(c->dmods, L, nqp, (int)pl.nY, g0, c->dmaskpow,
-                                                                         m->bias_delta, C); }
+        k_bias_mask<LOGN><<<(unsigned)(ng * L), nt_for(LOGN), full, st>>>(c->dmods, L, nqp, (int)pl.nY, g0, pl.rt,
+                                                                         c->dmaskpow, m->bias_delta, C); }
         count_launch(c);
-        for (size_t o = g0 / N; o <= (g0 + ng - 1) / N; ++o) {
-            const size_t ga = std::max(g0, o * N), gb = std::min(g0 + ng, (o + 1) * N);
-            ProfScope pr(c, BFV_K_COMPRESS, st);
-            k_compress<<<(unsigned)((ctw + 255) / 256), 256, 0, st>>>(c->dmods, N, L, ga, gb, g0, C, Yacc + o * ctw);
-            count_launch(c);
+        // compression: the pairs of request r that land in its output o are one contiguous range
+        for (int r = 0; r < nreq; ++r) {
+            const size_t pa = pl.rt.pair_start[r], pb = pl.rt.pair_start[r + 1];
+            if (pb <= g0 || pa >= g0 + ng) continue;
+            for (size_t o = 0; pa + o * N < pb; ++o) {
+                const size_t ga = std::max(g0, pa + o * N), gb = std::min({g0 + ng, pa + (o + 1) * N, pb});
+                if (ga >= gb) continue;
+                ProfScope pr(c, BFV_K_COMPRESS, st);
+                k_compress<<<(unsigned)((ctw + 255) / 256), 256, 0, st>>>(c->dmods, N, L, ga, gb, g0, C,
+                                                                          Yacc + (pl.ycts[r] + o) * ctw);
+                count_launch(c);
+            }
         }
         if ((rc = last_err())) return rc;
     }
-    return launch_ntt_limbs(c, Yacc, Y_ct, pl.nout, false, st);
+    for (int r = 0; r < nreq; ++r)
+        if ((rc = launch_ntt_limbs(c, Yacc + pl.ycts[r] * ctw, Y_ct[r], pl.nouts[r], false, st))) return rc;
+    return BFV_OK;
 }
 
 }  // namespace
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t chunk) {
+PackedPlan packed_plan_multi(const bfv_ctx *c, const bfv_model *m, int nreq, const size_t *nXs, size_t chunk) {
     PackedPlan p{};
     const size_t N = c->N, L = c->L, nqp = c->nqp;
-    p.nX = nX;
+    p.nreq = nreq;
     p.nY = m->nY;
     p.K = m->K;
-    p.npairs = nX * m->nY;
-    p.nout = (p.npairs + N - 1) / N;
+    p.rt.n = nreq;
+    size_t cts = 0, pairs = 0, outs = 0;
+    for (int r = 0; r < nreq; ++r) {
+        p.nXs[r] = nXs[r];
+        p.rt.pair_start[r] = pairs;
+        p.rt.xct[r] = (u32)cts;
+        p.ycts[r] = outs;
+        const size_t np = nXs[r] * m->nY;
+        p.nouts[r] = (np + N - 1) / N;
+        cts += nXs[r] * m->K;
+        pairs += np;
+        outs += p.nouts[r];
+    }
+    p.rt.pair_start[nreq] = pairs;
+    p.nX = nreq == 1 ? nXs[0] : 0;
+    p.npairs = pairs;
+    p.nout = outs;
     if (!chunk) {
         auto it = c->tuned_chunk.find(p.npairs);
         chunk = it != c->tuned_chunk.end() ? it->second : 2048;
     }
-    p.chunk = std::min(chunk, p.npairs);
+    p.chunk = std::max<size_t>(1, std::min(chunk, p.npairs));
     const size_t ctb = 2 * L * N * sizeof(u64);
     size_t off = 0;
-    p.off_xntt = off; off += al256(nX * p.K * ctb);
+    p.off_xntt = off; off += al256(cts * ctb);
     p.off_yacc = off; off += al256(p.nout * ctb);
     p.off_state = off; off += al256(p.chunk * ctb);
     p.off_digits = off; off += al256(p.chunk * L * N * sizeof(u64));
@@ -345,15 +382,24 @@ PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t c
     return p;
 }
 
+PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t chunk) {
+    return packed_plan_multi(c, m, 1, &nX, chunk);
+}
+
+int launch_packed_multi(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, int nreq, const u64 *const *X_ct,
+                        u64 *const *Y_ct, void *ws, const PackedPlan &plan, cudaStream_t st) {
+    switch (c->logN) {
+        case 12: return run_packed<12>(c, k, m, nreq, X_ct, Y_ct, (char *)ws, plan, st);
+        case 13: return run_packed<13>(c, k, m, nreq, X_ct, Y_ct, (char *)ws, plan, st);
+        case 14: return run_packed<14>(c, k, m, nreq, X_ct, Y_ct, (char *)ws, plan, st);
+        default: return BFV_ERR_BAD_PARAMS;
+    }
+}
+
 int launch_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const u64 *X_ct, size_t nX, u64 *Y_ct,
                   void *ws, const PackedPlan &plan, cudaStream_t st) {
     (void)nX;
-    switch (c->logN) {
-        case 12: return run_packed<12>(c, k, m, X_ct, Y_ct, (char *)ws, plan, st);
-        case 13: return run_packed<13>(c, k, m, X_ct, Y_ct, (char *)ws, plan, st);
-        case 14: return run_packed<14>(c, k, m, X_ct, Y_ct, (char *)ws, plan, st);
-        default: return BFV_ERR_BAD_PARAMS;
-    }
+    return launch_packed_multi(c, k, m, 1, &X_ct, &Y_ct, ws, plan, st);
 }
 
 int launch_pair_export(const bfv_ctx *c, const PackedPlan &plan, const void *ws, size_t slot, u64 *ct_out,

@@ -1,0 +1,180 @@
+"""Continuous-batching request loop for encrypted LR scoring (packed product, Algorithm 1).
+
+A request carries the encrypted inputs of one or more individuals (already on the device,
+uint64[nX][ceil(f/N)][2][L][N]) and receives its own output ciphertexts. The server keeps
+the Galois keys and the encoded model resident, and:
+
+  * admits waiting requests while the workspace of the launch they would join fits the HBM
+    budget next to the launches already in flight (larger requests wait for memory);
+  * fuses every admitted request (up to 64 requests / `max_pairs` pairs) into ONE packed
+    product (bfv_lr_scores_packed_multi), each request keeping its own outputs;
+  * runs up to `n_streams` such launches at once on separate CUDA streams, so a batch formed
+    from requests that arrived while another batch was on the GPU overlaps with it;
+  * detects completion from CUDA events and reports per-request latency (arrival to the end
+    of its product) with p50/p99 and predictions/s.
+
+Every request's output is bit-identical to running it alone (the fused product computes each
+pair exactly as the single-request call does).
+"""
+from __future__ import annotations
+
+import dataclasses
+import time
+
+import numpy as np
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    X_ct: object                 # device tensor [nX][K][2][L][N]
+    t_arrival: float             # seconds on the server clock
+    out: object = None           # device tensor of output ciphertexts, set at launch
+    t_done: float | None = None  # seconds on the server clock, set at completion
+    batch: int = -1
+
+    @property
+    def nX(self) -> int:
+        return int(self.X_ct.shape[0])
+
+
+class Server:
+    def __init__(self, ctx, keys, model, hbm_budget_bytes: int, n_streams: int = 2, max_pairs: int = 8192,
+                 pair_chunk: int = 0):
+        import torch
+        self.torch = torch
+        self.ctx, self.keys, self.model = ctx, keys, model
+        self.budget = int(hbm_budget_bytes)
+        self.max_pairs, self.pair_chunk = max_pairs, pair_chunk
+        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.busy = [None] * n_streams          # (event, requests, ws bytes, ws) per stream
+        self.waiting: list[Request] = []
+        self.done: list[Request] = []
+        self.in_flight_bytes = 0
+        self.nbatches = 0
+        self.max_concurrent = 0                 # most launches in flight at once
+        self.t0_event = torch.cuda.Event(enable_timing=True)
+        self.t0_host = None
+
+    # -- clock: host seconds since start; completions come from CUDA events against t0_event
+    def start(self):
+        self.torch.cuda.synchronize()
+        self.t0_event.record()
+        self.torch.cuda.synchronize()
+        self.t0_host = time.perf_counter()
+
+    def now(self) -> float:
+        return time.perf_counter() - self.t0_host
+
+    def submit(self, rid: int, X_ct, t_arrival: float | None = None) -> Request:
+        r = Request(rid, X_ct, self.now() if t_arrival is None else t_arrival)
+        self.waiting.append(r)
+        return r
+
+    def _ws_bytes(self, reqs) -> int:
+        return self.ctx.multi_workspace(self.model, [r.nX for r in reqs], self.pair_chunk)
+
+    def _retire(self):
+        for s, b in enumerate(self.busy):
+            if b is not None and b[0].query():
+                ev, reqs, nbytes, _ = b
+                t = self.t0_event.elapsed_time(ev) / 1e3
+                for r in reqs:
+                    r.t_done = t
+                    self.done.append(r)
+                self.in_flight_bytes -= nbytes
+                self.busy[s] = None
+
+    def _launch(self):
+        torch = self.torch
+        for s, b in enumerate(self.busy):
+            if b is not None or not self.waiting:
+                continue
+            # admission: take waiting requests in arrival order while pairs, request count and
+            # the HBM budget allow
+            take, pairs = [], 0
+            for r in self.waiting:
+                p = r.nX * self.model.nY
+                if take and (pairs + p > self.max_pairs or len(take) == 64):
+                    break
+                if self.in_flight_bytes + self._ws_bytes(take + [r]) > self.budget:
+                    break
+                take.append(r)
+                pairs += p
+            if not take:
+                return
+            nbytes = self._ws_bytes(take)
+            stream = self.streams[s]
+            with torch.cuda.stream(stream):
+                ws = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{self.ctx.device}")
+                outs = self.ctx.lr_scores_packed_multi(self.keys, self.model, [r.X_ct for r in take], ws=ws,
+                                                       pair_chunk=self.pair_chunk, stream=stream)
+                ev = torch.cuda.Event(enable_timing=True)
+                ev.record(stream)
+            for r, o in zip(take, outs):
+                r.out, r.batch = o, self.nbatches
+            self.nbatches += 1
+            self.waiting = self.waiting[len(take):]
+            self.in_flight_bytes += nbytes
+            self.busy[s] = (ev, take, nbytes, ws)
+            self.max_concurrent = max(self.max_concurrent, sum(x is not None for x in self.busy))
+
+    def step(self):
+        """One scheduling round: retire finished launches, start new ones on free streams."""
+        self._retire()
+        self._launch()
+
+    def idle(self) -> bool:
+        return not self.waiting and all(b is None for b in self.busy)
+
+    def run(self, arrivals, make_inputs, poll_s: float = 0.0005):
+        """Replays an arrival trace: arrivals = [(t_seconds, nX)], make_inputs(i, nX) -> X_ct.
+        Returns the completed requests."""
+        self.start()
+        k = 0
+        while k < len(arrivals) or not self.idle():
+            now = self.now()
+            while k < len(arrivals) and arrivals[k][0] <= now:
+                self.submit(k, make_inputs(k, arrivals[k][1]), arrivals[k][0])
+                k += 1
+            self.step()
+            if k < len(arrivals) and self.idle():
+                time.sleep(max(0.0, min(poll_s * 20, arrivals[k][0] - self.now())))
+            else:
+                time.sleep(poll_s)
+        self.torch.cuda.synchronize()
+        self._retire()
+        return sorted(self.done, key=lambda r: r.rid)
+
+
+def latency_report(reqs, nY: int) -> dict:
+    """p50/p99 latency (arrival to completion) and throughput of a finished trace."""
+    lat = np.array([r.t_done - r.t_arrival for r in reqs])
+    span = max(r.t_done for r in reqs) - min(r.t_arrival for r in reqs)
+    preds = sum(r.nX for r in reqs)
+    return {"requests": len(reqs), "predictions": preds, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+            "p99_ms": float(np.percentile(lat, 99) * 1e3), "predictions_per_s": preds / span if span > 0 else 0.0,
+            "span_s": span}
+
+
+def run_unbatched(ctx, keys, model, arrivals, make_inputs, pair_chunk: int = 0):
+    """The same trace served one request at a time (FIFO, one stream, no fusion)."""
+    import torch
+    torch.cuda.synchronize()
+    t0 = torch.cuda.Event(enable_timing=True)
+    t0.record()
+    torch.cuda.synchronize()
+    h0 = time.perf_counter()
+    done = []
+    for k, (ta, nX) in enumerate(arrivals):
+        while time.perf_counter() - h0 < ta:
+            time.sleep(0.0005)
+        X = make_inputs(k, nX)
+        ctx.lr_scores_packed(keys, model, X, pair_chunk=pair_chunk)
+        ev = torch.cuda.Event(enable_timing=True)
+        ev.record()
+        ev.synchronize()
+        r = Request(k, X, ta)
+        r.t_done = t0.elapsed_time(ev) / 1e3
+        done.append(r)
+    return done

@@ -1,0 +1,92 @@
+"""Continuous batching: several requests fused into one packed product, and the serving loop.
+Each request's output ciphertexts must be bit-identical (tolerance zero) whether it runs
+alone or in a mix with others, and decrypt to its closed-form scores."""
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import paper_2204_05496_gb300 as bfv
+    w = synth.WORKLOADS["tiny-1"]
+    ctx = bfv.Context.from_shape(w.params)
+    keys = ctx.keygen(w.seed_keys)
+    rng = np.random.default_rng(41)
+    X = (rng.random((40, 1000)) < 0.05).astype(np.uint8)
+    W = rng.integers(-127, 128, (1000, 8))
+    b = rng.integers(-127, 128, 8)
+    model = ctx.model_prepare(W, b)
+    pt = ctx.encode_features(torch.from_numpy(X).cuda())
+    X_ct = ctx.encrypt(keys, pt.reshape(-1, ctx.N), seed=5).reshape(40, 1, 2, ctx.L, ctx.N)
+    return bfv, ctx, keys, model, X, W, b, X_ct
+
+
+def _alone(ctx, keys, model, X_ct):
+    return ctx.lr_scores_packed(keys, model, X_ct)
+
+
+@pytest.mark.parametrize("chunk", [0, 20])
+def test_fused_requests_match_single_requests(env, chunk):
+    bfv, ctx, keys, model, X, W, b, X_ct = env
+    sizes = [1, 3, 1, 7, 2]
+    starts = np.cumsum([0] + sizes)
+    reqs = [X_ct[starts[k]:starts[k + 1]] for k in range(len(sizes))]
+    outs = ctx.lr_scores_packed_multi(keys, model, reqs, pair_chunk=chunk)
+    for k, (r, o) in enumerate(zip(reqs, outs)):
+        assert torch.equal(o, _alone(ctx, keys, model, r))
+        slots = ctx.decode(ctx.decrypt(keys, o)).cpu().numpy()
+        got = bfv.unpack_packed_scores(ctx.N, slots, sizes[k], 8)
+        assert np.array_equal(got, oracle.expected_scores(X[starts[k]:starts[k + 1]], W, b, ctx.t))
+
+
+def test_server_fuses_and_overlaps_and_keeps_results(env):
+    from paper_2204_05496_gb300 import serve
+    bfv, ctx, keys, model, X, W, b, X_ct = env
+    sizes = [1, 1, 4, 1, 2, 1, 8, 1, 1, 3, 1, 1]
+    starts = np.cumsum([0] + sizes)
+    # a burst at t = 0 and more requests arriving while it is on the GPU
+    arrivals = [(0.0 if k < 6 else 0.002 * (k - 5), n) for k, n in enumerate(sizes)]
+    srv = serve.Server(ctx, keys, model, hbm_budget_bytes=8 << 30, n_streams=2)
+    done = srv.run(arrivals, lambda k, n: X_ct[starts[k]:starts[k] + n])
+    assert len(done) == len(sizes) and all(r.t_done is not None and r.t_done >= r.t_arrival for r in done)
+    assert srv.nbatches < len(sizes)                  # requests were fused
+    for r in done:
+        assert torch.equal(r.out, _alone(ctx, keys, model, r.X_ct))
+    rep = serve.latency_report(done, 8)
+    assert rep["predictions"] == sum(sizes) and rep["p99_ms"] >= rep["p50_ms"] > 0
+
+
+def test_server_hbm_budget_limits_admission(env):
+    from paper_2204_05496_gb300 import serve
+    bfv, ctx, keys, model, X, W, b, X_ct = env
+    one = ctx.multi_workspace(model, [2])
+    srv = serve.Server(ctx, keys, model, hbm_budget_bytes=one, n_streams=2)   # room for one 2-individual launch
+    done = srv.run([(0.0, 2)] * 4, lambda k, n: X_ct[2 * k:2 * k + n])
+    assert srv.nbatches == 4                          # nothing fused, nothing concurrent
+    for r in done:
+        assert torch.equal(r.out, _alone(ctx, keys, model, r.X_ct))
+
+
+def test_server_overlaps_a_second_batch_with_the_first(env):
+    from paper_2204_05496_gb300 import serve
+    bfv, ctx, keys, model, X, W, b, X_ct = env
+    srv = serve.Server(ctx, keys, model, hbm_budget_bytes=8 << 30, n_streams=2)
+    srv.start()
+    first = [srv.submit(k, X_ct[4 * k:4 * k + 4]) for k in range(3)]
+    srv.step()                                        # batch 0 (3 requests) goes to stream 0
+    late = [srv.submit(3 + k, X_ct[12 + k:13 + k]) for k in range(2)]
+    srv.step()                                        # arrived while batch 0 runs -> stream 1
+    assert srv.nbatches == 2 and srv.max_concurrent == 2
+    while not srv.idle():
+        srv.step()
+    torch.cuda.synchronize()
+    srv.step()
+    for r in first + late:
+        assert r.t_done is not None
+        assert torch.equal(r.out, _alone(ctx, keys, model, r.X_ct))
