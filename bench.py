@@ -66,6 +66,10 @@ def parse_args(argv=None):
     p.add_argument("--only-standard", action="store_true",
                    help="profiling case: time only the standard product on the first --features features")
     p.add_argument("--features", type=int, default=40000)
+    p.add_argument("--serve", action="store_true",
+                   help="serving case: Poisson request traces through the continuous-batching loop")
+    p.add_argument("--rates", type=str, default="1,2,5,20,100,500")
+    p.add_argument("--serve-cap", type=int, default=1024, help="predictions offered per rate")
     return p.parse_args(argv)
 
 
@@ -630,8 +634,64 @@ def run_only_standard(args):
     return 0 if ok else 1
 
 
+def run_serve(args):
+    """Serving workload: Poisson arrivals, 70% single-individual and 30% 16..512-individual
+    requests on the 40,000-feature x 16-class model; keys and model resident; the
+    continuous-batching loop (HBM budget 64 GB, two streams) against the same requests served
+    one at a time. Each rate's trace stops once --serve-cap predictions have been offered."""
+    import torch
+    import paper_2204_05496_gb300 as bfv
+    from paper_2204_05496_gb300 import serve
+    bfv.build()
+    torch.cuda.set_device(0)
+    w = synth.WORKLOADS[WORKLOAD]
+    X, W, b = synth.workload_inputs(w)
+    N, L = w.params.N, w.params.L
+    ctx = bfv.Context.from_shape(w.params)
+    keys = ctx.keygen(w.seed_keys)
+    model = ctx.model_prepare(W, b)
+    pt = ctx.encode_features(torch.from_numpy(X).cuda())
+    pool = ctx.encrypt(keys, pt.reshape(-1, N), seed=w.seed_enc).reshape(len(X), model.K, 2, L, N)
+    del pt
+
+    def inputs(k, n):
+        i0 = (k * 131) % (len(X) - n + 1)
+        return pool[i0:i0 + n]
+
+    # warm-up: one fused launch and one single request
+    ctx.lr_scores_packed_multi(keys, model, [pool[:1], pool[1:17]])
+    ctx.lr_scores_packed(keys, model, pool[:1])
+    torch.cuda.synchronize()
+    results = {}
+    for rate in [float(r) for r in args.rates.split(",")]:
+        trace, offered = [], 0
+        for t, n in synth.poisson_arrivals(501, rate, 100000):
+            if offered >= args.serve_cap:
+                break
+            trace.append((t, n))
+            offered += n
+        srv = serve.Server(ctx, keys, model, hbm_budget_bytes=64 << 30, n_streams=2)
+        batched = serve.latency_report(srv.run(trace, inputs), model.nY)
+        batched.update(launches=srv.nbatches, max_concurrent=srv.max_concurrent)
+        torch.cuda.empty_cache()
+        srv = serve.Server(ctx, keys, model, hbm_budget_bytes=64 << 30, n_streams=2, small_pairs=16 * model.nY)
+        split = serve.latency_report(srv.run(trace, inputs), model.nY)
+        split.update(launches=srv.nbatches, max_concurrent=srv.max_concurrent)
+        torch.cuda.empty_cache()
+        single = serve.latency_report(serve.run_unbatched(ctx, keys, model, trace, inputs), model.nY)
+        results[str(rate)] = {"offered_req_per_s": rate, "batched": batched, "batched_priority": split,
+                              "one_by_one": single}
+        print(json.dumps({"rate": rate, "batched": batched, "batched_priority": split, "one_by_one": single}),
+              flush=True)
+    print(json.dumps({"case": "serve", "workload": "batch512-40k model, Poisson arrivals (70% x1, 30% x16..512)",
+                      "results": results}), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.serve:
+        return run_serve(args)
     if args.impl == "reference":
         return run_reference(args)
     if args.only_packed:

@@ -10,6 +10,9 @@ the Galois keys and the encoded model resident, and:
     product (bfv_lr_scores_packed_multi), each request keeping its own outputs;
   * runs up to `n_streams` such launches at once on separate CUDA streams, so a batch formed
     from requests that arrived while another batch was on the GPU overlaps with it;
+  * with `small_pairs` > 0, keeps two classes: requests of at most `small_pairs` pairs are
+    fused and launched on a high-priority stream of their own, so a single-individual request
+    is not held behind a large batch (the GPU block scheduler prefers its CTAs);
   * detects completion from CUDA events and reports per-request latency (arrival to the end
     of its product) with p50/p99 and predictions/s.
 
@@ -40,13 +43,22 @@ class Request:
 
 class Server:
     def __init__(self, ctx, keys, model, hbm_budget_bytes: int, n_streams: int = 2, max_pairs: int = 8192,
-                 pair_chunk: int = 0):
-        import torch
-        self.torch = torch
+                 pair_chunk: int = 0, small_pairs: int = 0, torch_module=None):
+        if torch_module is None:
+            import torch as torch_module
+        torch = self.torch = torch_module
         self.ctx, self.keys, self.model = ctx, keys, model
         self.budget = int(hbm_budget_bytes)
         self.max_pairs, self.pair_chunk = max_pairs, pair_chunk
-        self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+        self.small_pairs = small_pairs
+        # stream classes: None = any request; "small" / "large" when the classes are split
+        if small_pairs > 0:
+            lo, hi = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") else (0, -1)
+            self.streams = [torch.cuda.Stream(priority=min(lo, hi))] + [torch.cuda.Stream() for _ in range(n_streams - 1)]
+            self.classes = ["small"] + ["large"] * (n_streams - 1)
+        else:
+            self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
+            self.classes = [None] * n_streams
         self.busy = [None] * n_streams          # (event, requests, ws bytes, ws) per stream
         self.waiting: list[Request] = []
         self.done: list[Request] = []
@@ -85,15 +97,20 @@ class Server:
                 self.in_flight_bytes -= nbytes
                 self.busy[s] = None
 
+    def _class(self, r: Request) -> str:
+        return "small" if r.nX * self.model.nY <= self.small_pairs else "large"
+
     def _launch(self):
         torch = self.torch
         for s, b in enumerate(self.busy):
             if b is not None or not self.waiting:
                 continue
-            # admission: take waiting requests in arrival order while pairs, request count and
-            # the HBM budget allow
+            # admission: take waiting requests of this stream's class in arrival order while
+            # pairs, request count and the HBM budget allow
             take, pairs = [], 0
             for r in self.waiting:
+                if self.classes[s] is not None and self._class(r) != self.classes[s]:
+                    continue
                 p = r.nX * self.model.nY
                 if take and (pairs + p > self.max_pairs or len(take) == 64):
                     break
@@ -102,7 +119,7 @@ class Server:
                 take.append(r)
                 pairs += p
             if not take:
-                return
+                continue
             nbytes = self._ws_bytes(take)
             stream = self.streams[s]
             with torch.cuda.stream(stream):
@@ -114,7 +131,8 @@ class Server:
             for r, o in zip(take, outs):
                 r.out, r.batch = o, self.nbatches
             self.nbatches += 1
-            self.waiting = self.waiting[len(take):]
+            taken = set(id(r) for r in take)
+            self.waiting = [r for r in self.waiting if id(r) not in taken]
             self.in_flight_bytes += nbytes
             self.busy[s] = (ev, take, nbytes, ws)
             self.max_concurrent = max(self.max_concurrent, sum(x is not None for x in self.busy))
@@ -127,17 +145,28 @@ class Server:
     def idle(self) -> bool:
         return not self.waiting and all(b is None for b in self.busy)
 
-    def run(self, arrivals, make_inputs, poll_s: float = 0.0005):
+    def _check_admissible(self):
+        """With nothing in flight, every waiting request must fit the budget on its own."""
+        if all(b is None for b in self.busy):
+            for r in self.waiting:
+                if self._ws_bytes([r]) > self.budget:
+                    raise MemoryError(f"request {r.rid} needs {self._ws_bytes([r])} bytes, "
+                                      f"more than the HBM budget of {self.budget}")
+
+    def run(self, arrivals, make_inputs, poll_s: float = 0.0005, max_seconds: float = 600.0):
         """Replays an arrival trace: arrivals = [(t_seconds, nX)], make_inputs(i, nX) -> X_ct.
-        Returns the completed requests."""
+        Returns the completed requests. Raises TimeoutError after max_seconds of wall time."""
         self.start()
         k = 0
         while k < len(arrivals) or not self.idle():
             now = self.now()
+            if now > max_seconds:
+                raise TimeoutError(f"trace not served within {max_seconds} s")
             while k < len(arrivals) and arrivals[k][0] <= now:
                 self.submit(k, make_inputs(k, arrivals[k][1]), arrivals[k][0])
                 k += 1
             self.step()
+            self._check_admissible()
             if k < len(arrivals) and self.idle():
                 time.sleep(max(0.0, min(poll_s * 20, arrivals[k][0] - self.now())))
             else:
@@ -148,13 +177,19 @@ class Server:
 
 
 def latency_report(reqs, nY: int) -> dict:
-    """p50/p99 latency (arrival to completion) and throughput of a finished trace."""
+    """p50/p99 latency (arrival to completion) and throughput of a finished trace, overall and
+    for single-individual requests."""
     lat = np.array([r.t_done - r.t_arrival for r in reqs])
     span = max(r.t_done for r in reqs) - min(r.t_arrival for r in reqs)
     preds = sum(r.nX for r in reqs)
-    return {"requests": len(reqs), "predictions": preds, "p50_ms": float(np.percentile(lat, 50) * 1e3),
-            "p99_ms": float(np.percentile(lat, 99) * 1e3), "predictions_per_s": preds / span if span > 0 else 0.0,
-            "span_s": span}
+    single = np.array([r.t_done - r.t_arrival for r in reqs if r.nX == 1])
+    out = {"requests": len(reqs), "predictions": preds, "p50_ms": float(np.percentile(lat, 50) * 1e3),
+           "p99_ms": float(np.percentile(lat, 99) * 1e3), "predictions_per_s": preds / span if span > 0 else 0.0,
+           "span_s": span}
+    if len(single):
+        out["single_p50_ms"] = float(np.percentile(single, 50) * 1e3)
+        out["single_p99_ms"] = float(np.percentile(single, 99) * 1e3)
+    return out
 
 
 def run_unbatched(ctx, keys, model, arrivals, make_inputs, pair_chunk: int = 0):

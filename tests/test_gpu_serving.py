@@ -90,3 +90,17 @@ def test_server_overlaps_a_second_batch_with_the_first(env):
     for r in first + late:
         assert r.t_done is not None
         assert torch.equal(r.out, _alone(ctx, keys, model, r.X_ct))
+
+
+def test_server_priority_classes_keep_results(env):
+    from paper_2204_05496_gb300 import serve
+    bfv, ctx, keys, model, X, W, b, X_ct = env
+    sizes = [12, 1, 1, 9, 1, 2, 1]
+    starts = np.cumsum([0] + sizes)
+    srv = serve.Server(ctx, keys, model, hbm_budget_bytes=8 << 30, n_streams=2, small_pairs=2 * 8)
+    done = srv.run([(0.0, n) for n in sizes], lambda k, n: X_ct[starts[k]:starts[k] + n])
+    small = [r.batch for r in done if r.nX * 8 <= 16]
+    large = [r.batch for r in done if r.nX * 8 > 16]
+    assert not set(small) & set(large)                # the two classes never share a launch
+    for r in done:
+        assert torch.equal(r.out, _alone(ctx, keys, model, r.X_ct))

@@ -1,0 +1,109 @@
+"""Host-side scheduling logic of the serving loop, exercised on CPU with a fake context and
+fake CUDA objects: admission by class and HBM budget, fusion, and termination."""
+import types
+
+import pytest
+
+from paper_2204_05496_gb300 import serve
+
+
+class FakeEvent:
+    def __init__(self, *a, **k):
+        self.t = None
+
+    def record(self, stream=None):
+        self.t = serve.time.perf_counter()
+
+    def query(self):
+        return True
+
+    def elapsed_time(self, other):
+        return 1.0
+
+    def synchronize(self):
+        pass
+
+
+class FakeStream:
+    def __init__(self, priority=0):
+        self.priority = priority
+
+    @staticmethod
+    def priority_range():
+        return (0, -5)
+
+
+class _Ctx:
+    device = 0
+    N = 16
+
+    def __init__(self):
+        self.launches = []
+
+    def multi_workspace(self, model, nXs, chunk=0):
+        return 100 * sum(nXs)
+
+    def lr_scores_packed_multi(self, keys, model, xs, ws=None, pair_chunk=0, stream=None):
+        self.launches.append([x.shape[0] for x in xs])
+        return [object() for _ in xs]
+
+
+class _X:
+    def __init__(self, n):
+        self.shape = (n,)
+
+
+@pytest.fixture
+def fake_torch():
+    class _Cuda:
+        Stream = FakeStream
+        Event = FakeEvent
+
+        @staticmethod
+        def synchronize():
+            pass
+
+        @staticmethod
+        def stream(s):
+            class _C:
+                def __enter__(self):
+                    return s
+
+                def __exit__(self, *a):
+                    return False
+            return _C()
+
+    return types.SimpleNamespace(cuda=_Cuda, empty=lambda *a, **k: None, uint8=None)
+
+
+def make(fake_torch, **kw):
+    ctx = _Ctx()
+    srv = serve.Server(ctx, None, types.SimpleNamespace(nY=2), torch_module=fake_torch, **kw)
+    return srv, ctx
+
+
+def test_both_classes_launch_when_only_large_requests_wait(fake_torch):
+    srv, ctx = make(fake_torch, hbm_budget_bytes=10 ** 6, n_streams=2, small_pairs=4)
+    srv.start()
+    srv.submit(0, _X(9))          # 18 pairs: large class only
+    srv.step()
+    assert ctx.launches == [[9]]
+
+
+def test_fusion_respects_budget_and_classes(fake_torch):
+    srv, ctx = make(fake_torch, hbm_budget_bytes=500, n_streams=2, small_pairs=4)
+    srv.start()
+    for k, n in enumerate([1, 2, 1, 3, 1]):   # small: 1, 2, 1, 1 (<= 2 individuals), large: 3
+        srv.submit(k, _X(n))
+    srv.step()
+    # small stream fuses small requests until the 500-byte budget (100 bytes per individual)
+    # is reached; the large stream gets nothing because the budget is used up
+    assert ctx.launches[0] == [1, 2, 1, 1]
+    srv.step()                    # first launch retired (fake events complete) -> room again
+    assert [3] in ctx.launches
+
+
+def test_request_larger_than_budget_raises(fake_torch):
+    srv, ctx = make(fake_torch, hbm_budget_bytes=150, n_streams=2)
+    with pytest.raises(MemoryError):
+        srv.run([(0.0, 2)], lambda k, n: _X(n), max_seconds=5)
