@@ -195,17 +195,21 @@ __device__ __forceinline__ void ntt_forward(u64 *sm, const ModTab &T, int C, int
     fwd_passes<LOGM, NT, 0, 0>(sm, T, C, hidx, load, store);
 }
 
-// ------------------------------------------------------------------ inverse NTT driver (full size)
-// load(p) must return values < 2q in the bit-reversed evaluation layout; store(p, v) gets
-// coefficient p in [0, q).
+// ------------------------------------------------------------------ inverse NTT driver
+//
+// Runs the first LOGM Gentleman-Sande stages of the size-2^LOGN inverse transform on the
+// sub-array `hidx` of M = 2^LOGM consecutive evaluation positions (their butterflies never
+// leave it). With LOGM = LOGN this is the whole transform and N^-1 is folded into its last
+// stage. load(p) must return values < 2q (local position p); store(p, v) receives local
+// position p in [0, q) -- for the whole transform, coefficient p.
 
-template <int LOGN, int NT, int P, int S, class Load, class Store>
-__device__ __forceinline__ void inv_passes(u64 *sm, const ModTab &T, Load &load, Store &store) {
-    constexpr int NP = Sched<LOGN>::NP;
-    constexpr int R = Sched<LOGN>::template R<P>::value;
-    constexpr int N = 1 << LOGN;
+template <int LOGN, int LOGM, int NT, int P, int S, class Load, class Store>
+__device__ __forceinline__ void inv_passes(u64 *sm, const ModTab &T, int hidx, Load &load, Store &store) {
+    constexpr int NP = Sched<LOGM>::NP;
+    constexpr int R = Sched<LOGM>::template R<P>::value;
+    constexpr int M = 1 << LOGM;
     constexpr int TL = 1 << S;
-    constexpr int G = N >> R;
+    constexpr int G = M >> R;
     const u64 q = T.q, q2 = T.q2;
 #pragma unroll 1
     for (int g = threadIdx.x; g < G; g += NT) {
@@ -217,7 +221,8 @@ __device__ __forceinline__ void inv_passes(u64 *sm, const ModTab &T, Load &load,
             if constexpr (P == 0) x[r] = load(base + r * TL);
             else x[r] = sm[padi(base + r * TL)];
         }
-        inv_radix<R, P == NP - 1>(x, S, block, N, T.iw, T.ninv, T.ninvp, T.ilast, T.ilastp, q, q2);
+        inv_radix<R, LOGM == LOGN && P == NP - 1>(x, S, (hidx << (LOGM - S - R)) + block, 1 << LOGN, T.iw, T.ninv,
+                                                  T.ninvp, T.ilast, T.ilastp, q, q2);
 #pragma unroll
         for (int r = 0; r < (1 << R); ++r) {
             if constexpr (P == NP - 1) store(base + r * TL, red1(x[r], q));
@@ -226,13 +231,13 @@ __device__ __forceinline__ void inv_passes(u64 *sm, const ModTab &T, Load &load,
     }
     if constexpr (P < NP - 1) {
         __syncthreads();
-        inv_passes<LOGN, NT, P + 1, S + R>(sm, T, load, store);
+        inv_passes<LOGN, LOGM, NT, P + 1, S + R>(sm, T, hidx, load, store);
     }
 }
 
 template <int LOGN, int NT, class Load, class Store>
 __device__ __forceinline__ void ntt_inverse(u64 *sm, const ModTab &T, Load load, Store store) {
-    inv_passes<LOGN, NT, 0, 0>(sm, T, load, store);
+    inv_passes<LOGN, LOGN, NT, 0, 0>(sm, T, 0, load, store);
 }
 
 // ------------------------------------------------------------------ index maps
@@ -288,6 +293,115 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, u32 bytes, 
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
+}
+
+// ------------------------------------------------------------------ limbs split over a CTA pair
+//
+// Threads per CTA for a transform of 2^logm points.
+constexpr int nt_for(int logm) { return logm >= 13 ? 512 : (logm == 12 ? 256 : 128); }
+
+// A limb of N = 32768 points (256 KB) is larger than one CTA's shared memory. Such a limb is
+// handled by a cluster of S = 2 CTAs; CTA h (its rank in the cluster) owns the evaluation
+// positions and the coefficients [h M, (h+1) M), M = N/2:
+//  * forward: the first Cooley-Tukey stage (distance N/2) is done in the load -- each CTA
+//    reads both halves of the input -- and CTA h runs the remaining stages on its half;
+//  * inverse: CTA h runs the first log2 N - 1 Gentleman-Sande stages on its own half of the
+//    evaluation points (their butterflies stay inside it); after a cluster barrier the last
+//    stage (distance N/2, with N^-1) reads the partner's half from distributed shared memory.
+// For N <= 16384, S = 1 and these are the single-CTA transforms.
+template <int LOGN> struct Split {
+    static constexpr int S = LOGN > 14 ? 2 : 1;
+    static constexpr int LOGM = LOGN - (S == 2 ? 1 : 0);
+    static constexpr int M = 1 << LOGM;
+    static constexpr int NT = nt_for(LOGM);
+};
+
+__device__ __forceinline__ u32 cluster_rank() {
+    u32 r;
+    asm volatile("mov.u32 %0, %%cluster_ctarank;" : "=r"(r));
+    return r;
+}
+// All threads of all CTAs of the cluster; orders shared-memory writes before the barrier
+// with reads after it, across the cluster.
+__device__ __forceinline__ void cluster_sync() {
+    asm volatile("barrier.cluster.arrive.release.aligned;\n\tbarrier.cluster.wait.acquire.aligned;" ::: "memory");
+}
+// Shared-memory address of `p` in the CTA of cluster rank `rank`.
+__device__ __forceinline__ u32 cluster_map(const void *p, u32 rank) {
+    u32 r;
+    asm volatile("mapa.shared::cluster.u32 %0, %1, %2;" : "=r"(r) : "r"(smem_addr(p)), "r"(rank));
+    return r;
+}
+__device__ __forceinline__ u64 ld_cluster(u32 addr) {
+    u64 v;
+    asm volatile("ld.shared::cluster.u64 %0, [%1];" : "=l"(v) : "r"(addr) : "memory");
+    return v;
+}
+
+// The first C Cooley-Tukey stages of a size-N forward transform, restricted to the outputs
+// that land in sub-array `hidx` of size N/2^C: v[k] = input at p + k N/2^C (< 4q); returns
+// the stage-C value at local position p of the sub-array (< 4q).
+template <int C>
+__device__ __forceinline__ u64 fold_stages(const ModTab &T, int hidx, u64 (&v)[1 << C]) {
+    const u64 q = T.q, q2 = T.q2;
+#pragma unroll
+    for (int s = 0; s < C; ++s) {
+        const int half = 1 << (C - 1 - s);
+        const int side = (hidx >> (C - 1 - s)) & 1;
+        const ulonglong2 w = __ldg(T.fw + (1 << s) + (hidx >> (C - s)));
+#pragma unroll
+        for (int k = 0; k < half; ++k) {
+            const u64 a = red2(v[k], q2), t = mul_shoup(v[k + half], w.x, w.y, q);
+            v[k] = side ? a - t + q2 : a + t;
+        }
+    }
+    return v[0];
+}
+
+// Forward transform of one limb by CTA h of its group: load(k) returns coefficient k (< 4q,
+// any k < N); store(p, v) receives the evaluation positions p this CTA owns, in [0, q).
+template <int LOGN, class Load, class Store>
+__device__ __forceinline__ void limb_forward(u64 *sm, const ModTab &T, int h, Load load, Store store) {
+    using SP = Split<LOGN>;
+    if constexpr (SP::S == 1) {
+        ntt_forward<LOGN, SP::NT>(sm, T, 0, 0, load, store);
+    } else {
+        ntt_forward<SP::LOGM, SP::NT>(
+            sm, T, 1, h,
+            [&](int p) {
+                u64 v[2] = {load(p), load(p + SP::M)};
+                return fold_stages<1>(T, h, v);
+            },
+            [&](int p, u64 v) { store(h * SP::M + p, v); });
+    }
+}
+
+// Inverse transform of one limb by CTA h of its group: load(p) returns evaluation position p
+// (< 2q) for the positions this CTA owns; store(k, v) receives the coefficients k it owns,
+// in [0, q). With S = 2 every thread of the cluster must call it (two cluster barriers), and
+// sm must not be written by the caller between the call and the caller's next barrier.
+template <int LOGN, class Load, class Store>
+__device__ __forceinline__ void limb_inverse(u64 *sm, const ModTab &T, int h, Load load, Store store) {
+    using SP = Split<LOGN>;
+    if constexpr (SP::S == 1) {
+        ntt_inverse<LOGN, SP::NT>(sm, T, load, store);
+    } else {
+        constexpr int M = SP::M;
+        auto ld = [&](int p) { return load(h * M + p); };
+        auto st = [&](int p, u64 v) { sm[padi(p)] = v; };
+        inv_passes<LOGN, SP::LOGM, SP::NT, 0, 0>(sm, T, h, ld, st);
+        cluster_sync();
+        const u32 peer = cluster_map(sm, (u32)(h ^ 1));
+        const u64 q = T.q, q2 = T.q2;
+#pragma unroll 4
+        for (int p = threadIdx.x; p < M; p += SP::NT) {
+            const u64 own = sm[padi(p)], other = ld_cluster(peer + 8u * (u32)padi(p));
+            const u64 x0 = h == 0 ? own : other, x1 = h == 0 ? other : own;
+            const u64 v = h == 0 ? mul_shoup(x0 + x1, T.ninv, T.ninvp, q) : mul_shoup(x0 - x1 + q2, T.ilast, T.ilastp, q);
+            store(h * M + p, red1(v, q));
+        }
+        cluster_sync();
+    }
 }
 
 // ------------------------------------------------------------------ ChaCha20 (RFC 8439)

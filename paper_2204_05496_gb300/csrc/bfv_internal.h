@@ -121,6 +121,40 @@ struct ProfScope {
         if (e_ != cudaSuccess) return BFV_ERR_CUDA;     \
     } while (0)
 
+// Per-limb kernels run Split<LOGN>::S CTAs per limb (a two-CTA cluster at N = 32768): `h` is
+// the CTA's part of the limb, `unit` the limb's index in the grid.
+#define LIMB_KERNEL(LOGN) __global__ void __launch_bounds__(Split<LOGN>::NT)
+#define LIMB_INDEX(LOGN)                                                    \
+    constexpr int N = 1 << LOGN, M = Split<LOGN>::M;                        \
+    const int h = Split<LOGN>::S == 1 ? 0 : (int)cluster_rank();            \
+    const u32 unit = blockIdx.x / Split<LOGN>::S;                           \
+    (void)N; (void)M; (void)h; (void)unit
+
+// Launches a per-limb kernel over `units` limbs: Split<LOGN>::S CTAs of Split<LOGN>::NT
+// threads per limb (one two-CTA cluster per limb when S = 2), limb_smem<LOGN>() bytes of
+// dynamic shared memory unless `smem` says otherwise.
+template <int LOGN> constexpr size_t limb_smem() { return sizeof(u64) * PadSize<Split<LOGN>::M>::value; }
+template <int LOGN, class... KArgs, class... Args>
+cudaError_t launch_limbs(void (*kern)(KArgs...), size_t units, cudaStream_t st, size_t smem, Args... args) {
+    using SP = Split<LOGN>;
+    if (!units) return cudaSuccess;
+    if (!smem) smem = limb_smem<LOGN>();
+    cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3((unsigned)(units * SP::S), 1, 1);
+    cfg.blockDim = dim3(SP::NT, 1, 1);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = st;
+    cudaLaunchAttribute at[1];
+    at[0].id = cudaLaunchAttributeClusterDimension;
+    at[0].val.clusterDim.x = SP::S;
+    at[0].val.clusterDim.y = 1;
+    at[0].val.clusterDim.z = 1;
+    cfg.attrs = at;
+    cfg.numAttrs = SP::S > 1 ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kern, args...);
+}
+
 // ------------------------------------------------------------------ launchers (k_*.cu)
 // Each returns BFV_OK or BFV_ERR_CUDA (launch error); all are asynchronous on `st`.
 
@@ -171,5 +205,3 @@ size_t standard_smem_bytes();
 int launch_standard(const bfv_ctx *c, const bfv_model *m, const u64 *X_ct, u64 *Y_ct, void *ws, const StandardPlan &pl,
                     cudaStream_t st);
 
-// Threads per CTA for a transform of 2^logm points.
-constexpr int nt_for(int logm) { return logm >= 14 ? 512 : (logm == 13 ? 512 : (logm == 12 ? 256 : 128)); }

@@ -180,7 +180,7 @@ int gaussian_table_h(uint32_t num, uint32_t den, u64 *out) {
 
 bool params_ok(const bfv_params *p) {
     if (!p) return false;
-    if (p->N != 4096 && p->N != 8192 && p->N != 16384) return false;
+    if (p->N != 4096 && p->N != 8192 && p->N != 16384 && p->N != 32768) return false;
     if (p->L < 1 || p->L > BFV_MAXP - 1) return false;
     if (p->prime_bits < 30 || p->prime_bits > 60) return false;
     if (p->t < 3 || p->t >= (1ull << 31) || (p->t - 1) % (2ull * p->N) != 0 || !is_prime_h(p->t)) return false;

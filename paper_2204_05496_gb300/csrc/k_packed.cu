@@ -21,7 +21,6 @@
 
 namespace {
 
-template <int M> constexpr size_t pad_bytes() { return sizeof(u64) * PadSize<M>::value; }
 template <class K> void set_smem(K kern, size_t bytes) {
     cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
@@ -64,24 +63,35 @@ __global__ void __launch_bounds__(256) k_mac(const ModTab *__restrict__ mods, in
 
 // ------------------------------------------------------------------ key switching
 
-// grid.x = (g, c, l). c = 1: digit D[g][l] = INTT(sigma(C1[g][l])); c = 0: C0 += sigma(C0).
+// Limb unit (g, c, l). c = 1: digit D[g][l] = INTT(sigma(C1[g][l])); c = 0: C0 += sigma(C0).
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 gal, u64 *C,
-                                                           u64 *D) {
+LIMB_KERNEL(LOGN) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 gal, u64 *C, u64 *D) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
-    const int l = blockIdx.x % L, c = (blockIdx.x / L) % 2;
-    const size_t g = blockIdx.x / (2 * L);
+    LIMB_INDEX(LOGN);
+    constexpr int NT = Split<LOGN>::NT;
+    const int l = (int)(unit % L), c = (int)((unit / L) % 2);
+    const size_t g = unit / (2 * L);
     const ModTab T = mods[l];
     u64 *limb = C + ((g * 2 + c) * L + l) * (size_t)N;
     if (c == 1) {
         u64 *dst = D + (g * L + l) * (size_t)N;
-        ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return limb[auto_src(p, gal, LOGN)]; },
-                              [&](int p, u64 v) { dst[p] = v; });
-    } else {
+        limb_inverse<LOGN>(sm, T, h, [&](int p) { return limb[auto_src(p, gal, LOGN)]; },
+                           [&](int p, u64 v) { dst[p] = v; });
+    } else if constexpr (Split<LOGN>::S == 1) {
         for (int p = threadIdx.x; p < N; p += NT) sm[p] = limb[p];
         __syncthreads();
         for (int p = threadIdx.x; p < N; p += NT) limb[p] = add_mod(sm[p], sm[auto_src(p, gal, LOGN)], T.q);
+    } else {
+        // the permuted operand may sit in the partner CTA's half
+        for (int p = threadIdx.x; p < M; p += NT) sm[p] = limb[h * M + p];
+        cluster_sync();
+        const u32 peer = cluster_map(sm, (u32)(h ^ 1));
+        for (int p = threadIdx.x; p < M; p += NT) {
+            const int src = auto_src(h * M + p, gal, LOGN);
+            const u64 b = (src / M == h) ? sm[src & (M - 1)] : ld_cluster(peer + 8u * (u32)(src & (M - 1)));
+            limb[h * M + p] = add_mod(sm[p], b, T.q);
+        }
+        cluster_sync();
     }
 }
 
@@ -111,21 +121,33 @@ __device__ __forceinline__ void key_mac(u64 *acc0, u64 *acc1, const shoup_t *__r
     }
 }
 
-// grid.x = (g, j, h): U[g][c][j][h N/2 + p] = sum_i NTT_j(D[g][i] mod q_j)[h N/2 + p] * key[i][c][j].
+// ModUp splits each target limb into QS sub-arrays of H = N/QS evaluation points (QS = 2, or
+// 4 at N = 32768) so that the transform and both key-product accumulators fit one CTA's
+// shared memory; the first log2 QS Cooley-Tukey stages are done in the load.
+template <int LOGN> struct ModUpShape {
+    static constexpr int QS = LOGN > 14 ? 4 : 2;
+    static constexpr int C = QS == 4 ? 2 : 1;
+    static constexpr int LOGH = LOGN - C;
+    static constexpr int H = 1 << LOGH;
+    static constexpr int NT = nt_for(LOGH);
+    static constexpr size_t smem = sizeof(u64) * (PadSize<H>::value + 2 * H);
+};
+
+// grid.x = (g, j, h): U[g][c][j][h H + p] = sum_i NTT_j(D[g][i] mod q_j)[h H + p] * key[i][c][j].
 // The digit of index j itself is sigma(C1[g][j]) in evaluation form already (a permuted read).
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN - 1)) k_ks_modup(const ModTab *__restrict__ mods, int L, u32 gal,
-                                                                const u64 *__restrict__ C, const u64 *__restrict__ D,
-                                                                const shoup_t *__restrict__ key, u64 *U) {
+__global__ void __launch_bounds__(ModUpShape<LOGN>::NT) k_ks_modup(const ModTab *__restrict__ mods, int L, u32 gal,
+                                                                  const u64 *__restrict__ C, const u64 *__restrict__ D,
+                                                                  const shoup_t *__restrict__ key, u64 *U) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, H = N / 2, NT = nt_for(LOGN - 1);
+    using MS = ModUpShape<LOGN>;
+    constexpr int N = 1 << LOGN, H = MS::H, NT = MS::NT, QS = MS::QS;
     u64 *acc0 = sm + PadSize<H>::value, *acc1 = acc0 + H;
     const int nqp = L + 1;
-    const int h = blockIdx.x % 2, j = (blockIdx.x / 2) % nqp;
-    const size_t g = blockIdx.x / (2 * nqp);
+    const int h = blockIdx.x % QS, j = (blockIdx.x / QS) % nqp;
+    const size_t g = blockIdx.x / (QS * nqp);
     const ModTab T = mods[j];
     const u64 q = T.q, q2 = T.q2;
-    const shoup_t w1 = T.fw[1];
     for (int p = threadIdx.x; p < H; p += NT) { acc0[p] = 0; acc1[p] = 0; }
     const size_t keystride = (size_t)nqp * N;     // one (digit, component) block
 #pragma unroll 1
@@ -136,13 +158,14 @@ __global__ void __launch_bounds__(nt_for(LOGN - 1)) k_ks_modup(const ModTab *__r
             const u64 *c1 = C + ((g * 2 + 1) * L + j) * (size_t)N;
             key_mac<H, NT>(acc0, acc1, k0, k1, q, q2, [&](int p) { return c1[auto_src(h * H + p, gal, LOGN)]; });
         } else {
-            const u64 *d = D + (g * L + i) * (size_t)N;
-            ntt_forward<LOGN - 1, NT>(
-                sm, T, 1, h,
+            const u64 *d = D + (g * L + i) * (size_t)N;   // digit i < q_i < 2 q_j
+            ntt_forward<MS::LOGH, NT>(
+                sm, T, MS::C, h,
                 [&](int p) {
-                    const u64 a = red1(d[p], q), b = red1(d[p + H], q);
-                    const u64 t = mul_shoup(b, w1, q);
-                    return h == 0 ? a + t : a - t + q2;
+                    u64 v[QS];
+#pragma unroll
+                    for (int k = 0; k < QS; ++k) v[k] = d[p + k * H];
+                    return fold_stages<MS::C>(T, h, v);
                 },
                 [&](int p, u64 v) { sm[padi(p)] = v; });
             __syncthreads();
@@ -155,41 +178,40 @@ __global__ void __launch_bounds__(nt_for(LOGN - 1)) k_ks_modup(const ModTab *__r
     for (int p = threadIdx.x; p < H; p += NT) { u0[p] = red1(acc0[p], q); u1[p] = red1(acc1[p], q); }
 }
 
-// grid.x = (g, c): R[g][c] = [INTT_P(U[g][c][P]) + floor(P/2)]_P.
+// Limb unit (g, c): R[g][c] = [INTT_P(U[g][c][P]) + floor(P/2)]_P.
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_ks_moddown_p(const ModTab *__restrict__ mods, int L,
-                                                                const u64 *__restrict__ U, u64 *R) {
+LIMB_KERNEL(LOGN) k_ks_moddown_p(const ModTab *__restrict__ mods, int L, const u64 *__restrict__ U, u64 *R) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    LIMB_INDEX(LOGN);
     const int nqp = L + 1;
-    const size_t gc = blockIdx.x;
+    const size_t gc = unit;
     const ModTab T = mods[L];
     const u64 *src = U + (gc * nqp + L) * (size_t)N;
     u64 *dst = R + gc * N;
-    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return src[p]; },
-                          [&](int p, u64 v) { dst[p] = add_mod(v, T.phalf, T.q); });
+    limb_inverse<LOGN>(sm, T, h, [&](int p) { return src[p]; },
+                       [&](int p, u64 v) { dst[p] = add_mod(v, T.phalf, T.q); });
 }
 
-// grid.x = (g, c, l): C[g][c][l] += (U[g][c][l] + NTT_l(floor(P/2) - r)) * P^-1.
+// Limb unit (g, c, l): C[g][c][l] += (U[g][c][l] + NTT_l(floor(P/2) - r)) * P^-1.
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_ks_moddown(const ModTab *__restrict__ mods, int L,
-                                                              const u64 *__restrict__ U, const u64 *__restrict__ R,
-                                                              u64 *C) {
+LIMB_KERNEL(LOGN) k_ks_moddown(const ModTab *__restrict__ mods, int L, const u64 *__restrict__ U,
+                               const u64 *__restrict__ R, u64 *C) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    LIMB_INDEX(LOGN);
+    constexpr int NT = Split<LOGN>::NT;
     const int nqp = L + 1;
-    const int l = blockIdx.x % L, c = (blockIdx.x / L) % 2;
-    const size_t g = blockIdx.x / (2 * L);
+    const int l = (int)(unit % L), c = (int)((unit / L) % 2);
+    const size_t g = unit / (2 * L);
     const ModTab T = mods[l];
     const u64 *r = R + (g * 2 + c) * (size_t)N;
-    ntt_forward<LOGN, NT>(sm, T, 0, 0, [&](int p) { return T.phalf + (T.q - red1(r[p], T.q)); },
-                          [&](int p, u64 v) { sm[padi(p)] = v; });
+    limb_forward<LOGN>(sm, T, h, [&](int p) { return T.phalf + (T.q - red1(r[p], T.q)); },
+                       [&](int p, u64 v) { sm[padi(p & (M - 1))] = v; });
     __syncthreads();
-    const u64 *u = U + ((g * 2 + c) * nqp + l) * (size_t)N;
-    u64 *dst = C + ((g * 2 + c) * L + l) * (size_t)N;
-    static_assert(N % (4 * NT) == 0, "points per thread must be a multiple of 4");
+    const u64 *u = U + ((g * 2 + c) * nqp + l) * (size_t)N + (size_t)h * M;
+    u64 *dst = C + ((g * 2 + c) * L + l) * (size_t)N + (size_t)h * M;
+    static_assert(M % (4 * NT) == 0, "points per thread must be a multiple of 4");
 #pragma unroll 1
-    for (int p0 = threadIdx.x; p0 < N; p0 += 4 * NT) {
+    for (int p0 = threadIdx.x; p0 < M; p0 += 4 * NT) {
         u64 a[4], b[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) { a[e] = u[p0 + e * NT]; b[e] = dst[p0 + e * NT]; }
@@ -203,16 +225,16 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_ks_moddown(const ModTab *__res
 }
 
 // ------------------------------------------------------------------ bias + mask (lines 18-22)
-// grid.x = (g, l): C0 += Delta [b_j]_t; C *= NTT(centred lift of the one-hot plaintext at slot
+// Limb unit (g, l): C0 += Delta [b_j]_t; C *= NTT(centred lift of the one-hot plaintext at slot
 // (g0+g) mod N), whose coefficient k is N^-1 omega^(-e k) mod t, e the slot's exponent.
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_bias_mask(const ModTab *__restrict__ mods, int L, int tmod, int nY,
-                                                             size_t g0, const ReqTable rt, const u32 *__restrict__ maskpow,
-                                                             const u64 *__restrict__ bias_delta, u64 *C) {
+LIMB_KERNEL(LOGN) k_bias_mask(const ModTab *__restrict__ mods, int L, int tmod, int nY, size_t g0, const ReqTable rt,
+                              const u32 *__restrict__ maskpow, const u64 *__restrict__ bias_delta, u64 *C) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
-    const int l = blockIdx.x % L;
-    const size_t gl = blockIdx.x / L, gp = g0 + gl;
+    LIMB_INDEX(LOGN);
+    constexpr int NT = Split<LOGN>::NT;
+    const int l = (int)(unit % L);
+    const size_t gl = unit / L, gp = g0 + gl;
     const size_t g = gp - rt.pair_start[req_of(rt, gp)];
     const int j = (int)(g % nY), s = (int)(g % N);
     const ModTab T = mods[l];
@@ -224,18 +246,19 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_bias_mask(const ModTab *__rest
         base = (base * base) & (twoN - 1);
     }
     if (s >= N / 2) e = twoN - e;
-    ntt_forward<LOGN, NT>(
-        sm, T, 0, 0,
+    limb_forward<LOGN>(
+        sm, T, h,
         [&](int p) {
             const u32 idx = (twoN - ((e * (u32)p) & (twoN - 1))) & (twoN - 1);
             const u64 v = maskpow[idx];
             return v <= th ? v : T.q - (t - v);
         },
-        [&](int p, u64 v) { sm[padi(p)] = v; });
+        [&](int p, u64 v) { sm[padi(p & (M - 1))] = v; });
     __syncthreads();
     const u64 bd = bias_delta[(size_t)j * L + l];
-    u64 *c0 = C + ((gl * 2 + 0) * L + l) * (size_t)N, *c1 = C + ((gl * 2 + 1) * L + l) * (size_t)N;
-    for (int p = threadIdx.x; p < N; p += NT) {
+    u64 *c0 = C + ((gl * 2 + 0) * L + l) * (size_t)N + (size_t)h * M;
+    u64 *c1 = C + ((gl * 2 + 1) * L + l) * (size_t)N + (size_t)h * M;
+    for (int p = threadIdx.x; p < M; p += NT) {
         const u64 m = sm[padi(p)];
         c0[p] = mul_barrett(add_mod(c0[p], bd, T.q), m, T.q, T.mu, T.bits);
         c1[p] = mul_barrett(c1[p], m, T.q, T.mu, T.bits);
@@ -262,15 +285,14 @@ __global__ void __launch_bounds__(256) k_compress(const ModTab *__restrict__ mod
     Yacc[e] = acc;
 }
 
-// Pair state (evaluation form) -> coefficient form.
+// Pair state (evaluation form) -> coefficient form; limb unit x uses modulus x % L.
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_intt_copy(const ModTab *__restrict__ mods, int L,
-                                                             const u64 *__restrict__ in, u64 *out) {
+LIMB_KERNEL(LOGN) k_intt_copy(const ModTab *__restrict__ mods, int L, const u64 *__restrict__ in, u64 *out) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
-    const size_t x = blockIdx.x;
+    LIMB_INDEX(LOGN);
+    const size_t x = unit;
     const ModTab T = mods[x % L];
-    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return in[x * N + p]; }, [&](int p, u64 v) { out[x * N + p] = v; });
+    limb_inverse<LOGN>(sm, T, h, [&](int p) { return in[x * N + p]; }, [&](int p, u64 v) { out[x * N + p] = v; });
 }
 
 int last_err() { return cudaGetLastError() == cudaSuccess ? BFV_OK : BFV_ERR_CUDA; }
@@ -283,12 +305,8 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, int nreq
     const size_t ctw = 2 * (size_t)L * N;
     u64 *Xe = (u64 *)(ws + pl.off_xntt), *Yacc = (u64 *)(ws + pl.off_yacc), *C = (u64 *)(ws + pl.off_state);
     u64 *D = (u64 *)(ws + pl.off_digits), *U = (u64 *)(ws + pl.off_u), *R = (u64 *)(ws + pl.off_r);
-    const size_t full = pad_bytes<N>(), half = pad_bytes<N / 2>() + 2 * sizeof(u64) * (N / 2);
-    set_smem(k_ks_prep<LOGN>, full);
-    set_smem(k_ks_modup<LOGN>, half);
-    set_smem(k_ks_moddown_p<LOGN>, full);
-    set_smem(k_ks_moddown<LOGN>, full);
-    set_smem(k_bias_mask<LOGN>, full);
+    using MS = ModUpShape<LOGN>;
+    set_smem(k_ks_modup<LOGN>, MS::smem);
 
     int rc;
     for (int r = 0; r < nreq; ++r)
@@ -305,18 +323,18 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, int nreq
             const u32 gal = (u32)c->galois[s];
             const shoup_t *key = k->gk_eval + (size_t)s * keyblock;
             { ProfScope pr(c, BFV_K_KS_PREP, st);
-              k_ks_prep<LOGN><<<(unsigned)(ng * 2 * L), nt_for(LOGN), full, st>>>(c->dmods, L, gal, C, D); }
+              launch_limbs<LOGN>(k_ks_prep<LOGN>, ng * 2 * L, st, 0, c->dmods, L, gal, C, D); }
             { ProfScope pr(c, BFV_K_KS_MODUP, st);
-              k_ks_modup<LOGN><<<(unsigned)(ng * nqp * 2), nt_for(LOGN - 1), half, st>>>(c->dmods, L, gal, C, D, key, U); }
+              k_ks_modup<LOGN><<<(unsigned)(ng * nqp * MS::QS), MS::NT, MS::smem, st>>>(c->dmods, L, gal, C, D, key, U); }
             { ProfScope pr(c, BFV_K_KS_MODDOWN_P, st);
-              k_ks_moddown_p<LOGN><<<(unsigned)(ng * 2), nt_for(LOGN), full, st>>>(c->dmods, L, U, R); }
+              launch_limbs<LOGN>(k_ks_moddown_p<LOGN>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R); }
             { ProfScope pr(c, BFV_K_KS_MODDOWN, st);
-              k_ks_moddown<LOGN><<<(unsigned)(ng * 2 * L), nt_for(LOGN), full, st>>>(c->dmods, L, U, R, C); }
+              launch_limbs<LOGN>(k_ks_moddown<LOGN>, ng * 2 * L, st, 0, c->dmods, L, (const u64 *)U, (const u64 *)R, C); }
             count_launch(c, 4);
         }
         { ProfScope pr(c, BFV_K_BIAS_MASK, st);
-        k_bias_mask<LOGN><<<(unsigned)(ng * L), nt_for(LOGN), full, st>>>(c->dmods, L, nqp, (int)pl.nY, g0, pl.rt,
-                                                                         c->dmaskpow, m->bias_delta, C); }
+        launch_limbs<LOGN>(k_bias_mask<LOGN>, ng * L, st, 0, c->dmods, L, nqp, (int)pl.nY, g0, pl.rt,
+                           (const u32 *)c->dmaskpow, (const u64 *)m->bias_delta, C); }
         count_launch(c);
         // compression: the pairs of request r that land in its output o are one contiguous range
         for (int r = 0; r < nreq; ++r) {
@@ -392,6 +410,7 @@ int launch_packed_multi(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m,
         case 12: return run_packed<12>(c, k, m, nreq, X_ct, Y_ct, (char *)ws, plan, st);
         case 13: return run_packed<13>(c, k, m, nreq, X_ct, Y_ct, (char *)ws, plan, st);
         case 14: return run_packed<14>(c, k, m, nreq, X_ct, Y_ct, (char *)ws, plan, st);
+        case 15: return run_packed<15>(c, k, m, nreq, X_ct, Y_ct, (char *)ws, plan, st);
         default: return BFV_ERR_BAD_PARAMS;
     }
 }
@@ -406,15 +425,12 @@ int launch_pair_export(const bfv_ctx *c, const PackedPlan &plan, const void *ws,
                        cudaStream_t st) {
     const size_t ctw = 2 * (size_t)c->L * c->N;
     const u64 *C = (const u64 *)((const char *)ws + plan.off_state) + slot * ctw;
-#define L_(LG)                                                                                              \
-    {                                                                                                       \
-        set_smem(k_intt_copy<LG>, pad_bytes<(1 << LG)>());                                                  \
-        k_intt_copy<LG><<<2 * c->L, nt_for(LG), pad_bytes<(1 << LG)>(), st>>>(c->dmods, c->L, C, ct_out);   \
-    }
+#define L_(LG) launch_limbs<LG>(k_intt_copy<LG>, 2 * c->L, st, 0, c->dmods, c->L, C, ct_out)
     switch (c->logN) {
         case 12: L_(12); break;
         case 13: L_(13); break;
         case 14: L_(14); break;
+        case 15: L_(15); break;
         default: return BFV_ERR_BAD_PARAMS;
     }
 #undef L_

@@ -1,16 +1,13 @@
 // k_scheme.cu -- BFV scheme kernels: limb NTTs, batch encode/decode, key generation,
 // public-key encryption and exact decryption, model (weight) encoding.
+//
+// Every per-limb kernel runs Split<LOGN>::S CTAs per limb (a cluster of two at N = 32768,
+// one otherwise): `h` is the CTA's part of the limb, `unit` the limb's index in the grid.
 #include "bfv_internal.h"
 
 namespace {
 
 constexpr int kSkPurpose = 1, kPkA = 2, kPkE = 3, kGkA = 4, kGkE = 5, kEnc = 6;
-
-template <int LOGN> constexpr size_t smem_full() { return sizeof(u64) * PadSize<(1 << LOGN)>::value; }
-
-template <class K> void set_smem(K kern, size_t bytes) {
-    cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-}
 
 // uniform residue mod q from four ChaCha words taken as a 128-bit integer
 __device__ __forceinline__ u64 uniform_of(const u32 *w, const ModTab &T) {
@@ -20,106 +17,109 @@ __device__ __forceinline__ u64 uniform_of(const u32 *w, const ModTab &T) {
 }
 
 // ------------------------------------------------------------------ limb transforms
-// in/out: [nlimbs][N]; limb x uses modulus x % L.
+// in/out: [nlimbs][N]; limb x uses modulus x % L. The forward transform needs in != out.
 template <int LOGN, bool FWD>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_ntt_limbs(const ModTab *__restrict__ mods, int L,
-                                                             const u64 *in, u64 *out) {
+LIMB_KERNEL(LOGN) k_ntt_limbs(const ModTab *__restrict__ mods, int L, const u64 *in, u64 *out) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
-    const size_t x = blockIdx.x;
-    const ModTab T = mods[x % L];
-    const u64 *src = in + x * N;
-    u64 *dst = out + x * N;
+    LIMB_INDEX(LOGN);
+    const ModTab T = mods[unit % L];
+    const u64 *src = in + unit * N;
+    u64 *dst = out + unit * N;
     if constexpr (FWD)
-        ntt_forward<LOGN, NT>(sm, T, 0, 0, [&](int p) { return src[p]; }, [&](int p, u64 v) { dst[p] = v; });
+        limb_forward<LOGN>(sm, T, h, [&](int p) { return src[p]; }, [&](int p, u64 v) { dst[p] = v; });
     else
-        ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return src[p]; }, [&](int p, u64 v) { dst[p] = v; });
+        limb_inverse<LOGN>(sm, T, h, [&](int p) { return src[p]; }, [&](int p, u64 v) { dst[p] = v; });
 }
 
 // Inverse transform of evaluation-form {value, companion} arrays [limb][N]; limb x uses
-// modulus x % M; output [limb][N] coefficients.
+// modulus x % nmod; output [limb][N] coefficients.
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_intt_pairs(const ModTab *__restrict__ mods, int M,
-                                                              const shoup_t *__restrict__ in, u64 *out) {
+LIMB_KERNEL(LOGN) k_intt_pairs(const ModTab *__restrict__ mods, int nmod, const shoup_t *__restrict__ in, u64 *out) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
-    const size_t x = blockIdx.x;
-    const ModTab T = mods[x % M];
-    const shoup_t *src = in + x * N;
-    u64 *dst = out + x * N;
-    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return src[p].x; }, [&](int p, u64 v) { dst[p] = v; });
+    LIMB_INDEX(LOGN);
+    const ModTab T = mods[unit % nmod];
+    const shoup_t *src = in + unit * N;
+    u64 *dst = out + unit * N;
+    limb_inverse<LOGN>(sm, T, h, [&](int p) { return src[p].x; }, [&](int p, u64 v) { dst[p] = v; });
 }
 
 // ------------------------------------------------------------------ encode / decode (mod t)
+// A plaintext's slots are scattered to their evaluation positions (slot_pos) in shared
+// memory -- each CTA keeps the positions it owns -- then inverse-transformed mod t.
 
-// slots [count][N] -> plaintext [count][N]; slot l goes to evaluation position slot_pos[l].
+// slots [count][N] -> plaintext [count][N].
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_encode(const ModTab *__restrict__ mods, int tmod,
-                                                          const u32 *__restrict__ slot_pos, const int64_t *slots,
-                                                          u64 *pt) {
+LIMB_KERNEL(LOGN) k_encode(const ModTab *__restrict__ mods, int tmod, const u32 *__restrict__ slot_pos,
+                           const int64_t *slots, u64 *pt) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    LIMB_INDEX(LOGN);
     const ModTab T = mods[tmod];
-    const int64_t *src = slots + (size_t)blockIdx.x * N;
+    const int64_t *src = slots + unit * N;
     const int64_t t = (int64_t)T.q;
-    for (int l = threadIdx.x; l < N; l += NT) {
+    for (int l = threadIdx.x; l < N; l += Split<LOGN>::NT) {
+        const u32 pos = slot_pos[l];
+        if ((int)(pos / M) != h) continue;
         int64_t v = src[l] % t;
         if (v < 0) v += t;
-        sm[padi(slot_pos[l])] = (u64)v;
+        sm[padi(pos % M)] = (u64)v;
     }
     __syncthreads();
-    u64 *dst = pt + (size_t)blockIdx.x * N;
-    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return sm[padi(p)]; }, [&](int p, u64 v) { dst[p] = v; });
+    u64 *dst = pt + unit * N;
+    limb_inverse<LOGN>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) { dst[p] = v; });
 }
 
 // Packed features: plaintext (i, k) slot s = X[i][k N + s] (0 past f).
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_encode_features(const ModTab *__restrict__ mods, int tmod,
-                                                                   const u32 *__restrict__ slot_pos,
-                                                                   const uint8_t *__restrict__ X, size_t f, int K,
-                                                                   u64 *pt) {
+LIMB_KERNEL(LOGN) k_encode_features(const ModTab *__restrict__ mods, int tmod, const u32 *__restrict__ slot_pos,
+                                    const uint8_t *__restrict__ X, size_t f, int K, u64 *pt) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    LIMB_INDEX(LOGN);
     const ModTab T = mods[tmod];
-    const size_t i = blockIdx.x / K, k = blockIdx.x % K;
+    const size_t i = unit / K, k = unit % K;
     const uint8_t *row = X + i * f;
-    for (int s = threadIdx.x; s < N; s += NT) {
+    for (int s = threadIdx.x; s < N; s += Split<LOGN>::NT) {
+        const u32 pos = slot_pos[s];
+        if ((int)(pos / M) != h) continue;
         const size_t col = k * N + s;
-        sm[padi(slot_pos[s])] = col < f ? (u64)row[col] % T.q : 0;
+        sm[padi(pos % M)] = col < f ? (u64)row[col] % T.q : 0;
     }
     __syncthreads();
-    u64 *dst = pt + (size_t)blockIdx.x * N;
-    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return sm[padi(p)]; }, [&](int p, u64 v) { dst[p] = v; });
+    u64 *dst = pt + unit * N;
+    limb_inverse<LOGN>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) { dst[p] = v; });
 }
 
 // Feature columns: plaintext f' slot i = X[i][f'] for i < nX.
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_encode_columns(const ModTab *__restrict__ mods, int tmod,
-                                                                  const u32 *__restrict__ slot_pos,
-                                                                  const uint8_t *__restrict__ X, size_t nX, size_t f,
-                                                                  u64 *pt) {
+LIMB_KERNEL(LOGN) k_encode_columns(const ModTab *__restrict__ mods, int tmod, const u32 *__restrict__ slot_pos,
+                                   const uint8_t *__restrict__ X, size_t nX, size_t f, u64 *pt) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    LIMB_INDEX(LOGN);
     const ModTab T = mods[tmod];
-    const size_t col = blockIdx.x;
-    for (int s = threadIdx.x; s < N; s += NT) sm[padi(slot_pos[s])] = (size_t)s < nX ? (u64)X[s * f + col] % T.q : 0;
+    const size_t col = unit;
+    for (int s = threadIdx.x; s < N; s += Split<LOGN>::NT) {
+        const u32 pos = slot_pos[s];
+        if ((int)(pos / M) != h) continue;
+        sm[padi(pos % M)] = (size_t)s < nX ? (u64)X[s * f + col] % T.q : 0;
+    }
     __syncthreads();
     u64 *dst = pt + col * N;
-    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return sm[padi(p)]; }, [&](int p, u64 v) { dst[p] = v; });
+    limb_inverse<LOGN>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) { dst[p] = v; });
 }
 
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_decode(const ModTab *__restrict__ mods, int tmod,
-                                                          const u32 *__restrict__ slot_pos, const u64 *pt,
-                                                          int64_t *slots) {
+LIMB_KERNEL(LOGN) k_decode(const ModTab *__restrict__ mods, int tmod, const u32 *__restrict__ slot_pos, const u64 *pt,
+                           int64_t *slots) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    LIMB_INDEX(LOGN);
     const ModTab T = mods[tmod];
-    const u64 *src = pt + (size_t)blockIdx.x * N;
-    ntt_forward<LOGN, NT>(sm, T, 0, 0, [&](int p) { return src[p]; }, [&](int p, u64 v) { sm[padi(p)] = v; });
+    const u64 *src = pt + unit * N;
+    limb_forward<LOGN>(sm, T, h, [&](int p) { return src[p]; }, [&](int p, u64 v) { sm[padi(p & (M - 1))] = v; });
     __syncthreads();
-    int64_t *dst = slots + (size_t)blockIdx.x * N;
-    for (int l = threadIdx.x; l < N; l += NT) dst[l] = (int64_t)sm[padi(slot_pos[l])];
+    int64_t *dst = slots + unit * N;
+    for (int l = threadIdx.x; l < N; l += Split<LOGN>::NT) {
+        const u32 pos = slot_pos[l];
+        if ((int)(pos / M) == h) dst[l] = (int64_t)sm[padi(pos % M)];
+    }
 }
 
 // ------------------------------------------------------------------ key generation
@@ -134,38 +134,35 @@ __global__ void k_keygen_sk(u64 seed, int N, int8_t *sk) {
 
 // Evaluation form of s for every modulus of QP: out [nqp][N] {value, companion}.
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_keygen_sk_eval(const ModTab *__restrict__ mods,
-                                                                  const int8_t *__restrict__ sk, shoup_t *out) {
+LIMB_KERNEL(LOGN) k_keygen_sk_eval(const ModTab *__restrict__ mods, const int8_t *__restrict__ sk, shoup_t *out) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
-    const int j = blockIdx.x;
-    const ModTab T = mods[j];
-    shoup_t *dst = out + (size_t)j * N;
-    ntt_forward<LOGN, NT>(sm, T, 0, 0, [&](int p) { return lift_small(sk[p], T.q); },
-                          [&](int p, u64 v) { dst[p] = make_shoup(v, T.q); });
+    LIMB_INDEX(LOGN);
+    const ModTab T = mods[unit];
+    shoup_t *dst = out + unit * N;
+    limb_forward<LOGN>(sm, T, h, [&](int p) { return lift_small(sk[p], T.q); },
+                       [&](int p, u64 v) { dst[p] = make_shoup(v, T.q); });
 }
 
 // Public key limb l: pk1 = a (uniform), pk0 = -(a s + e); out [2][L][N] {value, companion}.
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_keygen_pk(const ModTab *__restrict__ mods, const u64 *__restrict__ cdt,
-                                                             int cdt_len, u64 seed, int L, const shoup_t *__restrict__ sk_eval,
-                                                             shoup_t *pk) {
+LIMB_KERNEL(LOGN) k_keygen_pk(const ModTab *__restrict__ mods, const u64 *__restrict__ cdt, int cdt_len, u64 seed,
+                              int L, const shoup_t *__restrict__ sk_eval, shoup_t *pk) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
-    const int l = blockIdx.x;
+    LIMB_INDEX(LOGN);
+    const int l = (int)unit;
     const ModTab T = mods[l];
     shoup_t *pk0 = pk + (size_t)l * N, *pk1 = pk + ((size_t)L + l) * N;
     const shoup_t *s = sk_eval + (size_t)l * N;
-    ntt_forward<LOGN, NT>(
-        sm, T, 0, 0,
+    limb_forward<LOGN>(
+        sm, T, h,
         [&](int p) { u32 w[16]; chacha20_block(seed, (u32)p, kPkA, 0, (u32)l, w); return uniform_of(w, T); },
         [&](int p, u64 v) {
             pk1[p] = make_shoup(v, T.q);
             pk0[p].x = red1(mul_shoup(v, s[p], T.q), T.q);   // a s, finished below
         });
     __syncthreads();
-    ntt_forward<LOGN, NT>(
-        sm, T, 0, 0,
+    limb_forward<LOGN>(
+        sm, T, h,
         [&](int p) { u32 w[16]; chacha20_block(seed, (u32)p, kPkE, 0, 0, w); return lift_small(gauss_of(w[0], w[1], w[2], cdt, cdt_len), T.q); },
         [&](int p, u64 v) { pk0[p] = make_shoup(sub_mod(0, add_mod(pk0[p].x, v, T.q), T.q), T.q); });
 }
@@ -173,21 +170,20 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_keygen_pk(const ModTab *__rest
 // Galois key (element gi, digit i, limb j of QP):
 //   k1 = a, k0 = -a s + e + [i == j] [P]_{q_j} sigma_g(s); out [ng][L][2][nqp][N] {value, companion}.
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_keygen_galois(const ModTab *__restrict__ mods, const u64 *__restrict__ cdt,
-                                                                 int cdt_len, u64 seed, int L, const u64 *__restrict__ gal,
-                                                                 const shoup_t *__restrict__ sk_eval, shoup_t *gk) {
+LIMB_KERNEL(LOGN) k_keygen_galois(const ModTab *__restrict__ mods, const u64 *__restrict__ cdt, int cdt_len, u64 seed,
+                                  int L, const u64 *__restrict__ gal, const shoup_t *__restrict__ sk_eval, shoup_t *gk) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
+    LIMB_INDEX(LOGN);
     const int nqp = L + 1;
-    const int j = blockIdx.x % nqp, i = (blockIdx.x / nqp) % L, gi = blockIdx.x / (nqp * L);
+    const int j = (int)(unit % nqp), i = (int)((unit / nqp) % L), gi = (int)(unit / ((size_t)nqp * L));
     const ModTab T = mods[j];
     const u32 obj = (u32)gi * 256u + (u32)i;
     const u32 g = (u32)gal[gi];
     shoup_t *k0 = gk + ((((size_t)gi * L + i) * 2 + 0) * nqp + j) * N;
     shoup_t *k1 = gk + ((((size_t)gi * L + i) * 2 + 1) * nqp + j) * N;
     const shoup_t *s = sk_eval + (size_t)j * N;
-    ntt_forward<LOGN, NT>(
-        sm, T, 0, 0,
+    limb_forward<LOGN>(
+        sm, T, h,
         [&](int p) { u32 w[16]; chacha20_block(seed, (u32)p, kGkA, obj, (u32)j, w); return uniform_of(w, T); },
         [&](int p, u64 v) {
             k1[p] = make_shoup(v, T.q);
@@ -195,8 +191,8 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_keygen_galois(const ModTab *__
         });
     __syncthreads();
     const u64 pmod = mods[L].q % T.q;
-    ntt_forward<LOGN, NT>(
-        sm, T, 0, 0,
+    limb_forward<LOGN>(
+        sm, T, h,
         [&](int p) { u32 w[16]; chacha20_block(seed, (u32)p, kGkE, obj, 0, w); return lift_small(gauss_of(w[0], w[1], w[2], cdt, cdt_len), T.q); },
         [&](int p, u64 v) {
             u64 r = sub_mod(v, k0[p].x, T.q);
@@ -222,24 +218,23 @@ __global__ void k_enc_sample(const u64 *__restrict__ cdt, int cdt_len, u64 seed,
     dst[2 * N + k] = (int8_t)gauss_of(w[4], w[5], w[6], cdt, cdt_len);
 }
 
-// CTA (c, comp, l): comp 0 -> pk0 u + e1 + Delta m, comp 1 -> pk1 u + e2 (limb l).
+// Limb unit (c, comp, l): comp 0 -> pk0 u + e1 + Delta m, comp 1 -> pk1 u + e2 (limb l).
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_enc_main(const ModTab *__restrict__ mods, int L,
-                                                            const shoup_t *__restrict__ pk, const int8_t *__restrict__ rnd,
-                                                            const u64 *__restrict__ pt, u64 *ct) {
+LIMB_KERNEL(LOGN) k_enc_main(const ModTab *__restrict__ mods, int L, const shoup_t *__restrict__ pk,
+                             const int8_t *__restrict__ rnd, const u64 *__restrict__ pt, u64 *ct) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
-    const int l = blockIdx.x % L, comp = (blockIdx.x / L) % 2;
-    const size_t c = blockIdx.x / (2 * L);
+    LIMB_INDEX(LOGN);
+    const int l = (int)(unit % L), comp = (int)((unit / L) % 2);
+    const size_t c = unit / (2 * L);
     const ModTab T = mods[l];
     const int8_t *u = rnd + c * 3 * N, *e = rnd + c * 3 * N + (size_t)(1 + comp) * N;
     const shoup_t *key = pk + ((size_t)comp * L + l) * N;
     const u64 *m = pt + c * N;
     u64 *out = ct + ((c * 2 + comp) * L + l) * (size_t)N;
-    ntt_forward<LOGN, NT>(sm, T, 0, 0, [&](int p) { return lift_small(u[p], T.q); },
-                          [&](int p, u64 v) { sm[padi(p)] = mul_shoup(v, key[p], T.q); });
+    limb_forward<LOGN>(sm, T, h, [&](int p) { return lift_small(u[p], T.q); },
+                       [&](int p, u64 v) { sm[padi(p & (M - 1))] = mul_shoup(v, key[p], T.q); });
     __syncthreads();
-    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return sm[padi(p)]; }, [&](int p, u64 v) {
+    limb_inverse<LOGN>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) {
         u64 r = add_mod(v, lift_small(e[p], T.q), T.q);
         if (comp == 0) r = add_mod(r, mul_barrett(T.delta, m[p] % T.q, T.q, T.mu, T.bits), T.q);
         out[p] = r;
@@ -248,24 +243,23 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_enc_main(const ModTab *__restr
 
 // ------------------------------------------------------------------ decryption
 
-// CTA (c, l): x_l = [c0 + c1 s]_{q_l} -> ws [count][L][N].
+// Limb unit (c, l): x_l = [c0 + c1 s]_{q_l} -> ws [count][L][N].
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_dec_inner(const ModTab *__restrict__ mods, int L,
-                                                             const shoup_t *__restrict__ sk_eval, const u64 *__restrict__ ct,
-                                                             u64 *x) {
+LIMB_KERNEL(LOGN) k_dec_inner(const ModTab *__restrict__ mods, int L, const shoup_t *__restrict__ sk_eval,
+                              const u64 *__restrict__ ct, u64 *x) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
-    const int l = blockIdx.x % L;
-    const size_t c = blockIdx.x / L;
+    LIMB_INDEX(LOGN);
+    const int l = (int)(unit % L);
+    const size_t c = unit / L;
     const ModTab T = mods[l];
     const u64 *c0 = ct + (c * 2 * L + l) * (size_t)N, *c1 = ct + ((c * 2 + 1) * L + l) * (size_t)N;
     const shoup_t *s = sk_eval + (size_t)l * N;
-    ntt_forward<LOGN, NT>(sm, T, 0, 0, [&](int p) { return c1[p]; },
-                          [&](int p, u64 v) { sm[padi(p)] = mul_shoup(v, s[p], T.q); });
+    limb_forward<LOGN>(sm, T, h, [&](int p) { return c1[p]; },
+                       [&](int p, u64 v) { sm[padi(p & (M - 1))] = mul_shoup(v, s[p], T.q); });
     __syncthreads();
     u64 *dst = x + (c * L + l) * (size_t)N;
-    ntt_inverse<LOGN, NT>(sm, T, [&](int p) { return sm[padi(p)]; },
-                          [&](int p, u64 v) { dst[p] = add_mod(v, c0[p], T.q); });
+    limb_inverse<LOGN>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; },
+                       [&](int p, u64 v) { dst[p] = add_mod(v, c0[p], T.q); });
 }
 
 // m = floor((t x + floor(Q/2)) / Q) mod t per coefficient, x = CRT(x_0..x_{L-1}) in [0, Q):
@@ -334,19 +328,18 @@ __global__ void k_dec_round(const ModTab *__restrict__ mods, const DecConst *__r
 // ------------------------------------------------------------------ model weights
 // plaintext (j, k) mod t -> centred lift into q_l -> evaluation form; out [nY*K][L][N] {value, companion}.
 template <int LOGN>
-__global__ void __launch_bounds__(nt_for(LOGN)) k_model_weights(const ModTab *__restrict__ mods, int L, int tmod,
-                                                                 const u64 *__restrict__ pt, shoup_t *out) {
+LIMB_KERNEL(LOGN) k_model_weights(const ModTab *__restrict__ mods, int L, int tmod, const u64 *__restrict__ pt,
+                                  shoup_t *out) {
     extern __shared__ u64 sm[];
-    constexpr int N = 1 << LOGN, NT = nt_for(LOGN);
-    const int l = blockIdx.x % L;
-    const size_t jk = blockIdx.x / L;
+    LIMB_INDEX(LOGN);
+    const int l = (int)(unit % L);
+    const size_t jk = unit / L;
     const ModTab T = mods[l];
     const u64 t = mods[tmod].q, th = (t - 1) / 2;
     const u64 *src = pt + jk * N;
     shoup_t *dst = out + (jk * L + l) * (size_t)N;
-    ntt_forward<LOGN, NT>(sm, T, 0, 0,
-                          [&](int p) { const u64 v = src[p]; return v <= th ? v : T.q - (t - v); },
-                          [&](int p, u64 v) { dst[p] = make_shoup(v, T.q); });
+    limb_forward<LOGN>(sm, T, h, [&](int p) { const u64 v = src[p]; return v <= th ? v : T.q - (t - v); },
+                       [&](int p, u64 v) { dst[p] = make_shoup(v, T.q); });
 }
 
 // ------------------------------------------------------------------ dispatch helper
@@ -356,6 +349,7 @@ __global__ void __launch_bounds__(nt_for(LOGN)) k_model_weights(const ModTab *__
         case 12: FN(12); break;        \
         case 13: FN(13); break;        \
         case 14: FN(14); break;        \
+        case 15: FN(15); break;        \
         default: return BFV_ERR_BAD_PARAMS; \
     }
 
@@ -369,12 +363,7 @@ int launch_ntt_limbs(const bfv_ctx *c, const u64 *in, u64 *out, size_t nct, bool
     ProfScope prof_(c, BFV_K_NTT, st);
     const size_t nl = nct * 2 * c->L;
     if (!nl) return BFV_OK;
-#define L_(LG)                                                                                          \
-    {                                                                                                   \
-        auto k = forward ? k_ntt_limbs<LG, true> : k_ntt_limbs<LG, false>;                              \
-        set_smem(k, smem_full<LG>());                                                                   \
-        k<<<(unsigned)nl, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->L, in, out);                  \
-    }
+#define L_(LG) launch_limbs<LG>(forward ? k_ntt_limbs<LG, true> : k_ntt_limbs<LG, false>, nl, st, 0, c->dmods, c->L, in, out)
     DISPATCH_LOGN(c, L_)
 #undef L_
     count_launch(c);
@@ -383,11 +372,7 @@ int launch_ntt_limbs(const bfv_ctx *c, const u64 *in, u64 *out, size_t nct, bool
 
 int launch_encode(const bfv_ctx *c, const int64_t *slots, size_t count, u64 *pt, cudaStream_t st) {
     ProfScope prof_(c, BFV_K_ENCODE, st);
-#define L_(LG)                                                                                                  \
-    {                                                                                                           \
-        set_smem(k_encode<LG>, smem_full<LG>());                                                                \
-        k_encode<LG><<<(unsigned)count, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->nqp, c->dslot, slots, pt); \
-    }
+#define L_(LG) launch_limbs<LG>(k_encode<LG>, count, st, 0, c->dmods, c->nqp, c->dslot, slots, pt)
     DISPATCH_LOGN(c, L_)
 #undef L_
     count_launch(c);
@@ -396,11 +381,7 @@ int launch_encode(const bfv_ctx *c, const int64_t *slots, size_t count, u64 *pt,
 
 int launch_decode(const bfv_ctx *c, const u64 *pt, size_t count, int64_t *slots, cudaStream_t st) {
     ProfScope prof_(c, BFV_K_ENCODE, st);
-#define L_(LG)                                                                                                  \
-    {                                                                                                           \
-        set_smem(k_decode<LG>, smem_full<LG>());                                                                \
-        k_decode<LG><<<(unsigned)count, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->nqp, c->dslot, pt, slots); \
-    }
+#define L_(LG) launch_limbs<LG>(k_decode<LG>, count, st, 0, c->dmods, c->nqp, c->dslot, pt, slots)
     DISPATCH_LOGN(c, L_)
 #undef L_
     count_launch(c);
@@ -410,12 +391,7 @@ int launch_decode(const bfv_ctx *c, const u64 *pt, size_t count, int64_t *slots,
 int launch_encode_features(const bfv_ctx *c, const uint8_t *X, size_t nX, size_t f, u64 *pt, cudaStream_t st) {
     ProfScope prof_(c, BFV_K_ENCODE, st);
     const int K = (int)((f + c->N - 1) / c->N);
-#define L_(LG)                                                                                                 \
-    {                                                                                                          \
-        set_smem(k_encode_features<LG>, smem_full<LG>());                                                      \
-        k_encode_features<LG><<<(unsigned)(nX * K), nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->nqp, c->dslot, X, \
-                                                                                        f, K, pt);            \
-    }
+#define L_(LG) launch_limbs<LG>(k_encode_features<LG>, nX * K, st, 0, c->dmods, c->nqp, c->dslot, X, f, K, pt)
     DISPATCH_LOGN(c, L_)
 #undef L_
     count_launch(c);
@@ -424,11 +400,7 @@ int launch_encode_features(const bfv_ctx *c, const uint8_t *X, size_t nX, size_t
 
 int launch_encode_columns(const bfv_ctx *c, const uint8_t *X, size_t nX, size_t f, u64 *pt, cudaStream_t st) {
     ProfScope prof_(c, BFV_K_ENCODE, st);
-#define L_(LG)                                                                                                  \
-    {                                                                                                           \
-        set_smem(k_encode_columns<LG>, smem_full<LG>());                                                        \
-        k_encode_columns<LG><<<(unsigned)f, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->nqp, c->dslot, X, nX, f, pt); \
-    }
+#define L_(LG) launch_limbs<LG>(k_encode_columns<LG>, f, st, 0, c->dmods, c->nqp, c->dslot, X, nX, f, pt)
     DISPATCH_LOGN(c, L_)
 #undef L_
     count_launch(c);
@@ -440,22 +412,20 @@ int launch_keygen(const bfv_ctx *c, bfv_keys *k, u64 seed, cudaStream_t st) {
     if (cudaMalloc(&dgal, sizeof(u64) * c->galois.size()) != cudaSuccess) return BFV_ERR_OOM;
     cudaMemcpyAsync(dgal, c->galois.data(), sizeof(u64) * c->galois.size(), cudaMemcpyHostToDevice, st);
     k_keygen_sk<<<(c->N + 255) / 256, 256, 0, st>>>(seed, c->N, k->sk);
-#define L_(LG)                                                                                                   \
-    {                                                                                                            \
-        set_smem(k_keygen_sk_eval<LG>, smem_full<LG>());                                                         \
-        set_smem(k_keygen_pk<LG>, smem_full<LG>());                                                              \
-        set_smem(k_keygen_galois<LG>, smem_full<LG>());                                                          \
-        k_keygen_sk_eval<LG><<<c->nqp, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, k->sk, k->sk_eval);          \
-        k_keygen_pk<LG><<<c->L, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->dcdt, c->cdt_len, seed, c->L,    \
-                                                                   k->sk_eval, k->pk_eval);                      \
-        k_keygen_galois<LG><<<(unsigned)(k->ng * c->L * c->nqp), nt_for(LG), smem_full<LG>(), st>>>(             \
-            c->dmods, c->dcdt, c->cdt_len, seed, c->L, dgal, k->sk_eval, k->gk_eval);                            \
+#define L_(LG)                                                                                                  \
+    {                                                                                                           \
+        launch_limbs<LG>(k_keygen_sk_eval<LG>, c->nqp, st, 0, c->dmods, (const int8_t *)k->sk, k->sk_eval);     \
+        launch_limbs<LG>(k_keygen_pk<LG>, c->L, st, 0, c->dmods, (const u64 *)c->dcdt, c->cdt_len, seed, c->L,  \
+                         (const shoup_t *)k->sk_eval, k->pk_eval);                                              \
+        launch_limbs<LG>(k_keygen_galois<LG>, (size_t)k->ng * c->L * c->nqp, st, 0, c->dmods, (const u64 *)c->dcdt, \
+                         c->cdt_len, seed, c->L, (const u64 *)dgal, (const shoup_t *)k->sk_eval, k->gk_eval);   \
     }
     int rc = BFV_OK;
     switch (c->logN) {
         case 12: L_(12); break;
         case 13: L_(13); break;
         case 14: L_(14); break;
+        case 15: L_(15); break;
         default: rc = BFV_ERR_BAD_PARAMS;
     }
 #undef L_
@@ -468,12 +438,11 @@ int launch_keygen(const bfv_ctx *c, bfv_keys *k, u64 seed, cudaStream_t st) {
 
 int launch_keys_export(const bfv_ctx *c, const bfv_keys *k, int8_t *sk, u64 *pk, u64 *gk, cudaStream_t st) {
     if (sk && cudaMemcpyAsync(sk, k->sk, c->N, cudaMemcpyDeviceToDevice, st) != cudaSuccess) return BFV_ERR_CUDA;
-    const unsigned npk = 2 * c->L, ngk = (unsigned)(k->ng * c->L * 2 * c->nqp);
-#define L_(LG)                                                                                           \
-    {                                                                                                    \
-        set_smem(k_intt_pairs<LG>, smem_full<LG>());                                                     \
-        if (pk) { k_intt_pairs<LG><<<npk, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->L, k->pk_eval, pk); count_launch(c); } \
-        if (gk) { k_intt_pairs<LG><<<ngk, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->nqp, k->gk_eval, gk); count_launch(c); } \
+    const size_t npk = 2 * c->L, ngk = (size_t)k->ng * c->L * 2 * c->nqp;
+#define L_(LG)                                                                                                     \
+    {                                                                                                              \
+        if (pk) { launch_limbs<LG>(k_intt_pairs<LG>, npk, st, 0, c->dmods, c->L, (const shoup_t *)k->pk_eval, pk); count_launch(c); } \
+        if (gk) { launch_limbs<LG>(k_intt_pairs<LG>, ngk, st, 0, c->dmods, c->nqp, (const shoup_t *)k->gk_eval, gk); count_launch(c); } \
     }
     DISPATCH_LOGN(c, L_)
 #undef L_
@@ -485,13 +454,10 @@ int launch_encrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *pt, size_t co
     ProfScope prof_(c, BFV_K_ENCRYPT, st);
     int8_t *rnd = (int8_t *)ws;
     const size_t total = count * c->N;
+    if (!total) return BFV_OK;
     k_enc_sample<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(c->dcdt, c->cdt_len, seed, obj0, c->N, total, rnd);
-#define L_(LG)                                                                                                 \
-    {                                                                                                          \
-        set_smem(k_enc_main<LG>, smem_full<LG>());                                                             \
-        k_enc_main<LG><<<(unsigned)(count * 2 * c->L), nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->L, k->pk_eval, \
-                                                                                           rnd, pt, ct);       \
-    }
+#define L_(LG) launch_limbs<LG>(k_enc_main<LG>, count * 2 * c->L, st, 0, c->dmods, c->L, (const shoup_t *)k->pk_eval, \
+                                (const int8_t *)rnd, pt, ct)
     DISPATCH_LOGN(c, L_)
 #undef L_
     count_launch(c, 2);
@@ -501,27 +467,19 @@ int launch_encrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *pt, size_t co
 int launch_decrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *ct, size_t count, u64 *pt, void *ws, cudaStream_t st) {
     ProfScope prof_(c, BFV_K_DECRYPT, st);
     u64 *x = (u64 *)ws;
-#define L_(LG)                                                                                              \
-    {                                                                                                       \
-        set_smem(k_dec_inner<LG>, smem_full<LG>());                                                         \
-        k_dec_inner<LG><<<(unsigned)(count * c->L), nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->L, k->sk_eval, \
-                                                                                        ct, x);             \
-    }
+    const size_t total = count * c->N;
+    if (!total) return BFV_OK;
+#define L_(LG) launch_limbs<LG>(k_dec_inner<LG>, count * c->L, st, 0, c->dmods, c->L, (const shoup_t *)k->sk_eval, ct, x)
     DISPATCH_LOGN(c, L_)
 #undef L_
-    const size_t total = count * c->N;
     k_dec_round<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(c->dmods, c->ddec, x, c->N, total, pt);
     count_launch(c, 2);
     return last_err();
 }
 
 int launch_model_weights(const bfv_ctx *c, bfv_model *m, const u64 *w_pt, cudaStream_t st) {
-    const unsigned n = (unsigned)(m->nY * m->K * c->L);
-#define L_(LG)                                                                                           \
-    {                                                                                                    \
-        set_smem(k_model_weights<LG>, smem_full<LG>());                                                  \
-        k_model_weights<LG><<<n, nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->L, c->nqp, w_pt, m->w_eval); \
-    }
+    const size_t n = m->nY * m->K * c->L;
+#define L_(LG) launch_limbs<LG>(k_model_weights<LG>, n, st, 0, c->dmods, c->L, c->nqp, w_pt, m->w_eval)
     DISPATCH_LOGN(c, L_)
 #undef L_
     count_launch(c);
@@ -574,12 +532,8 @@ extern "C" int bfv_decrypt_noalloc(bfv_ctx *ctx, const bfv_keys *keys, const uin
     const bfv_ctx *c = ctx;
     cudaStream_t st = (cudaStream_t)stream;
     // every scratch word k_dec_round reads is written by k_dec_inner in the same call
-#define L_(LG)                                                                                                    \
-    {                                                                                                             \
-        set_smem(k_dec_inner<LG>, smem_full<LG>());                                                               \
-        k_dec_inner<LG><<<(unsigned)(count * c->L), nt_for(LG), smem_full<LG>(), st>>>(c->dmods, c->L, keys->sk_eval, \
-                                                                                        (const u64 *)ct, x);      \
-    }
+#define L_(LG) launch_limbs<LG>(k_dec_inner<LG>, count * c->L, st, 0, c->dmods, c->L, (const shoup_t *)keys->sk_eval, \
+                                (const u64 *)ct, x)
     DISPATCH_LOGN(c, L_)
 #undef L_
     const size_t total = count * c->N;

@@ -35,7 +35,7 @@ def test_library_exports_every_declared_function(bfv):
     assert bfv.lib().bfv_abi_version() == 1
 
 
-@pytest.mark.parametrize("shape", [synth.TINY, synth.PAPER16K])
+@pytest.mark.parametrize("shape", [synth.TINY, synth.PAPER16K, synth.WIDE32K])
 def test_host_prime_rule_matches_oracle(bfv, shape):
     assert bfv.primes(shape.N, shape.L, shape.prime_bits, shape.t) == oracle.ntt_primes(shape.prime_bits, shape.N, shape.L + 1)
 
