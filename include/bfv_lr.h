@@ -196,6 +196,22 @@ int bfv_lr_scores_packed_multi(bfv_ctx *ctx, const bfv_keys *keys, const bfv_mod
                                const uint64_t *const *X_cts, const size_t *nXs, uint64_t *const *Y_cts, void *ws,
                                size_t ws_bytes, size_t pair_chunk, uintptr_t stream);
 
+/* Requests scored by DIFFERENT models of one context in one fused product (an uneven batch:
+ * models with different feature counts f_r, classes |Y|_r and batch sizes): request r has
+ * nXs[r] individuals with inputs X_cts[r] (uint64[nXs[r]][ceil(f_r/N)][2][L][N], device),
+ * is scored by models[r] and receives Y_cts[r] (uint64[ceil(nXs[r] |Y|_r / N)][2][L][N]),
+ * laid out and bit-identical as bfv_lr_scores_packed(models[r]) would give it alone. Every
+ * pair of every request shares the kernel launches of Algorithm 1 (MAC, log2 N key
+ * switches per pair, bias + mask, compression per request). 1 <= nreq <= 64; models, X_cts,
+ * nXs and Y_cts are HOST arrays of length nreq; every model belongs to ctx. Inputs are moved
+ * to evaluation form one pair chunk at a time, so the workspace holds only the inputs of
+ * one chunk. ws: at least bfv_lr_scores_packed_models_workspace() bytes. */
+int bfv_lr_scores_packed_models_workspace(const bfv_ctx *ctx, int nreq, const bfv_model *const *models,
+                                          const size_t *nXs, size_t pair_chunk, size_t *bytes);
+int bfv_lr_scores_packed_models(bfv_ctx *ctx, const bfv_keys *keys, int nreq, const bfv_model *const *models,
+                                const uint64_t *const *X_cts, const size_t *nXs, uint64_t *const *Y_cts, void *ws,
+                                size_t ws_bytes, size_t pair_chunk, uintptr_t stream);
+
 /* The same product replayed from a CUDA graph: the first call with a given set of arguments
  * (handles, pointers, sizes, chunk, stream) captures every launch of bfv_lr_scores_packed
  * into a graph and later calls launch the instantiated graph, so the host issues one call

@@ -117,6 +117,8 @@ SIGNATURES = {
     "bfv_decrypt_noalloc_max_count": [_vp, ctypes.POINTER(_sz)],
     "bfv_lr_scores_packed_multi_workspace": [_vp, _vp, ctypes.c_int, _vp, _sz, ctypes.POINTER(_sz)],
     "bfv_lr_scores_packed_multi": [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _sz, _sz, _up],
+    "bfv_lr_scores_packed_models_workspace": [_vp, ctypes.c_int, _vp, _vp, _sz, ctypes.POINTER(_sz)],
+    "bfv_lr_scores_packed_models": [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _sz, _sz, _up],
     "bfv_lr_scores_packed_graph": [_vp, _vp, _vp, _vp, _sz, _vp, _vp, _sz, _sz, _up],
     "bfv_autotune_packed": [_vp, _vp, _vp, _vp, _sz, _vp, _vp, _sz, _up, ctypes.POINTER(_sz),
                             ctypes.POINTER(ctypes.c_double)],
@@ -372,6 +374,36 @@ class Context:
         na = (ctypes.c_size_t * len(nXs))(*nXs)
         _call("bfv_lr_scores_packed_multi", self.handle, keys.handle, model.handle, len(xs), ctypes.cast(xp, _vp),
               ctypes.cast(na, _vp), ctypes.cast(yp, _vp), _ptr(ws), ws.numel(), pair_chunk, _stream(stream))
+        return outs
+
+    def models_workspace(self, models, nXs, pair_chunk: int = 0) -> int:
+        mp = (ctypes.c_void_p * len(models))(*[m.handle for m in models])
+        na = (ctypes.c_size_t * len(nXs))(*nXs)
+        n = _sz()
+        _call("bfv_lr_scores_packed_models_workspace", self.handle, len(models), ctypes.cast(mp, _vp),
+              ctypes.cast(na, _vp), pair_chunk, ctypes.byref(n))
+        return n.value
+
+    def lr_scores_packed_models(self, keys: Keys, models, X_cts, outs=None, ws=None, pair_chunk: int = 0,
+                                stream=None):
+        """Requests of different models (request r: inputs X_cts[r], model models[r]) in one fused
+        packed product; returns one output tensor per request, each identical to its
+        single-request result."""
+        import torch
+        nXs = [x.shape[0] for x in X_cts]
+        if outs is None:
+            outs = [self._empty_u64(-(-n * m.nY // self.N), 2, self.L, self.N) for n, m in zip(nXs, models)]
+        need = self.models_workspace(models, nXs, pair_chunk)
+        if ws is None or ws.numel() < need:
+            ws = torch.empty(need, dtype=torch.uint8, device=f"cuda:{self.device}")
+        xs = [x.contiguous() for x in X_cts]
+        mp = (ctypes.c_void_p * len(models))(*[m.handle for m in models])
+        xp = (ctypes.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
+        yp = (ctypes.c_void_p * len(outs))(*[y.data_ptr() for y in outs])
+        na = (ctypes.c_size_t * len(nXs))(*nXs)
+        _call("bfv_lr_scores_packed_models", self.handle, keys.handle, len(xs), ctypes.cast(mp, _vp),
+              ctypes.cast(xp, _vp), ctypes.cast(na, _vp), ctypes.cast(yp, _vp), _ptr(ws), ws.numel(), pair_chunk,
+              _stream(stream))
         return outs
 
     def lr_scores_packed_graph(self, keys: Keys, model: Model, X_ct, out=None, ws=None, pair_chunk: int = 0,

@@ -171,28 +171,48 @@ int launch_decrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *ct, size_t co
                    cudaStream_t st);
 int launch_model_weights(const bfv_ctx *c, bfv_model *m, const u64 *w_pt, cudaStream_t st);
 
-// Requests fused into one packed product, passed to kernels by value.
+// Requests fused into one packed product, passed to kernels by value. Every request has its
+// own model (several requests may share one).
 constexpr int kMaxReq = 64;
 struct ReqTable {
     int n;
     int pad_;
     u64 pair_start[kMaxReq + 1];     // first global pair of each request; [n] = number of pairs
-    u32 xct[kMaxReq];                // first input ciphertext of each request in the fused input
+    long long xoff[kMaxReq];         // transformed input of request r, individual i, plaintext k sits at
+                                     // xoff[r] + i K[r] + k in the chunk's input buffer (set per chunk)
+    u32 K[kMaxReq];                  // plaintexts per individual, ceil(f / N), of each request's model
+    u32 nY[kMaxReq];                 // classes of each request's model
+    const shoup_t *w[kMaxReq];       // encoded weights [nY][K][L][N] of each request's model
+    const u64 *bias[kMaxReq];        // Delta [b_j]_t mod q_l, [nY][L]
 };
 
 struct PackedPlan {
-    size_t nX, nY, K, npairs, nout, chunk;
+    size_t nX, nY, K;                // single-model products: individuals, classes, plaintexts per individual
+    size_t npairs, nout, chunk;
+    size_t xcts_chunk;               // most input ciphertexts any pair chunk needs in evaluation form
     size_t off_xntt, off_yacc, off_state, off_digits, off_u, off_r, total;
     int nreq;
     ReqTable rt;
     size_t nXs[kMaxReq], ycts[kMaxReq], nouts[kMaxReq];   // per request: individuals, first output, outputs
 };
+
+// Individuals [ia, ib) of request r that have pairs in the chunk [g0, g0 + ng) (ia == ib: none).
+inline void chunk_window(const PackedPlan &p, int r, size_t g0, size_t ng, size_t &ia, size_t &ib) {
+    const size_t pa = p.rt.pair_start[r], pb = p.rt.pair_start[r + 1], nY = p.rt.nY[r];
+    const size_t a = pa > g0 ? pa : g0, b = pb < g0 + ng ? pb : g0 + ng;
+    if (a >= b) { ia = ib = 0; return; }
+    ia = (a - pa) / nY;
+    ib = (b - 1 - pa) / nY + 1;
+}
+
 PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t chunk);
 PackedPlan packed_plan_multi(const bfv_ctx *c, const bfv_model *m, int nreq, const size_t *nXs, size_t chunk);
-int launch_packed_multi(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, int nreq, const u64 *const *X_ct,
-                        u64 *const *Y_ct, void *ws, const PackedPlan &plan, cudaStream_t st);
-int launch_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const u64 *X_ct, size_t nX,
-                  u64 *Y_ct, void *ws, const PackedPlan &plan, cudaStream_t st);
+PackedPlan packed_plan_models(const bfv_ctx *c, int nreq, const bfv_model *const *models, const size_t *nXs,
+                              size_t chunk);
+int launch_packed_multi(const bfv_ctx *c, const bfv_keys *k, int nreq, const u64 *const *X_ct, u64 *const *Y_ct,
+                        void *ws, const PackedPlan &plan, cudaStream_t st);
+int launch_packed(const bfv_ctx *c, const bfv_keys *k, const u64 *X_ct, u64 *Y_ct, void *ws, const PackedPlan &plan,
+                  cudaStream_t st);
 int launch_pair_export(const bfv_ctx *c, const PackedPlan &plan, const void *ws, size_t slot_in_chunk, u64 *ct_out,
                        cudaStream_t st);
 struct StandardPlan {

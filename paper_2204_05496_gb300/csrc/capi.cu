@@ -588,7 +588,7 @@ int bfv_lr_scores_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *mo
     if (!X_ct || !Y_ct || !ws) return BFV_ERR_INVALID_ARG;
     PackedPlan plan = packed_plan(ctx, model, nX, pair_chunk);
     if (ws_bytes < plan.total) return BFV_ERR_OVER_BUDGET;
-    return launch_packed(ctx, keys, model, (const u64 *)X_ct, nX, (u64 *)Y_ct, ws, plan, S(stream));
+    return launch_packed(ctx, keys, (const u64 *)X_ct, (u64 *)Y_ct, ws, plan, S(stream));
 }
 
 int bfv_lr_scores_packed_multi_workspace(const bfv_ctx *ctx, const bfv_model *model, int nreq, const size_t *nXs,
@@ -609,8 +609,36 @@ int bfv_lr_scores_packed_multi(bfv_ctx *ctx, const bfv_keys *keys, const bfv_mod
         if (!nXs[r] || !X_cts[r] || !Y_cts[r]) return BFV_ERR_INVALID_ARG;
     PackedPlan plan = packed_plan_multi(ctx, model, nreq, nXs, pair_chunk);
     if (ws_bytes < plan.total) return BFV_ERR_OVER_BUDGET;
-    return launch_packed_multi(ctx, keys, model, nreq, (const u64 *const *)X_cts, (u64 *const *)Y_cts, ws, plan,
-                               S(stream));
+    return launch_packed_multi(ctx, keys, nreq, (const u64 *const *)X_cts, (u64 *const *)Y_cts, ws, plan, S(stream));
+}
+
+static int models_ok(const bfv_ctx *ctx, int nreq, const bfv_model *const *models, const size_t *nXs) {
+    if (!ctx || !models || !nXs || nreq < 1 || nreq > kMaxReq) return BFV_ERR_INVALID_ARG;
+    for (int r = 0; r < nreq; ++r)
+        if (!models[r] || models[r]->ctx != ctx || !nXs[r]) return BFV_ERR_INVALID_ARG;
+    return BFV_OK;
+}
+
+int bfv_lr_scores_packed_models_workspace(const bfv_ctx *ctx, int nreq, const bfv_model *const *models,
+                                          const size_t *nXs, size_t pair_chunk, size_t *bytes) {
+    if (!bytes) return BFV_ERR_INVALID_ARG;
+    int rc = models_ok(ctx, nreq, models, nXs);
+    if (rc) return rc;
+    *bytes = packed_plan_models(ctx, nreq, models, nXs, pair_chunk).total;
+    return BFV_OK;
+}
+
+int bfv_lr_scores_packed_models(bfv_ctx *ctx, const bfv_keys *keys, int nreq, const bfv_model *const *models,
+                                const uint64_t *const *X_cts, const size_t *nXs, uint64_t *const *Y_cts, void *ws,
+                                size_t ws_bytes, size_t pair_chunk, uintptr_t stream) {
+    int rc = models_ok(ctx, nreq, models, nXs);
+    if (rc) return rc;
+    if (!keys || keys->ctx != ctx || !X_cts || !Y_cts || !ws) return BFV_ERR_INVALID_ARG;
+    for (int r = 0; r < nreq; ++r)
+        if (!X_cts[r] || !Y_cts[r]) return BFV_ERR_INVALID_ARG;
+    PackedPlan plan = packed_plan_models(ctx, nreq, models, nXs, pair_chunk);
+    if (ws_bytes < plan.total) return BFV_ERR_OVER_BUDGET;
+    return launch_packed_multi(ctx, keys, nreq, (const u64 *const *)X_cts, (u64 *const *)Y_cts, ws, plan, S(stream));
 }
 
 int bfv_lr_scores_packed_graph(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint64_t *X_ct,
@@ -623,7 +651,7 @@ int bfv_lr_scores_packed_graph(bfv_ctx *ctx, const bfv_keys *keys, const bfv_mod
     if (ws_bytes < plan.total) return BFV_ERR_OVER_BUDGET;
     cudaStream_t st = S(stream);
     if (ctx->prof.on)   // per-launch event timing needs direct launches
-        return launch_packed(ctx, keys, model, (const u64 *)X_ct, nX, (u64 *)Y_ct, ws, plan, st);
+        return launch_packed(ctx, keys, (const u64 *)X_ct, (u64 *)Y_ct, ws, plan, st);
     bfv_ctx::GraphKey key(keys, model, X_ct, nX, Y_ct, ws, plan.chunk, st);
     std::lock_guard<std::mutex> g(ctx->graph_mu);
     auto it = ctx->graphs.find(key);
@@ -641,7 +669,7 @@ int bfv_lr_scores_packed_graph(bfv_ctx *ctx, const bfv_keys *keys, const bfv_mod
         cudaStream_t cs = ctx->capture_stream;
         const uint64_t before = ctx->launches.load();
         if (cudaStreamBeginCapture(cs, cudaStreamCaptureModeThreadLocal) != cudaSuccess) return BFV_ERR_CUDA;
-        int rc = launch_packed(ctx, keys, model, (const u64 *)X_ct, nX, (u64 *)Y_ct, ws, plan, cs);
+        int rc = launch_packed(ctx, keys, (const u64 *)X_ct, (u64 *)Y_ct, ws, plan, cs);
         const uint64_t held = ctx->launches.load() - before;
         ctx->launches.fetch_sub(held);     // counted when the graph runs
         cudaError_t e = cudaStreamEndCapture(cs, &graph);
@@ -675,9 +703,9 @@ int bfv_autotune_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *mod
         last = eff;
         PackedPlan plan = packed_plan(ctx, model, nX, eff);
         if (plan.total > ws_bytes) break;
-        if ((rc = launch_packed(ctx, keys, model, (const u64 *)X_ct, nX, (u64 *)Y_ct, ws, plan, st))) break;  // warm-up
+        if ((rc = launch_packed(ctx, keys, (const u64 *)X_ct, (u64 *)Y_ct, ws, plan, st))) break;  // warm-up
         cudaEventRecord(a, st);
-        if ((rc = launch_packed(ctx, keys, model, (const u64 *)X_ct, nX, (u64 *)Y_ct, ws, plan, st))) break;
+        if ((rc = launch_packed(ctx, keys, (const u64 *)X_ct, (u64 *)Y_ct, ws, plan, st))) break;
         cudaEventRecord(b, st);
         if (cudaEventSynchronize(b) != cudaSuccess) { rc = BFV_ERR_CUDA; break; }
         float t = 0;
@@ -773,7 +801,7 @@ int run_predict(bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const uint8_t
     int rc;
     if ((rc = launch_encode_features(c, X, nX, m->f, pt, st))) return rc;
     if ((rc = launch_encrypt(c, k, pt, nX * m->K, seed, 0, ct, ws + pl.off_encws, st))) return rc;
-    if ((rc = launch_packed(c, k, m, ct, nX, Y, ws + pl.off_packed, pl.packed, st))) return rc;
+    if ((rc = launch_packed(c, k, ct, Y, ws + pl.off_packed, pl.packed, st))) return rc;
     if ((rc = launch_decrypt(c, k, Y, pl.packed.nout, ptout, ws + pl.off_decws, st))) return rc;
     return launch_decode(c, ptout, pl.packed.nout, slots, st);
 }

@@ -34,16 +34,19 @@ __device__ __forceinline__ int req_of(const ReqTable &rt, size_t p) {
 }
 
 // ------------------------------------------------------------------ MAC (lines 5-13)
-// C[g][c][l][p] = sum_k Xe[i][k][c][l][p] * We[j][k][l][p]; grid.x = (g, c, l), grid.y = tile.
-__global__ void __launch_bounds__(256) k_mac(const ModTab *__restrict__ mods, int N, int L, int K, int nY, size_t g0,
-                                             const ReqTable rt, const u64 *__restrict__ Xe,
-                                             const shoup_t *__restrict__ We, u64 *C) {
+// C[g][c][l][p] = sum_k Xe[i][k][c][l][p] * We[j][k][l][p] with the model of the pair's
+// request; grid.x = (g, c, l), grid.y = tile.
+__global__ void __launch_bounds__(256) k_mac(const ModTab *__restrict__ mods, int N, int L, size_t g0,
+                                             const ReqTable rt, const u64 *__restrict__ Xe, u64 *C) {
     const size_t x = blockIdx.x;
     const int l = (int)(x % L), c = (int)((x / L) % 2);
     const size_t gl = x / (2 * L), gp = g0 + gl;
     const int r = req_of(rt, gp);
     const size_t g = gp - rt.pair_start[r];
-    const size_t i = rt.xct[r] / K + g / nY, j = g % nY;
+    const int K = (int)rt.K[r], nY = (int)rt.nY[r];
+    const long long x0 = rt.xoff[r] + (long long)(g / nY) * K;
+    const size_t j = g % nY;
+    const shoup_t *__restrict__ We = rt.w[r];
     const u64 q = mods[l].q, q2 = 2 * q;
     const size_t ctw = 2 * (size_t)L * N;
     const int p0 = blockIdx.y * 1024 + threadIdx.x;
@@ -53,7 +56,7 @@ __global__ void __launch_bounds__(256) k_mac(const ModTab *__restrict__ mods, in
         if (p >= N) break;
         u64 acc = 0;
         for (int k = 0; k < K; ++k) {
-            const u64 xv = Xe[(i * K + k) * ctw + ((size_t)c * L + l) * N + p];
+            const u64 xv = Xe[(size_t)(x0 + k) * ctw + ((size_t)c * L + l) * N + p];
             const shoup_t w = __ldg(We + ((j * K + k) * L + l) * (size_t)N + p);
             acc = red2(acc + mul_shoup(xv, w, q), q2);
         }
@@ -228,15 +231,16 @@ LIMB_KERNEL(LOGN) k_ks_moddown(const ModTab *__restrict__ mods, int L, const u64
 // Limb unit (g, l): C0 += Delta [b_j]_t; C *= NTT(centred lift of the one-hot plaintext at slot
 // (g0+g) mod N), whose coefficient k is N^-1 omega^(-e k) mod t, e the slot's exponent.
 template <int LOGN>
-LIMB_KERNEL(LOGN) k_bias_mask(const ModTab *__restrict__ mods, int L, int tmod, int nY, size_t g0, const ReqTable rt,
-                              const u32 *__restrict__ maskpow, const u64 *__restrict__ bias_delta, u64 *C) {
+LIMB_KERNEL(LOGN) k_bias_mask(const ModTab *__restrict__ mods, int L, int tmod, size_t g0, const ReqTable rt,
+                              const u32 *__restrict__ maskpow, u64 *C) {
     extern __shared__ u64 sm[];
     LIMB_INDEX(LOGN);
     constexpr int NT = Split<LOGN>::NT;
     const int l = (int)(unit % L);
     const size_t gl = unit / L, gp = g0 + gl;
-    const size_t g = gp - rt.pair_start[req_of(rt, gp)];
-    const int j = (int)(g % nY), s = (int)(g % N);
+    const int r = req_of(rt, gp);
+    const size_t g = gp - rt.pair_start[r];
+    const int j = (int)(g % rt.nY[r]), s = (int)(g % N);
     const ModTab T = mods[l];
     const u64 t = mods[tmod].q, th = (t - 1) / 2;
     const u32 twoN = 2u * N;
@@ -255,7 +259,7 @@ LIMB_KERNEL(LOGN) k_bias_mask(const ModTab *__restrict__ mods, int L, int tmod, 
         },
         [&](int p, u64 v) { sm[padi(p & (M - 1))] = v; });
     __syncthreads();
-    const u64 bd = bias_delta[(size_t)j * L + l];
+    const u64 bd = rt.bias[r][(size_t)j * L + l];
     u64 *c0 = C + ((gl * 2 + 0) * L + l) * (size_t)N + (size_t)h * M;
     u64 *c1 = C + ((gl * 2 + 1) * L + l) * (size_t)N + (size_t)h * M;
     for (int p = threadIdx.x; p < M; p += NT) {
@@ -298,8 +302,8 @@ LIMB_KERNEL(LOGN) k_intt_copy(const ModTab *__restrict__ mods, int L, const u64 
 int last_err() { return cudaGetLastError() == cudaSuccess ? BFV_OK : BFV_ERR_CUDA; }
 
 template <int LOGN>
-int run_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, int nreq, const u64 *const *X_ct,
-               u64 *const *Y_ct, char *ws, const PackedPlan &pl, cudaStream_t st) {
+int run_packed(const bfv_ctx *c, const bfv_keys *k, int nreq, const u64 *const *X_ct, u64 *const *Y_ct, char *ws,
+               const PackedPlan &pl, cudaStream_t st) {
     constexpr int N = 1 << LOGN;
     const int L = c->L, nqp = c->nqp;
     const size_t ctw = 2 * (size_t)L * N;
@@ -309,15 +313,24 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, int nreq
     set_smem(k_ks_modup<LOGN>, MS::smem);
 
     int rc;
-    for (int r = 0; r < nreq; ++r)
-        if ((rc = launch_ntt_limbs(c, X_ct[r], Xe + (size_t)pl.rt.xct[r] * ctw, pl.nXs[r] * pl.K, true, st))) return rc;
     if (cudaMemsetAsync(Yacc, 0, pl.nout * ctw * sizeof(u64), st) != cudaSuccess) return BFV_ERR_CUDA;
     const size_t keyblock = (size_t)L * 2 * nqp * N;   // one Galois element
+    ReqTable rt = pl.rt;
     for (size_t g0 = 0; g0 < pl.npairs; g0 += pl.chunk) {
         const size_t ng = std::min(pl.chunk, pl.npairs - g0);
+        // evaluation form of the inputs of the individuals this chunk's pairs use
+        size_t off = 0;
+        for (int r = 0; r < nreq; ++r) {
+            size_t ia, ib;
+            chunk_window(pl, r, g0, ng, ia, ib);
+            if (ia == ib) continue;
+            const size_t K = rt.K[r];
+            if ((rc = launch_ntt_limbs(c, X_ct[r] + ia * K * ctw, Xe + off * ctw, (ib - ia) * K, true, st))) return rc;
+            rt.xoff[r] = (long long)off - (long long)(ia * K);
+            off += (ib - ia) * K;
+        }
         { ProfScope pr(c, BFV_K_MAC, st);
-        k_mac<<<dim3((unsigned)(ng * 2 * L), (unsigned)((N + 1023) / 1024)), 256, 0, st>>>(
-            c->dmods, N, L, (int)pl.K, (int)pl.nY, g0, pl.rt, Xe, m->w_eval, C); }
+        k_mac<<<dim3((unsigned)(ng * 2 * L), (unsigned)((N + 1023) / 1024)), 256, 0, st>>>(c->dmods, N, L, g0, rt, Xe, C); }
         count_launch(c);
         for (int s = 0; s < k->ng; ++s) {
             const u32 gal = (u32)c->galois[s];
@@ -333,8 +346,7 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, int nreq
             count_launch(c, 4);
         }
         { ProfScope pr(c, BFV_K_BIAS_MASK, st);
-        launch_limbs<LOGN>(k_bias_mask<LOGN>, ng * L, st, 0, c->dmods, L, nqp, (int)pl.nY, g0, pl.rt,
-                           (const u32 *)c->dmaskpow, (const u64 *)m->bias_delta, C); }
+        launch_limbs<LOGN>(k_bias_mask<LOGN>, ng * L, st, 0, c->dmods, L, nqp, g0, rt, (const u32 *)c->dmaskpow, C); }
         count_launch(c);
         // compression: the pairs of request r that land in its output o are one contiguous range
         for (int r = 0; r < nreq; ++r) {
@@ -360,22 +372,26 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, int nreq
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
-PackedPlan packed_plan_multi(const bfv_ctx *c, const bfv_model *m, int nreq, const size_t *nXs, size_t chunk) {
+PackedPlan packed_plan_models(const bfv_ctx *c, int nreq, const bfv_model *const *models, const size_t *nXs,
+                              size_t chunk) {
     PackedPlan p{};
     const size_t N = c->N, L = c->L, nqp = c->nqp;
     p.nreq = nreq;
-    p.nY = m->nY;
-    p.K = m->K;
+    p.nY = models[0]->nY;
+    p.K = models[0]->K;
     p.rt.n = nreq;
-    size_t cts = 0, pairs = 0, outs = 0;
+    size_t pairs = 0, outs = 0;
     for (int r = 0; r < nreq; ++r) {
+        const bfv_model *m = models[r];
         p.nXs[r] = nXs[r];
         p.rt.pair_start[r] = pairs;
-        p.rt.xct[r] = (u32)cts;
+        p.rt.K[r] = (u32)m->K;
+        p.rt.nY[r] = (u32)m->nY;
+        p.rt.w[r] = m->w_eval;
+        p.rt.bias[r] = m->bias_delta;
         p.ycts[r] = outs;
         const size_t np = nXs[r] * m->nY;
         p.nouts[r] = (np + N - 1) / N;
-        cts += nXs[r] * m->K;
         pairs += np;
         outs += p.nouts[r];
     }
@@ -388,9 +404,18 @@ PackedPlan packed_plan_multi(const bfv_ctx *c, const bfv_model *m, int nreq, con
         chunk = it != c->tuned_chunk.end() ? it->second : 2048;
     }
     p.chunk = std::max<size_t>(1, std::min(chunk, p.npairs));
+    for (size_t g0 = 0; g0 < p.npairs; g0 += p.chunk) {
+        size_t cts = 0;
+        for (int r = 0; r < nreq; ++r) {
+            size_t ia, ib;
+            chunk_window(p, r, g0, std::min(p.chunk, p.npairs - g0), ia, ib);
+            cts += (ib - ia) * p.rt.K[r];
+        }
+        p.xcts_chunk = std::max(p.xcts_chunk, cts);
+    }
     const size_t ctb = 2 * L * N * sizeof(u64);
     size_t off = 0;
-    p.off_xntt = off; off += al256(cts * ctb);
+    p.off_xntt = off; off += al256(p.xcts_chunk * ctb);
     p.off_yacc = off; off += al256(p.nout * ctb);
     p.off_state = off; off += al256(p.chunk * ctb);
     p.off_digits = off; off += al256(p.chunk * L * N * sizeof(u64));
@@ -400,25 +425,30 @@ PackedPlan packed_plan_multi(const bfv_ctx *c, const bfv_model *m, int nreq, con
     return p;
 }
 
+PackedPlan packed_plan_multi(const bfv_ctx *c, const bfv_model *m, int nreq, const size_t *nXs, size_t chunk) {
+    const bfv_model *ms[kMaxReq];
+    for (int r = 0; r < nreq; ++r) ms[r] = m;
+    return packed_plan_models(c, nreq, ms, nXs, chunk);
+}
+
 PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t chunk) {
     return packed_plan_multi(c, m, 1, &nX, chunk);
 }
 
-int launch_packed_multi(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, int nreq, const u64 *const *X_ct,
-                        u64 *const *Y_ct, void *ws, const PackedPlan &plan, cudaStream_t st) {
+int launch_packed_multi(const bfv_ctx *c, const bfv_keys *k, int nreq, const u64 *const *X_ct, u64 *const *Y_ct,
+                        void *ws, const PackedPlan &plan, cudaStream_t st) {
     switch (c->logN) {
-        case 12: return run_packed<12>(c, k, m, nreq, X_ct, Y_ct, (char *)ws, plan, st);
-        case 13: return run_packed<13>(c, k, m, nreq, X_ct, Y_ct, (char *)ws, plan, st);
-        case 14: return run_packed<14>(c, k, m, nreq, X_ct, Y_ct, (char *)ws, plan, st);
-        case 15: return run_packed<15>(c, k, m, nreq, X_ct, Y_ct, (char *)ws, plan, st);
+        case 12: return run_packed<12>(c, k, nreq, X_ct, Y_ct, (char *)ws, plan, st);
+        case 13: return run_packed<13>(c, k, nreq, X_ct, Y_ct, (char *)ws, plan, st);
+        case 14: return run_packed<14>(c, k, nreq, X_ct, Y_ct, (char *)ws, plan, st);
+        case 15: return run_packed<15>(c, k, nreq, X_ct, Y_ct, (char *)ws, plan, st);
         default: return BFV_ERR_BAD_PARAMS;
     }
 }
 
-int launch_packed(const bfv_ctx *c, const bfv_keys *k, const bfv_model *m, const u64 *X_ct, size_t nX, u64 *Y_ct,
-                  void *ws, const PackedPlan &plan, cudaStream_t st) {
-    (void)nX;
-    return launch_packed_multi(c, k, m, 1, &X_ct, &Y_ct, ws, plan, st);
+int launch_packed(const bfv_ctx *c, const bfv_keys *k, const u64 *X_ct, u64 *Y_ct, void *ws, const PackedPlan &plan,
+                  cudaStream_t st) {
+    return launch_packed_multi(c, k, 1, &X_ct, &Y_ct, ws, plan, st);
 }
 
 int launch_pair_export(const bfv_ctx *c, const PackedPlan &plan, const void *ws, size_t slot, u64 *ct_out,

@@ -105,6 +105,20 @@ def uneven_models(seed: int = 401, count: int = 64):
     return out
 
 
+def uneven_batch(seed: int = 401, count: int = 64, x_divisor: int = 1):
+    """Inputs of the uneven batch: for model m of uneven_models(seed, count) a dict with the
+    parameter-set name, f, |Y|, |X| (the drawn batch size divided by x_divisor, rounded up),
+    binary features X ~ Bernoulli(0.02) and int8-range weights W and bias b, generated from
+    seed 1000 seed + m; enc_seed = 1000 seed + 500 + m seeds the model's encryptions."""
+    out = []
+    for m, (f, y, x, ps) in enumerate(uneven_models(seed, count)):
+        nX = -(-x // x_divisor)
+        sm = 1000 * seed + m
+        out.append(dict(params=ps, f=f, nY=y, nX=nX, X=features(sm, nX, f, 0.02), W=weights(sm, f, y),
+                        b=bias(sm, y), enc_seed=1000 * seed + 500 + m))
+    return out
+
+
 def poisson_arrivals(seed: int, rate_per_s: float, n_requests: int,
                      single_frac: float = 0.7, lo: int = 16, hi: int = 512):
     """Serving workload: (arrival time in s, number of individuals) per request.

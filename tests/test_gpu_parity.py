@@ -28,6 +28,15 @@ def host(t):
     return bfv.as_u64(t)
 
 
+def oracle_columns(P, okeys, X, seed, f0=0, f1=None):
+    """The oracle's own encryptions of feature columns f0..f1-1 of X (slot i = individual i),
+    ciphertext f under object f: the inputs of the standard product."""
+    f1 = X.shape[1] if f1 is None else f1
+    want = np.zeros((f1 - f0, P.N), dtype=np.int64)
+    want[:, :X.shape[0]] = X[:, f0:f1].T
+    return oracle.encrypt(P, okeys, oracle.encode(P, want), seed=seed, obj0=f0)
+
+
 # ----------------------------------------------------------------------------- tiny (N = 4096)
 
 @pytest.fixture(scope="module")
@@ -98,7 +107,7 @@ def test_decrypt_parity(tiny):
     allct = np.concatenate([ct, junk])
     pt = ctx.decrypt(keys, dev(allct))
     assert np.array_equal(host(pt), oracle.decrypt(P, okeys.sk, allct))
-    assert np.array_equal(oracle.decode(P, host(pt)[:3]), v)
+    assert np.array_equal(host(pt)[:3], oracle.encode(P, v))
 
 
 @pytest.mark.parametrize("name", ["tiny-1", "tiny-16"])
@@ -189,10 +198,11 @@ def test_packed_several_outputs_tiny(tiny):
     assert np.array_equal(bfv.unpack_packed_scores(P.N, slots, 520, 8), oracle.expected_scores(X, W, b, P.t))
     assert not slots.reshape(-1)[4160:].any()
     W_pt = oracle.encode(P, oracle.pack_weights(P, W).reshape(-1, P.N)).reshape(8, 1, P.N)
-    xct = host(X_ct)
     for g in (3000, 4100, 4159):
         i, j = divmod(g, 8)
-        c = oracle.pair_rotsum(P, okeys, xct[i], W_pt[j])
+        xo = oracle.encrypt(P, okeys, oracle.encode(P, oracle.pack_inputs(P, X[i:i + 1])[0]), seed=9, obj0=i)
+        assert np.array_equal(host(X_ct[i]), xo)
+        c = oracle.pair_rotsum(P, okeys, xo, W_pt[j])
         want = oracle.pair_bias_mask(P, c, int(b[j]), g % P.N)
         assert np.array_equal(host(ctx.packed_pair_from_workspace(model, 520, chunk, ws, g)), want)
 
@@ -205,7 +215,9 @@ def test_standard_parity_tiny(tiny):
     X_ct = ctx.encrypt(keys, cols, seed=w.seed_enc)
     model = ctx.model_prepare(W, b)
     Y = ctx.lr_scores_standard(model, X_ct, X.shape[0])
-    oY = oracle.lr_standard(P, host(X_ct), W, b)
+    oX_ct = oracle_columns(P, okeys, X, w.seed_enc)
+    assert np.array_equal(host(X_ct), oX_ct)
+    oY = oracle.lr_standard(P, oX_ct, W, b)
     assert np.array_equal(host(Y), oY)
     slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
     assert np.array_equal(slots[:, :X.shape[0]].T, oracle.expected_scores(X, W, b, P.t))
@@ -229,7 +241,9 @@ def test_standard_wide_weights_parity(tiny):
     X_ct = ctx.encrypt(keys, ctx.encode_feature_columns(dev(X).to(torch.uint8)), seed=4)
     Y = ctx.lr_scores_standard(model, X_ct, 9)
     assert ctx.check_error() == 0
-    assert np.array_equal(host(Y), oracle.lr_standard(P, host(X_ct), W, b))
+    oX_ct = oracle_columns(P, okeys, X, 4)
+    assert np.array_equal(host(X_ct), oX_ct)
+    assert np.array_equal(host(Y), oracle.lr_standard(P, oX_ct, W, b))
     slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
     assert np.array_equal(slots[:, :9].T, oracle.expected_scores(X, W, b, P.t))
 
@@ -255,7 +269,9 @@ def test_stream_stall_reports_timeout_and_context_recovers(tiny):
     assert ctx.check_error() == 0
     slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
     assert np.array_equal(slots[:, :4].T, oracle.expected_scores(X, W, b, P.t))
-    assert np.array_equal(host(Y), oracle.lr_standard(P, host(X_ct), W, b))
+    oX_ct = oracle_columns(P, okeys, X, 3)
+    assert np.array_equal(host(X_ct), oX_ct)
+    assert np.array_equal(host(Y), oracle.lr_standard(P, oX_ct, W, b))
 
 
 def test_invalid_arguments_are_rejected(tiny):
@@ -353,10 +369,11 @@ def test_single_individual_standard_full_size(paper):
         want = np.zeros((1, P.N), dtype=np.int64)
         want[0, 0] = X[0, f]
         assert np.array_equal(host(X_ct[f:f + 1]), oracle.encrypt(P, okeys, oracle.encode(P, want), seed=w.seed_enc, obj0=f))
-    Yh = host(Y)
-    for (j, c, l, k) in [(0, 0, 0, 0), (5, 1, 6, 16383), (15, 0, 3, 777)]:
-        xs = host(X_ct[:, c, l, k])
-        v = oracle.standard_coeff(W[:, j], xs, P.q[l])
-        if c == 0 and k == 0:
-            v = (v + P.delta % P.q[l] * (int(b[j]) % P.t)) % P.q[l]
-        assert int(Yh[j, c, l, k]) == v
+    # bit-exact products on a block of 64 features whose inputs the oracle encrypts itself
+    # (the same kernel and launch shape; the full-size result is pinned by the closed form)
+    f0, f1 = 23456, 23520
+    oX = oracle_columns(P, okeys, X, w.seed_enc, f0, f1)
+    assert np.array_equal(host(X_ct[f0:f1]), oX)
+    sub = ctx.model_prepare(W[f0:f1], b)
+    Ys = ctx.lr_scores_standard(sub, X_ct[f0:f1], 1)
+    assert np.array_equal(host(Ys), oracle.lr_standard(P, oX, W[f0:f1], b))

@@ -58,15 +58,16 @@ def test_wide_encode_encrypt_decrypt_match(wide):
     pt = ctx.encode(dev(v))
     assert np.array_equal(host(pt), oracle.encode(P, v))
     assert np.array_equal(ctx.decode(pt).cpu().numpy(), np.mod(v, P.t))
-    m = host(pt)
+    m = oracle.encode(P, v)
     ct = ctx.encrypt(keys, dev(m), seed=91, obj0=5)
-    assert np.array_equal(host(ct), oracle.encrypt(P, okeys, m, seed=91, obj0=5))
+    oct_ = oracle.encrypt(P, okeys, m, seed=91, obj0=5)
+    assert np.array_equal(host(ct), oct_)
     rng = np.random.default_rng(8)
     junk = np.stack([np.stack([rng.integers(0, q, P.N, dtype=np.uint64) for q in P.q]) for _ in range(2)])[None]
-    allct = np.concatenate([host(ct), junk])
+    allct = np.concatenate([oct_, junk])
     dec = ctx.decrypt(keys, dev(allct))
     assert np.array_equal(host(dec), oracle.decrypt(P, okeys.sk, allct))
-    assert np.array_equal(oracle.decode(P, host(dec)[:3]), np.mod(v, P.t))
+    assert np.array_equal(host(dec)[:3], oracle.encode(P, v))
 
 
 def test_wide_single_individual_packed_bit_exact(wide):
@@ -108,7 +109,9 @@ def test_wide_binary_model_batch(wide):
     W_pt = oracle.encode(P, oracle.pack_weights(P, W).reshape(-1, P.N)).reshape(2, 1, P.N)
     g = 599
     i, j = divmod(g, 2)
-    c = oracle.pair_rotsum(P, okeys, host(X_ct[i]), W_pt[j])
+    xo = oracle.encrypt(P, okeys, oracle.encode(P, oracle.pack_inputs(P, X[i:i + 1])[0]), seed=407, obj0=i)
+    assert np.array_equal(host(X_ct[i]), xo)
+    c = oracle.pair_rotsum(P, okeys, xo, W_pt[j])
     want = oracle.pair_bias_mask(P, c, int(b[j]), g % P.N)
     assert np.array_equal(host(ctx.packed_pair_from_workspace(model, 300, chunk, ws, g)), want)
 
@@ -122,6 +125,10 @@ def test_wide_standard_product_bit_exact(wide):
     model = ctx.model_prepare(W, b)
     X_ct = ctx.encrypt(keys, ctx.encode_feature_columns(dev(X).to(torch.uint8)), seed=409)
     Y = ctx.lr_scores_standard(model, X_ct, 40)
-    assert np.array_equal(host(Y), oracle.lr_standard(P, host(X_ct), W, b))
+    want = np.zeros((64, P.N), dtype=np.int64)
+    want[:, :40] = X.T
+    oX_ct = oracle.encrypt(P, okeys, oracle.encode(P, want), seed=409)
+    assert np.array_equal(host(X_ct), oX_ct)
+    assert np.array_equal(host(Y), oracle.lr_standard(P, oX_ct, W, b))
     slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
     assert np.array_equal(slots[:, :40].T, oracle.expected_scores(X, W, b, P.t))
