@@ -63,6 +63,7 @@ def parse_args(argv=None):
     p.add_argument("--only-packed", action="store_true",
                    help="profiling case: time only the packed product on --individuals of the batch")
     p.add_argument("--individuals", type=int, default=512)
+    p.add_argument("--ring", choices=["16k", "32k"], default="16k", help="parameter set of --only-packed")
     p.add_argument("--only-standard", action="store_true",
                    help="profiling case: time only the standard product on the first --features features")
     p.add_argument("--features", type=int, default=40000)
@@ -565,7 +566,8 @@ def standard_leg(args, ctx, keys, model, X, W, b, dev, packed_step_ms, packed_la
 
 def run_only_packed(args):
     """Small profiling case: the packed product alone on the first --individuals of the batch
-    (same parameters, same kernels, fewer pairs), --warmup untimed then --steps timed calls."""
+    (same kernels, fewer pairs; --ring 32k runs it on the N = 32768 parameter set),
+    --warmup untimed then --steps timed calls, then one call with per-kernel timing."""
     import torch
     import paper_2204_05496_gb300 as bfv
     bfv.build()
@@ -573,8 +575,9 @@ def run_only_packed(args):
     w = synth.WORKLOADS[WORKLOAD]
     X, W, b = synth.workload_inputs(w)
     X = X[:args.individuals]
-    N, L = w.params.N, w.params.L
-    ctx = bfv.Context.from_shape(w.params)
+    shape = synth.WIDE32K if args.ring == "32k" else w.params
+    N, L = shape.N, shape.L
+    ctx = bfv.Context.from_shape(shape)
     keys = ctx.keygen(w.seed_keys)
     model = ctx.model_prepare(W, b)
     pt = ctx.encode_features(torch.from_numpy(X).cuda())
@@ -590,11 +593,20 @@ def run_only_packed(args):
         ctx.lr_scores_packed(keys, model, X_ct, out=Y, ws=ws, pair_chunk=args.pair_chunk)
     z.record()
     torch.cuda.synchronize()
+    ms = a.elapsed_time(z) / args.steps
+    ctx.profile(True)
+    ctx.profile_read()
+    ctx.lr_scores_packed(keys, model, X_ct, out=Y, ws=ws, pair_chunk=args.pair_chunk)
+    torch.cuda.synchronize()
+    ctx.profile(False)
+    kern = {k: round(v[1], 3) for k, v in ctx.profile_read().items() if v[0]}
     slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
     got = bfv.unpack_packed_scores(N, slots, len(X), W.shape[1])
-    ok = bool(np.array_equal(got, (X.astype(np.int64) @ W + b[None, :]) % w.params.t))
-    print(json.dumps({"case": "only-packed", "individuals": len(X), "pair_chunk": args.pair_chunk,
-                      "ms_per_call": a.elapsed_time(z) / args.steps, "correct": ok}), flush=True)
+    ok = bool(np.array_equal(got, (X.astype(np.int64) @ W + b[None, :]) % shape.t))
+    pairs = len(X) * W.shape[1]
+    print(json.dumps({"case": "only-packed", "ring": N, "individuals": len(X), "pairs": pairs,
+                      "pair_chunk": args.pair_chunk, "ms_per_call": round(ms, 3),
+                      "us_per_pair": round(ms * 1e3 / pairs, 2), "kernel_ms": kern, "correct": ok}), flush=True)
     return 0 if ok else 1
 
 
