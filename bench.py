@@ -64,6 +64,9 @@ def parse_args(argv=None):
                    help="profiling case: time only the packed product on --individuals of the batch")
     p.add_argument("--individuals", type=int, default=512)
     p.add_argument("--ring", choices=["16k", "32k"], default="16k", help="parameter set of --only-packed")
+    p.add_argument("--uneven", action="store_true",
+                   help="the uneven batch: 64 models on the N = 16384 and N = 32768 sets in one CUDA graph")
+    p.add_argument("--uneven-divisor", type=int, default=1, help="divide the drawn batch sizes by this")
     p.add_argument("--only-standard", action="store_true",
                    help="profiling case: time only the standard product on the first --features features")
     p.add_argument("--features", type=int, default=40000)
@@ -610,6 +613,87 @@ def run_only_packed(args):
     return 0 if ok else 1
 
 
+def run_uneven(args):
+    """The uneven batch: 64 models (f in {1k, 5k, 20k, 40k}, |Y| in {2, 8, 16}, |X| in 1..512 divided
+    by --uneven-divisor) on the N = 16384 and N = 32768 parameter sets. The models of each ring
+    form one fused packed product; both products are captured into one CUDA graph. A sub-sampled
+    pass (batch sizes / 64) through the same path loads every kernel first; then the graph of the
+    requested batch is replayed once, timed with CUDA events, and every score is checked."""
+    import torch
+    import paper_2204_05496_gb300 as bfv
+    bfv.build()
+    torch.cuda.set_device(0)
+    rings = ("PAPER16K", "WIDE32K")
+    ctxs = {r: bfv.Context.from_shape(getattr(synth, r)) for r in rings}
+    keys = {r: ctxs[r].keygen(402) for r in rings}
+
+    def prepare(div):
+        items = synth.uneven_batch(x_divisor=div)
+        for it in items:
+            ctx = ctxs[it["params"]]
+            it["model"] = ctx.model_prepare(it["W"], it["b"])
+            pt = ctx.encode_features(torch.from_numpy(it["X"]).cuda())
+            it["X_ct"] = ctx.encrypt(keys[it["params"]], pt.reshape(-1, ctx.N), seed=it["enc_seed"]).reshape(
+                it["nX"], -1, 2, ctx.L, ctx.N)
+            del pt
+        plan = {}
+        for r in rings:
+            grp = [it for it in items if it["params"] == r]
+            ctx = ctxs[r]
+            models = [it["model"] for it in grp]
+            ws = torch.empty(ctx.models_workspace(models, [it["nX"] for it in grp]), dtype=torch.uint8, device="cuda")
+            outs = [ctx._empty_u64(-(-it["nX"] * it["nY"] // ctx.N), 2, ctx.L, ctx.N) for it in grp]
+            plan[r] = (grp, models, [it["X_ct"] for it in grp], outs, ws)
+        torch.cuda.synchronize()
+        g = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(g, capture_error_mode="thread_local"):
+            st = torch.cuda.current_stream()
+            for r in rings:
+                grp, models, xs, outs, ws = plan[r]
+                ctxs[r].lr_scores_packed_models(keys[r], models, xs, outs=outs, ws=ws, stream=st)
+        return items, plan, g
+
+    def check(plan):
+        for r in rings:
+            grp, models, xs, outs, ws = plan[r]
+            ctx = ctxs[r]
+            for it, o in zip(grp, outs):
+                slots = ctx.decode(ctx.decrypt(keys[r], o)).cpu().numpy()
+                got = bfv.unpack_packed_scores(ctx.N, slots, it["nX"], it["nY"])
+                want = (it["X"].astype(np.int64) @ it["W"] + it["b"][None, :]) % ctx.t
+                if not np.array_equal(got, want):
+                    return False
+        return True
+
+    items, plan, g = prepare(64)
+    g.replay()
+    torch.cuda.synchronize()
+    ok_small = check(plan)
+    del items, plan, g
+    torch.cuda.empty_cache()
+    items, plan, g = prepare(args.uneven_divisor)
+    a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record()
+    g.replay()
+    z.record()
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(z)
+    ok = ok_small and check(plan)
+    per = {}
+    for r in rings:
+        grp = plan[r][0]
+        per[r] = {"models": len(grp), "individuals": sum(it["nX"] for it in grp),
+                  "pairs": sum(it["nX"] * it["nY"] for it in grp),
+                  "input_ciphertexts": sum(it["X_ct"].shape[0] * it["X_ct"].shape[1] for it in grp)}
+    preds = sum(it["nX"] for it in items)
+    pairs = sum(v["pairs"] for v in per.values())
+    print(json.dumps({"case": "uneven", "batch_divisor": args.uneven_divisor, "graph_launches": 1,
+                      "ms": round(ms, 1), "predictions": preds, "pairs": pairs,
+                      "predictions_per_s": round(preds / (ms / 1e3), 2), "pairs_per_s": round(pairs / (ms / 1e3), 1),
+                      "rings": per, "correct": ok}), flush=True)
+    return 0 if ok else 1
+
+
 def run_only_standard(args):
     """Small profiling case: the standard product alone on the first --features features of the
     batch (same parameters and kernels), --warmup untimed then --steps timed calls."""
@@ -708,6 +792,8 @@ def main(argv=None):
         return run_reference(args)
     if args.only_packed:
         return run_only_packed(args)
+    if args.uneven:
+        return run_uneven(args)
     if args.only_standard:
         return run_only_standard(args)
     return run_gpu(args)
