@@ -86,6 +86,16 @@ __device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u6
     X = x + t;
     Y = x - t + q2;
 }
+// Without the reduction of X: both outputs exceed the inputs' bound by less than 2q (t < 2q),
+// so a transform entered below 4q leaves below (4 + 2 stages) q -- below 32q < 2^60 for the
+// 15 stages of N = 32768 and primes below 2^55. Only for outputs consumed by Shoup products
+// (which take any 64-bit input).
+__device__ __forceinline__ void ct_bfly_lazy(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 q2) {
+    const u64 t = mul_shoup(Y, w, wp, q);
+    const u64 x = X;
+    X = x + t;
+    Y = x - t + q2;
+}
 __device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 q2) {
     const u64 s = X + Y, d = X - Y + q2;
     X = red2(s, q2);
@@ -105,7 +115,7 @@ template <int M> struct PadSize { static constexpr int value = M + (M >> 4); };
 
 // Forward Cooley-Tukey stages s .. s+R-1 (global stage numbers) on a group of 2^R values
 // x[r] = a[base + r * t_last]; gblock is the global block index at stage s.
-template <int R>
+template <int R, bool LAZY = false>
 __device__ __forceinline__ void fwd_radix(u64 (&x)[1 << R], int s, int gblock, const ulonglong2 *__restrict__ fw,
                                           u64 q, u64 q2) {
 #pragma unroll
@@ -116,7 +126,10 @@ __device__ __forceinline__ void fwd_radix(u64 (&x)[1 << R], int s, int gblock, c
             const int ti = (1 << (s + u)) + (gblock << u) + k;
             const ulonglong2 w = __ldg(fw + ti);
 #pragma unroll
-            for (int j = 0; j < half; ++j) ct_bfly(x[k * 2 * half + j], x[k * 2 * half + j + half], w.x, w.y, q, q2);
+            for (int j = 0; j < half; ++j) {
+                if constexpr (LAZY) ct_bfly_lazy(x[k * 2 * half + j], x[k * 2 * half + j + half], w.x, w.y, q, q2);
+                else ct_bfly(x[k * 2 * half + j], x[k * 2 * half + j + half], w.x, w.y, q, q2);
+            }
         }
     }
 }
@@ -158,8 +171,10 @@ template <int LOGM> struct Sched {
 // position p (for C > 0: the value after stage C-1, produced by the caller); store(p, v)
 // receives the final value in [0, q). sm: shared buffer of PadSize<M> words. Values given by
 // load must be < 4q. The driver ends without a barrier after the last store.
+// LAZY: no reductions at all (ct_bfly_lazy); store receives values below (4 + 2 log2 N) q, for
+// consumers that only multiply them by Shoup constants.
 
-template <int LOGM, int NT, int P, int S, class Load, class Store>
+template <int LOGM, int NT, int P, int S, bool LAZY, class Load, class Store>
 __device__ __forceinline__ void fwd_passes(u64 *sm, const ModTab &T, int C, int hidx, Load &load, Store &store) {
     constexpr int NP = Sched<LOGM>::NP;
     constexpr int R = Sched<LOGM>::template R<P>::value;
@@ -177,22 +192,26 @@ __device__ __forceinline__ void fwd_passes(u64 *sm, const ModTab &T, int C, int 
             if constexpr (P == 0) x[r] = load(base + r * TL);
             else x[r] = sm[padi(base + r * TL)];
         }
-        fwd_radix<R>(x, S + C, (hidx << S) + block, T.fw, q, q2);
+        fwd_radix<R, LAZY>(x, S + C, (hidx << S) + block, T.fw, q, q2);
 #pragma unroll
         for (int r = 0; r < (1 << R); ++r) {
-            if constexpr (P == NP - 1) store(base + r * TL, red1(red2(x[r], q2), q));
+            if constexpr (P == NP - 1) store(base + r * TL, LAZY ? x[r] : red1(red2(x[r], q2), q));
             else sm[padi(base + r * TL)] = x[r];
         }
     }
     if constexpr (P < NP - 1) {
         __syncthreads();
-        fwd_passes<LOGM, NT, P + 1, S + R>(sm, T, C, hidx, load, store);
+        fwd_passes<LOGM, NT, P + 1, S + R, LAZY>(sm, T, C, hidx, load, store);
     }
 }
 
 template <int LOGM, int NT, class Load, class Store>
 __device__ __forceinline__ void ntt_forward(u64 *sm, const ModTab &T, int C, int hidx, Load load, Store store) {
-    fwd_passes<LOGM, NT, 0, 0>(sm, T, C, hidx, load, store);
+    fwd_passes<LOGM, NT, 0, 0, false>(sm, T, C, hidx, load, store);
+}
+template <int LOGM, int NT, class Load, class Store>
+__device__ __forceinline__ void ntt_forward_lazy(u64 *sm, const ModTab &T, int C, int hidx, Load load, Store store) {
+    fwd_passes<LOGM, NT, 0, 0, true>(sm, T, C, hidx, load, store);
 }
 
 // ------------------------------------------------------------------ inverse NTT driver
@@ -359,20 +378,20 @@ __device__ __forceinline__ u64 fold_stages(const ModTab &T, int hidx, u64 (&v)[1
 }
 
 // Forward transform of one limb by CTA h of its group: load(k) returns coefficient k (< 4q,
-// any k < N); store(p, v) receives the evaluation positions p this CTA owns, in [0, q).
-template <int LOGN, class Load, class Store>
+// any k < N); store(p, v) receives the evaluation positions p this CTA owns, in [0, q)
+// (LAZY: below 32q, for Shoup-product consumers only).
+template <int LOGN, bool LAZY = false, class Load, class Store>
 __device__ __forceinline__ void limb_forward(u64 *sm, const ModTab &T, int h, Load load, Store store) {
     using SP = Split<LOGN>;
     if constexpr (SP::S == 1) {
-        ntt_forward<LOGN, SP::NT>(sm, T, 0, 0, load, store);
+        fwd_passes<LOGN, SP::NT, 0, 0, LAZY>(sm, T, 0, 0, load, store);
     } else {
-        ntt_forward<SP::LOGM, SP::NT>(
-            sm, T, 1, h,
-            [&](int p) {
-                u64 v[2] = {load(p), load(p + SP::M)};
-                return fold_stages<1>(T, h, v);
-            },
-            [&](int p, u64 v) { store(h * SP::M + p, v); });
+        auto ld = [&](int p) {
+            u64 v[2] = {load(p), load(p + SP::M)};
+            return fold_stages<1>(T, h, v);
+        };
+        auto st = [&](int p, u64 v) { store(h * SP::M + p, v); };
+        fwd_passes<SP::LOGM, SP::NT, 0, 0, LAZY>(sm, T, 1, h, ld, st);
     }
 }
 

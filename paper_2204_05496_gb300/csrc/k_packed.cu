@@ -162,7 +162,7 @@ __global__ void __launch_bounds__(ModUpShape<LOGN>::NT) k_ks_modup(const ModTab 
             key_mac<H, NT>(acc0, acc1, k0, k1, q, q2, [&](int p) { return c1[auto_src(h * H + p, gal, LOGN)]; });
         } else {
             const u64 *d = D + (g * L + i) * (size_t)N;   // digit i < q_i < 2 q_j
-            ntt_forward<MS::LOGH, NT>(
+            ntt_forward_lazy<MS::LOGH, NT>(       // outputs feed Shoup products only
                 sm, T, MS::C, h,
                 [&](int p) {
                     u64 v[QS];
@@ -207,7 +207,7 @@ LIMB_KERNEL(LOGN) k_ks_moddown(const ModTab *__restrict__ mods, int L, const u64
     const size_t g = unit / (2 * L);
     const ModTab T = mods[l];
     const u64 *r = R + (g * 2 + c) * (size_t)N;
-    limb_forward<LOGN>(sm, T, h, [&](int p) { return T.phalf + (T.q - red1(r[p], T.q)); },
+    limb_forward<LOGN, true>(sm, T, h, [&](int p) { return T.phalf + (T.q - red1(r[p], T.q)); },
                        [&](int p, u64 v) { sm[padi(p & (M - 1))] = v; });
     __syncthreads();
     const u64 *u = U + ((g * 2 + c) * nqp + l) * (size_t)N + (size_t)h * M;

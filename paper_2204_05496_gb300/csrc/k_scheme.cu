@@ -17,7 +17,8 @@ __device__ __forceinline__ u64 uniform_of(const u32 *w, const ModTab &T) {
 }
 
 // ------------------------------------------------------------------ limb transforms
-// in/out: [nlimbs][N]; limb x uses modulus x % L. The forward transform needs in != out.
+// in/out: [nlimbs][N]; limb x uses modulus x % L. The forward transform needs in != out and
+// leaves its values unreduced (below 32q): its outputs only enter Shoup products (k_mac).
 template <int LOGN, bool FWD>
 LIMB_KERNEL(LOGN) k_ntt_limbs(const ModTab *__restrict__ mods, int L, const u64 *in, u64 *out) {
     extern __shared__ u64 sm[];
@@ -26,7 +27,7 @@ LIMB_KERNEL(LOGN) k_ntt_limbs(const ModTab *__restrict__ mods, int L, const u64 
     const u64 *src = in + unit * N;
     u64 *dst = out + unit * N;
     if constexpr (FWD)
-        limb_forward<LOGN>(sm, T, h, [&](int p) { return src[p]; }, [&](int p, u64 v) { dst[p] = v; });
+        limb_forward<LOGN, true>(sm, T, h, [&](int p) { return src[p]; }, [&](int p, u64 v) { dst[p] = v; });
     else
         limb_inverse<LOGN>(sm, T, h, [&](int p) { return src[p]; }, [&](int p, u64 v) { dst[p] = v; });
 }
@@ -231,7 +232,7 @@ LIMB_KERNEL(LOGN) k_enc_main(const ModTab *__restrict__ mods, int L, const shoup
     const shoup_t *key = pk + ((size_t)comp * L + l) * N;
     const u64 *m = pt + c * N;
     u64 *out = ct + ((c * 2 + comp) * L + l) * (size_t)N;
-    limb_forward<LOGN>(sm, T, h, [&](int p) { return lift_small(u[p], T.q); },
+    limb_forward<LOGN, true>(sm, T, h, [&](int p) { return lift_small(u[p], T.q); },
                        [&](int p, u64 v) { sm[padi(p & (M - 1))] = mul_shoup(v, key[p], T.q); });
     __syncthreads();
     limb_inverse<LOGN>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) {
@@ -254,7 +255,7 @@ LIMB_KERNEL(LOGN) k_dec_inner(const ModTab *__restrict__ mods, int L, const shou
     const ModTab T = mods[l];
     const u64 *c0 = ct + (c * 2 * L + l) * (size_t)N, *c1 = ct + ((c * 2 + 1) * L + l) * (size_t)N;
     const shoup_t *s = sk_eval + (size_t)l * N;
-    limb_forward<LOGN>(sm, T, h, [&](int p) { return c1[p]; },
+    limb_forward<LOGN, true>(sm, T, h, [&](int p) { return c1[p]; },
                        [&](int p, u64 v) { sm[padi(p & (M - 1))] = mul_shoup(v, s[p], T.q); });
     __syncthreads();
     u64 *dst = x + (c * L + l) * (size_t)N;
