@@ -44,7 +44,7 @@ extern "C" {
 /* BFV parameter shape. Primes: the L+1 largest primes below 2^prime_bits that are 1 mod 2N,
  * in descending order; the first L form the ciphertext modulus Q, the last is the
  * key-switching prime P. Supported: N in {4096, 8192, 16384, 32768}, 1 <= L <= 15,
- * 30 <= prime_bits <= 60, t prime with t = 1 mod 2N and t < 2^31. The Gaussian error has
+ * 30 <= prime_bits <= 59, t prime with t = 1 mod 2N and t < 2^31. The Gaussian error has
  * width sigma = sigma_num / sigma_den and is truncated at floor(6 sigma). At N = 32768 each
  * limb transform runs on a cluster of two CTAs (a limb is larger than one CTA's shared
  * memory). */

@@ -1,6 +1,6 @@
 // bfv_device.cuh -- device-side modular arithmetic and the shared-memory negacyclic NTT.
 //
-// Residues are 64-bit words modulo primes below 2^61. Constant operands (twiddles, keys,
+// Residues are 64-bit words modulo primes below 2^59. Constant operands (twiddles, keys,
 // encoded weights, P^-1) are multiplied with Shoup's method (a precomputed companion
 // w' = floor(w 2^64 / q) turns the reduction into one high and two low 64-bit products);
 // variable x variable products use Barrett reduction with mu = floor(2^(2b) / q).
@@ -34,6 +34,7 @@ struct ModTab {
     u64 phalf;              // floor(P/2) mod q
     u64 delta;              // floor(Q/t) mod q
     u64 r64, r64p;          // 2^64 mod q and companion
+    u64 onep;               // floor(2^64 / q): Shoup companion of 1 (reduces any 64-bit word to [0, 2q))
     const ulonglong2 *fw;   // forward twiddles {psi^brev(k), Shoup companion}, k < N
     const ulonglong2 *iw;   // inverse twiddles {psi^-brev(k), Shoup companion}
 };

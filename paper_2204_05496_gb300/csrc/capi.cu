@@ -182,7 +182,7 @@ bool params_ok(const bfv_params *p) {
     if (!p) return false;
     if (p->N != 4096 && p->N != 8192 && p->N != 16384 && p->N != 32768) return false;
     if (p->L < 1 || p->L > BFV_MAXP - 1) return false;
-    if (p->prime_bits < 30 || p->prime_bits > 60) return false;
+    if (p->prime_bits < 30 || p->prime_bits > 59) return false;   // lazy transforms stay below 32q < 2^64
     if (p->t < 3 || p->t >= (1ull << 31) || (p->t - 1) % (2ull * p->N) != 0 || !is_prime_h(p->t)) return false;
     if (p->sigma_num == 0 || p->sigma_den == 0) return false;
     return true;
@@ -309,6 +309,7 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
         }
         T.r64 = (u64)(((u128)1 << 64) % q);
         T.r64p = shoup_h(T.r64, q);
+        T.onep = shoup_h(1, q);
         const u64 *base = c->dtw + (size_t)j * 4 * N;
         T.fw = (const ulonglong2 *)base;
         T.iw = (const ulonglong2 *)(base + 2 * N);

@@ -99,10 +99,11 @@ LIMB_KERNEL(LOGN) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 gal, u64
 }
 
 // acc_c[p] += v(p) * key_c[p] for this thread's points p = tid + e NT, four at a time with
-// all loads issued first.
+// all loads issued first. The sums are not reduced: L products below 2q each stay below
+// 2 L q <= 30q < 2^64 and are reduced once at the end.
 template <int H, int NT, class Val>
 __device__ __forceinline__ void key_mac(u64 *acc0, u64 *acc1, const shoup_t *__restrict__ k0,
-                                        const shoup_t *__restrict__ k1, u64 q, u64 q2, Val val) {
+                                        const shoup_t *__restrict__ k1, u64 q, Val val) {
     static_assert(H % (4 * NT) == 0, "points per thread must be a multiple of 4");
 #pragma unroll 1
     for (int p0 = threadIdx.x; p0 < H; p0 += 4 * NT) {
@@ -118,8 +119,8 @@ __device__ __forceinline__ void key_mac(u64 *acc0, u64 *acc1, const shoup_t *__r
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int p = p0 + e * NT;
-            acc0[p] = red2(acc0[p] + mul_shoup(v[e], a[e], q), q2);
-            acc1[p] = red2(acc1[p] + mul_shoup(v[e], b[e], q), q2);
+            acc0[p] += mul_shoup(v[e], a[e], q);
+            acc1[p] += mul_shoup(v[e], b[e], q);
         }
     }
 }
@@ -150,7 +151,7 @@ __global__ void __launch_bounds__(ModUpShape<LOGN>::NT) k_ks_modup(const ModTab 
     const int h = blockIdx.x % QS, j = (blockIdx.x / QS) % nqp;
     const size_t g = blockIdx.x / (QS * nqp);
     const ModTab T = mods[j];
-    const u64 q = T.q, q2 = T.q2;
+    const u64 q = T.q;
     for (int p = threadIdx.x; p < H; p += NT) { acc0[p] = 0; acc1[p] = 0; }
     const size_t keystride = (size_t)nqp * N;     // one (digit, component) block
 #pragma unroll 1
@@ -159,7 +160,7 @@ __global__ void __launch_bounds__(ModUpShape<LOGN>::NT) k_ks_modup(const ModTab 
         const shoup_t *k1 = key + ((size_t)i * 2 + 1) * keystride + (size_t)j * N + (size_t)h * H;
         if (i == j) {
             const u64 *c1 = C + ((g * 2 + 1) * L + j) * (size_t)N;
-            key_mac<H, NT>(acc0, acc1, k0, k1, q, q2, [&](int p) { return c1[auto_src(h * H + p, gal, LOGN)]; });
+            key_mac<H, NT>(acc0, acc1, k0, k1, q, [&](int p) { return c1[auto_src(h * H + p, gal, LOGN)]; });
         } else {
             const u64 *d = D + (g * L + i) * (size_t)N;   // digit i < q_i < 2 q_j
             ntt_forward_lazy<MS::LOGH, NT>(       // outputs feed Shoup products only
@@ -172,13 +173,16 @@ __global__ void __launch_bounds__(ModUpShape<LOGN>::NT) k_ks_modup(const ModTab 
                 },
                 [&](int p, u64 v) { sm[padi(p)] = v; });
             __syncthreads();
-            key_mac<H, NT>(acc0, acc1, k0, k1, q, q2, [&](int p) { return sm[padi(p)]; });
+            key_mac<H, NT>(acc0, acc1, k0, k1, q, [&](int p) { return sm[padi(p)]; });
             __syncthreads();
         }
     }
     u64 *u0 = U + ((g * 2 + 0) * nqp + j) * (size_t)N + (size_t)h * H;
     u64 *u1 = U + ((g * 2 + 1) * nqp + j) * (size_t)N + (size_t)h * H;
-    for (int p = threadIdx.x; p < H; p += NT) { u0[p] = red1(acc0[p], q); u1[p] = red1(acc1[p], q); }
+    for (int p = threadIdx.x; p < H; p += NT) {
+        u0[p] = red1(mul_shoup(acc0[p], 1, T.onep, q), q);
+        u1[p] = red1(mul_shoup(acc1[p], 1, T.onep, q), q);
+    }
 }
 
 // Limb unit (g, c): R[g][c] = [INTT_P(U[g][c][P]) + floor(P/2)]_P.

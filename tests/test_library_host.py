@@ -52,6 +52,12 @@ def test_bad_parameters_rejected_on_host(bfv):
     assert bfv.lib().bfv_params_primes(ctypes.byref(p), ctypes.cast(out, ctypes.c_void_p)) == bfv.BFV_ERR_INVALID_ARG
     p = bfv.Params(3000, 3, 36, 0, 65537, 16, 5)
     assert bfv.lib().bfv_params_primes(ctypes.byref(p), ctypes.cast(out, ctypes.c_void_p)) == bfv.BFV_ERR_INVALID_ARG
+    # primes must stay below 2^59: unreduced forward transforms and key sums reach 32q
+    p = bfv.Params(4096, 3, 60, 0, 65537, 16, 5)
+    assert bfv.lib().bfv_params_primes(ctypes.byref(p), ctypes.cast(out, ctypes.c_void_p)) == bfv.BFV_ERR_INVALID_ARG
+    p = bfv.Params(4096, 3, 59, 0, 65537, 16, 5)
+    assert bfv.lib().bfv_params_primes(ctypes.byref(p), ctypes.cast(out, ctypes.c_void_p)) == bfv.BFV_OK
+    assert list(out)[:4] == oracle.ntt_primes(59, 4096, 4)
 
 
 def test_setup_without_gpu_fails_loudly(bfv):
