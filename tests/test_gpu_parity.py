@@ -377,3 +377,69 @@ def test_single_individual_standard_full_size(paper):
     sub = ctx.model_prepare(W[f0:f1], b)
     Ys = ctx.lr_scores_standard(sub, X_ct[f0:f1], 1)
     assert np.array_equal(host(Ys), oracle.lr_standard(P, oX, W[f0:f1], b))
+
+
+# ----------------------------------------------------------------------------- edge cases
+
+def test_max_prime_bits_packed_parity():
+    """59-bit primes, the largest allowed: the unreduced forward transforms reach 32q < 2^64 and
+    the unreduced key sums 2Lq; ciphertexts must still match the oracle bit for bit."""
+    shape = synth.BfvShape(N=4096, L=3, prime_bits=59, t=65537)
+    ctx = bfv.Context.from_shape(shape)
+    keys = ctx.keygen(91)
+    P = oracle.Params.from_shape(shape)
+    okeys = oracle.keygen(P, 91)
+    assert ctx.primes == P.qs and all(q.bit_length() == 59 for q in P.qs)
+    rng = np.random.default_rng(92)
+    X = (rng.random((3, 5000)) < 0.3).astype(np.uint8)      # K = 2
+    W = rng.integers(-127, 128, (5000, 5))
+    b = rng.integers(-127, 128, 5)
+    oX_ct, _, oY = oracle.packed_pipeline(P, okeys, X, W, b, 93)
+    pt = ctx.encode_features(dev(X).to(torch.uint8))
+    X_ct = ctx.encrypt(keys, pt.reshape(-1, P.N), seed=93).reshape(3, 2, 2, P.L, P.N)
+    assert np.array_equal(host(X_ct), oX_ct)
+    Y = ctx.lr_scores_packed(keys, ctx.model_prepare(W, b), X_ct)
+    assert np.array_equal(host(Y), oY)
+    slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
+    assert np.array_equal(bfv.unpack_packed_scores(P.N, slots, 3, 5), oracle.expected_scores(X, W, b, P.t))
+
+
+def test_degenerate_shapes_packed_tiny(tiny):
+    """One feature and one class (f = 1, |Y| = 1), and pair counts exactly filling the N slots of
+    one output (nX |Y| = N) and one past it (a second output holding a single pair)."""
+    ctx, keys, P, okeys = tiny
+    rng = np.random.default_rng(94)
+    X = np.ones((2, 1), dtype=np.uint8)
+    W = np.array([[-127]])
+    b = np.array([127])
+    oX_ct, _, oY = oracle.packed_pipeline(P, okeys, X, W, b, 95)
+    Y = ctx.lr_scores_packed(keys, ctx.model_prepare(W, b), dev(oX_ct))
+    assert Y.shape[0] == 1 and np.array_equal(host(Y), oY)
+    for nX in (P.N // 4, P.N // 4 + 1):                          # |Y| = 4: 4096 and 4100 pairs
+        X = (rng.random((nX, 30)) < 0.5).astype(np.uint8)
+        W = rng.integers(-127, 128, (30, 4))
+        b = rng.integers(-127, 128, 4)
+        X_ct = ctx.encrypt(keys, ctx.encode_features(dev(X).to(torch.uint8)).reshape(-1, P.N),
+                           seed=96).reshape(nX, 1, 2, P.L, P.N)
+        Y = ctx.lr_scores_packed(keys, ctx.model_prepare(W, b), X_ct, pair_chunk=1024)
+        assert Y.shape[0] == -(-nX * 4 // P.N)
+        slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
+        assert np.array_equal(bfv.unpack_packed_scores(P.N, slots, nX, 4), oracle.expected_scores(X, W, b, P.t))
+
+
+def test_standard_all_slots_tiny(tiny):
+    """The standard product with every slot used (nX = N individuals) and a single feature."""
+    ctx, keys, P, okeys = tiny
+    rng = np.random.default_rng(97)
+    X = (rng.random((P.N, 3)) < 0.5).astype(np.uint8)
+    W = rng.integers(-127, 128, (3, 2))
+    b = rng.integers(-127, 128, 2)
+    X_ct = ctx.encrypt(keys, ctx.encode_feature_columns(dev(X).to(torch.uint8)), seed=98)
+    oX_ct = oracle_columns(P, okeys, X, 98)
+    assert np.array_equal(host(X_ct), oX_ct)
+    Y = ctx.lr_scores_standard(ctx.model_prepare(W, b), X_ct, P.N)
+    assert np.array_equal(host(Y), oracle.lr_standard(P, oX_ct, W, b))
+    slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
+    assert np.array_equal(slots.T, oracle.expected_scores(X, W, b, P.t))
+    Y1 = ctx.lr_scores_standard(ctx.model_prepare(W[:1], b), X_ct[:1], P.N)
+    assert np.array_equal(host(Y1), oracle.lr_standard(P, oX_ct[:1], W[:1], b))
