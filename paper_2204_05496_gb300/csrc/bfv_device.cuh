@@ -175,7 +175,8 @@ template <int LOGM> struct Sched {
 // LAZY: no reductions at all (ct_bfly_lazy); store receives values below (4 + 2 log2 N) q, for
 // consumers that only multiply them by Shoup constants.
 
-template <int LOGM, int NT, int P, int S, bool LAZY, class Load, class Store>
+// ILP2: the two radix-8 groups a thread handles in a pass are interleaved.
+template <int LOGM, int NT, int P, int S, bool LAZY, bool ILP2 = false, class Load, class Store>
 __device__ __forceinline__ void fwd_passes(u64 *sm, const ModTab &T, int C, int hidx, Load &load, Store &store) {
     constexpr int NP = Sched<LOGM>::NP;
     constexpr int R = Sched<LOGM>::template R<P>::value;
@@ -183,7 +184,7 @@ __device__ __forceinline__ void fwd_passes(u64 *sm, const ModTab &T, int C, int 
     constexpr int TL = M >> (S + R);
     constexpr int G = M >> R;
     const u64 q = T.q, q2 = T.q2;
-#pragma unroll 1
+#pragma unroll (ILP2 && R == 3 && G == 2 * NT ? 2 : 1)
     for (int g = threadIdx.x; g < G; g += NT) {
         const int block = g / TL, off = g % TL;
         const int base = block * (TL << R) + off;
@@ -202,7 +203,7 @@ __device__ __forceinline__ void fwd_passes(u64 *sm, const ModTab &T, int C, int 
     }
     if constexpr (P < NP - 1) {
         __syncthreads();
-        fwd_passes<LOGM, NT, P + 1, S + R, LAZY>(sm, T, C, hidx, load, store);
+        fwd_passes<LOGM, NT, P + 1, S + R, LAZY, ILP2>(sm, T, C, hidx, load, store);
     }
 }
 
@@ -210,9 +211,9 @@ template <int LOGM, int NT, class Load, class Store>
 __device__ __forceinline__ void ntt_forward(u64 *sm, const ModTab &T, int C, int hidx, Load load, Store store) {
     fwd_passes<LOGM, NT, 0, 0, false>(sm, T, C, hidx, load, store);
 }
-template <int LOGM, int NT, class Load, class Store>
+template <int LOGM, int NT, bool ILP2 = false, class Load, class Store>
 __device__ __forceinline__ void ntt_forward_lazy(u64 *sm, const ModTab &T, int C, int hidx, Load load, Store store) {
-    fwd_passes<LOGM, NT, 0, 0, true>(sm, T, C, hidx, load, store);
+    fwd_passes<LOGM, NT, 0, 0, true, ILP2>(sm, T, C, hidx, load, store);
 }
 
 // ------------------------------------------------------------------ inverse NTT driver

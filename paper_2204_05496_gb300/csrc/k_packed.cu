@@ -163,7 +163,8 @@ __global__ void __launch_bounds__(ModUpShape<LOGN>::NT) k_ks_modup(const ModTab 
             key_mac<H, NT>(acc0, acc1, k0, k1, q, [&](int p) { return c1[auto_src(h * H + p, gal, LOGN)]; });
         } else {
             const u64 *d = D + (g * L + i) * (size_t)N;   // digit i < q_i < 2 q_j
-            ntt_forward_lazy<MS::LOGH, NT>(       // outputs feed Shoup products only
+            ntt_forward_lazy<MS::LOGH, NT, MS::QS == 2>(   // outputs feed Shoup products only; interleaved
+                                                            // radix-8 groups measured faster at QS = 2 only
                 sm, T, MS::C, h,
                 [&](int p) {
                     u64 v[QS];
