@@ -425,6 +425,46 @@ __device__ __forceinline__ void limb_inverse(u64 *sm, const ModTab &T, int h, Lo
     }
 }
 
+// ------------------------------------------------------------------ tensor memory (TMEM)
+//
+// 128 lanes x 512 columns of 32-bit cells per SM. A warp reaches the 32 lanes of its quarter
+// (warp % 4); an address is (lane << 16) | column relative to the allocation's base.
+
+// One whole warp: allocate ncols columns (a power of two >= 32) and write the base address to
+// *slot; then give up the right to allocate again so that other CTAs may.
+__device__ __forceinline__ void tmem_alloc(u32 *slot, u32 ncols) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(slot)), "r"(ncols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+// One whole warp, after every thread's last access (see tmem_fence_*).
+__device__ __forceinline__ void tmem_dealloc(u32 base, u32 ncols) {
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(base), "r"(ncols) : "memory");
+}
+// Order TMEM accesses across a thread barrier: before_sync ... __syncthreads() ... after_sync.
+__device__ __forceinline__ void tmem_fence_before_sync() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void tmem_fence_after_sync() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+// 16 consecutive columns of this thread's lane (warp-wide, lane field = the warp's quarter).
+__device__ __forceinline__ void tmem_ld16(u32 addr, u32 (&r)[16]) {
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]), "=r"(r[8]),
+          "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(addr)
+        : "memory");
+}
+__device__ __forceinline__ void tmem_st16(u32 addr, const u32 (&r)[16]) {
+    asm volatile(
+        "tcgen05.st.sync.aligned.32x32b.x16.b32 [%0], {%1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+        "%15, %16};" ::"r"(addr),
+        "r"(r[0]), "r"(r[1]), "r"(r[2]), "r"(r[3]), "r"(r[4]), "r"(r[5]), "r"(r[6]), "r"(r[7]), "r"(r[8]), "r"(r[9]),
+        "r"(r[10]), "r"(r[11]), "r"(r[12]), "r"(r[13]), "r"(r[14]), "r"(r[15])
+        : "memory");
+}
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+__device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
 // ------------------------------------------------------------------ ChaCha20 (RFC 8439)
 
 __device__ __forceinline__ u32 rotl(u32 x, int n) { return __funnelshift_l(x, x, n); }

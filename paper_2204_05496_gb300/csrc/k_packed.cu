@@ -98,44 +98,56 @@ LIMB_KERNEL(LOGN) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 gal, u64
     }
 }
 
-// acc_c[p] += v(p) * key_c[p] for this thread's points p = tid + e NT, four at a time with
-// all loads issued first. The sums are not reduced: L products below 2q each stay below
-// 2 L q <= 30q < 2^64 and are reduced once at the end.
+// ModUp works on halves of H = N/2 evaluation points of a target limb: the first Cooley-Tukey
+// stage is done in the load (each CTA reads both halves of the digit) and the key-product
+// accumulators live in tensor memory, so that a half of up to 16,384 points and its
+// transform fit one CTA (the shared memory holds the transform only).
+template <int LOGN> struct ModUpShape {
+    static constexpr int LOGH = LOGN - 1;
+    static constexpr int H = 1 << LOGH;
+    static constexpr int NT = nt_for(LOGH);
+    static constexpr int PTS = H / NT;               // points per thread
+    static constexpr unsigned COLS = H / 32;         // 4 cells per point over 128 lanes
+    static constexpr size_t smem = sizeof(u64) * PadSize<H>::value + 16;   // + the TMEM base address
+    static_assert(PTS % 4 == 0 && COLS >= 32 && COLS <= 512 && (COLS & (COLS - 1)) == 0, "ModUp TMEM layout");
+};
+
+// Accumulators in tensor memory: thread t of warp w owns the points p = t + e NT (e < PTS) and
+// keeps them in lane 32 (w % 4) + t % 32, columns 4 PTS (w / 4) + 4 e + {0, 1, 2, 3} = (acc0 low,
+// acc0 high, acc1 low, acc1 high). tacc is the warp's address of its first column.
+// acc_c[p] += v(p) * key_c[p], four points per TMEM access, key loads issued first. The sums
+// are not reduced: L products below 2q each stay below 2 L q <= 30q < 2^64 (reduced at the end).
 template <int H, int NT, class Val>
-__device__ __forceinline__ void key_mac(u64 *acc0, u64 *acc1, const shoup_t *__restrict__ k0,
-                                        const shoup_t *__restrict__ k1, u64 q, Val val) {
-    static_assert(H % (4 * NT) == 0, "points per thread must be a multiple of 4");
+__device__ __forceinline__ void key_mac(u32 tacc, const shoup_t *__restrict__ k0, const shoup_t *__restrict__ k1,
+                                        u64 q, Val val) {
+    constexpr int PTS = H / NT;
 #pragma unroll 1
-    for (int p0 = threadIdx.x; p0 < H; p0 += 4 * NT) {
+    for (int e0 = 0; e0 < PTS; e0 += 4) {
         u64 v[4];
         shoup_t a[4], b[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const int p = p0 + e * NT;
+            const int p = threadIdx.x + (e0 + e) * NT;
             a[e] = __ldg(k0 + p);
             b[e] = __ldg(k1 + p);
             v[e] = val(p);
         }
+        u32 r[16];
+        tmem_ld16(tacc + 4u * e0, r);
+        tmem_wait_ld();
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const int p = p0 + e * NT;
-            acc0[p] += mul_shoup(v[e], a[e], q);
-            acc1[p] += mul_shoup(v[e], b[e], q);
+            const u64 s0 = (((u64)r[4 * e + 1] << 32) | r[4 * e]) + mul_shoup(v[e], a[e], q);
+            const u64 s1 = (((u64)r[4 * e + 3] << 32) | r[4 * e + 2]) + mul_shoup(v[e], b[e], q);
+            r[4 * e] = (u32)s0;
+            r[4 * e + 1] = (u32)(s0 >> 32);
+            r[4 * e + 2] = (u32)s1;
+            r[4 * e + 3] = (u32)(s1 >> 32);
         }
+        tmem_st16(tacc + 4u * e0, r);
     }
+    tmem_wait_st();
 }
-
-// ModUp splits each target limb into QS sub-arrays of H = N/QS evaluation points (QS = 2, or
-// 4 at N = 32768) so that the transform and both key-product accumulators fit one CTA's
-// shared memory; the first log2 QS Cooley-Tukey stages are done in the load.
-template <int LOGN> struct ModUpShape {
-    static constexpr int QS = LOGN > 14 ? 4 : 2;
-    static constexpr int C = QS == 4 ? 2 : 1;
-    static constexpr int LOGH = LOGN - C;
-    static constexpr int H = 1 << LOGH;
-    static constexpr int NT = nt_for(LOGH);
-    static constexpr size_t smem = sizeof(u64) * (PadSize<H>::value + 2 * H);
-};
 
 // grid.x = (g, j, h): U[g][c][j][h H + p] = sum_i NTT_j(D[g][i] mod q_j)[h H + p] * key[i][c][j].
 // The digit of index j itself is sigma(C1[g][j]) in evaluation form already (a permuted read).
@@ -145,14 +157,28 @@ __global__ void __launch_bounds__(ModUpShape<LOGN>::NT) k_ks_modup(const ModTab 
                                                                   const shoup_t *__restrict__ key, u64 *U) {
     extern __shared__ u64 sm[];
     using MS = ModUpShape<LOGN>;
-    constexpr int N = 1 << LOGN, H = MS::H, NT = MS::NT, QS = MS::QS;
-    u64 *acc0 = sm + PadSize<H>::value, *acc1 = acc0 + H;
+    constexpr int N = 1 << LOGN, H = MS::H, NT = MS::NT, PTS = MS::PTS;
+    u32 *tslot = (u32 *)(sm + PadSize<H>::value);
     const int nqp = L + 1;
-    const int h = blockIdx.x % QS, j = (blockIdx.x / QS) % nqp;
-    const size_t g = blockIdx.x / (QS * nqp);
+    const int h = blockIdx.x % 2, j = (blockIdx.x / 2) % nqp;
+    const size_t g = blockIdx.x / (2 * nqp);
     const ModTab T = mods[j];
     const u64 q = T.q;
-    for (int p = threadIdx.x; p < H; p += NT) { acc0[p] = 0; acc1[p] = 0; }
+    const int warp = threadIdx.x >> 5;
+    if (warp == 0) tmem_alloc(tslot, MS::COLS);
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    const u32 tbase = *tslot;
+    const u32 tacc = tbase + ((u32)(32 * (warp & 3)) << 16) + (u32)(4 * PTS * (warp >> 2));
+    {
+        u32 z[16];
+#pragma unroll
+        for (int k = 0; k < 16; ++k) z[k] = 0;
+#pragma unroll 1
+        for (int e0 = 0; e0 < PTS; e0 += 4) tmem_st16(tacc + 4u * e0, z);
+        tmem_wait_st();
+    }
     const size_t keystride = (size_t)nqp * N;     // one (digit, component) block
 #pragma unroll 1
     for (int i = 0; i < L; ++i) {
@@ -160,30 +186,40 @@ __global__ void __launch_bounds__(ModUpShape<LOGN>::NT) k_ks_modup(const ModTab 
         const shoup_t *k1 = key + ((size_t)i * 2 + 1) * keystride + (size_t)j * N + (size_t)h * H;
         if (i == j) {
             const u64 *c1 = C + ((g * 2 + 1) * L + j) * (size_t)N;
-            key_mac<H, NT>(acc0, acc1, k0, k1, q, [&](int p) { return c1[auto_src(h * H + p, gal, LOGN)]; });
+            key_mac<H, NT>(tacc, k0, k1, q, [&](int p) { return c1[auto_src(h * H + p, gal, LOGN)]; });
         } else {
             const u64 *d = D + (g * L + i) * (size_t)N;   // digit i < q_i < 2 q_j
-            ntt_forward_lazy<MS::LOGH, NT, MS::QS == 2>(   // outputs feed Shoup products only; interleaved
-                                                            // radix-8 groups measured faster at QS = 2 only
-                sm, T, MS::C, h,
+            ntt_forward_lazy<MS::LOGH, NT, true>(         // outputs feed Shoup products only
+                sm, T, 1, h,
                 [&](int p) {
-                    u64 v[QS];
-#pragma unroll
-                    for (int k = 0; k < QS; ++k) v[k] = d[p + k * H];
-                    return fold_stages<MS::C>(T, h, v);
+                    u64 v[2] = {d[p], d[p + H]};
+                    return fold_stages<1>(T, h, v);
                 },
                 [&](int p, u64 v) { sm[padi(p)] = v; });
             __syncthreads();
-            key_mac<H, NT>(acc0, acc1, k0, k1, q, [&](int p) { return sm[padi(p)]; });
+            key_mac<H, NT>(tacc, k0, k1, q, [&](int p) { return sm[padi(p)]; });
             __syncthreads();
         }
     }
     u64 *u0 = U + ((g * 2 + 0) * nqp + j) * (size_t)N + (size_t)h * H;
     u64 *u1 = U + ((g * 2 + 1) * nqp + j) * (size_t)N + (size_t)h * H;
-    for (int p = threadIdx.x; p < H; p += NT) {
-        u0[p] = red1(mul_shoup(acc0[p], 1, T.onep, q), q);
-        u1[p] = red1(mul_shoup(acc1[p], 1, T.onep, q), q);
+#pragma unroll 1
+    for (int e0 = 0; e0 < PTS; e0 += 4) {
+        u32 r[16];
+        tmem_ld16(tacc + 4u * e0, r);
+        tmem_wait_ld();
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int p = threadIdx.x + (e0 + e) * NT;
+            const u64 s0 = ((u64)r[4 * e + 1] << 32) | r[4 * e], s1 = ((u64)r[4 * e + 3] << 32) | r[4 * e + 2];
+            u0[p] = red1(mul_shoup(s0, 1, T.onep, q), q);
+            u1[p] = red1(mul_shoup(s1, 1, T.onep, q), q);
+        }
     }
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    if (warp == 0) tmem_dealloc(tbase, MS::COLS);
 }
 
 // Limb unit (g, c): R[g][c] = [INTT_P(U[g][c][P]) + floor(P/2)]_P.
@@ -343,7 +379,7 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, int nreq, const u64 *const *
             { ProfScope pr(c, BFV_K_KS_PREP, st);
               launch_limbs<LOGN>(k_ks_prep<LOGN>, ng * 2 * L, st, 0, c->dmods, L, gal, C, D); }
             { ProfScope pr(c, BFV_K_KS_MODUP, st);
-              k_ks_modup<LOGN><<<(unsigned)(ng * nqp * MS::QS), MS::NT, MS::smem, st>>>(c->dmods, L, gal, C, D, key, U); }
+              k_ks_modup<LOGN><<<(unsigned)(ng * nqp * 2), MS::NT, MS::smem, st>>>(c->dmods, L, gal, C, D, key, U); }
             { ProfScope pr(c, BFV_K_KS_MODDOWN_P, st);
               launch_limbs<LOGN>(k_ks_moddown_p<LOGN>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R); }
             { ProfScope pr(c, BFV_K_KS_MODDOWN, st);
