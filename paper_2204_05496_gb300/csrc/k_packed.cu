@@ -105,7 +105,9 @@ LIMB_KERNEL(LOGN) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 gal, u64
 template <int LOGN> struct ModUpShape {
     static constexpr int LOGH = LOGN - 1;
     static constexpr int H = 1 << LOGH;
-    static constexpr int NT = nt_for(LOGH);
+    // 256 threads where two CTAs fit an SM's shared memory (their barriers then overlap)
+    static constexpr int NT = LOGH == 13 ? 256 : nt_for(LOGH);
+    static constexpr int MINB = LOGH == 13 ? 2 : 1;
     static constexpr int PTS = H / NT;               // points per thread
     static constexpr unsigned COLS = H / 32;         // 4 cells per point over 128 lanes
     static constexpr size_t smem = sizeof(u64) * PadSize<H>::value + 16;   // + the TMEM base address
@@ -152,7 +154,7 @@ __device__ __forceinline__ void key_mac(u32 tacc, const shoup_t *__restrict__ k0
 // grid.x = (g, j, h): U[g][c][j][h H + p] = sum_i NTT_j(D[g][i] mod q_j)[h H + p] * key[i][c][j].
 // The digit of index j itself is sigma(C1[g][j]) in evaluation form already (a permuted read).
 template <int LOGN>
-__global__ void __launch_bounds__(ModUpShape<LOGN>::NT) k_ks_modup(const ModTab *__restrict__ mods, int L, u32 gal,
+__global__ void __launch_bounds__(ModUpShape<LOGN>::NT, ModUpShape<LOGN>::MINB) k_ks_modup(const ModTab *__restrict__ mods, int L, u32 gal,
                                                                   const u64 *__restrict__ C, const u64 *__restrict__ D,
                                                                   const shoup_t *__restrict__ key, u64 *U) {
     extern __shared__ u64 sm[];
