@@ -330,11 +330,15 @@ constexpr int nt_for(int logm) { return logm >= 13 ? 512 : (logm == 12 ? 256 : 1
 //    evaluation points (their butterflies stay inside it); after a cluster barrier the last
 //    stage (distance N/2, with N^-1) reads the partner's half from distributed shared memory.
 // For N <= 16384, S = 1 and these are the single-CTA transforms.
-template <int LOGN> struct Split {
-    static constexpr int S = LOGN > 14 ? 2 : 1;
+// MODE 1 also splits an N = 16384 limb over two CTAs of 256 threads (68 KB of shared memory
+// each), so that two CTAs share an SM and one's barrier waits overlap the other's work.
+template <int LOGN, int MODE = 0> struct Split {
+    static constexpr bool PAIR16K = MODE == 1 && LOGN == 14;
+    static constexpr int S = (LOGN > 14 || PAIR16K) ? 2 : 1;
     static constexpr int LOGM = LOGN - (S == 2 ? 1 : 0);
     static constexpr int M = 1 << LOGM;
-    static constexpr int NT = nt_for(LOGM);
+    static constexpr int NT = PAIR16K ? 256 : nt_for(LOGM);
+    static constexpr int MINB = PAIR16K ? 2 : 1;
 };
 
 __device__ __forceinline__ u32 cluster_rank() {
@@ -382,9 +386,9 @@ __device__ __forceinline__ u64 fold_stages(const ModTab &T, int hidx, u64 (&v)[1
 // Forward transform of one limb by CTA h of its group: load(k) returns coefficient k (< 4q,
 // any k < N); store(p, v) receives the evaluation positions p this CTA owns, in [0, q)
 // (LAZY: below 32q, for Shoup-product consumers only).
-template <int LOGN, bool LAZY = false, class Load, class Store>
+template <int LOGN, bool LAZY = false, int MODE = 0, class Load, class Store>
 __device__ __forceinline__ void limb_forward(u64 *sm, const ModTab &T, int h, Load load, Store store) {
-    using SP = Split<LOGN>;
+    using SP = Split<LOGN, MODE>;
     if constexpr (SP::S == 1) {
         fwd_passes<LOGN, SP::NT, 0, 0, LAZY>(sm, T, 0, 0, load, store);
     } else {
@@ -401,9 +405,9 @@ __device__ __forceinline__ void limb_forward(u64 *sm, const ModTab &T, int h, Lo
 // (< 2q) for the positions this CTA owns; store(k, v) receives the coefficients k it owns,
 // in [0, q). With S = 2 every thread of the cluster must call it (two cluster barriers), and
 // sm must not be written by the caller between the call and the caller's next barrier.
-template <int LOGN, class Load, class Store>
+template <int LOGN, int MODE = 0, class Load, class Store>
 __device__ __forceinline__ void limb_inverse(u64 *sm, const ModTab &T, int h, Load load, Store store) {
-    using SP = Split<LOGN>;
+    using SP = Split<LOGN, MODE>;
     if constexpr (SP::S == 1) {
         ntt_inverse<LOGN, SP::NT>(sm, T, load, store);
     } else {

@@ -123,22 +123,24 @@ struct ProfScope {
 
 // Per-limb kernels run Split<LOGN>::S CTAs per limb (a two-CTA cluster at N = 32768): `h` is
 // the CTA's part of the limb, `unit` the limb's index in the grid.
-#define LIMB_KERNEL(LOGN) __global__ void __launch_bounds__(Split<LOGN>::NT)
-#define LIMB_INDEX(LOGN)                                                    \
-    constexpr int N = 1 << LOGN, M = Split<LOGN>::M;                        \
-    const int h = Split<LOGN>::S == 1 ? 0 : (int)cluster_rank();            \
-    const u32 unit = blockIdx.x / Split<LOGN>::S;                           \
+#define LIMB_KERNEL_M(LOGN, MODE) __global__ void __launch_bounds__(Split<LOGN, MODE>::NT, Split<LOGN, MODE>::MINB)
+#define LIMB_KERNEL(LOGN) LIMB_KERNEL_M(LOGN, 0)
+#define LIMB_INDEX_M(LOGN, MODE)                                            \
+    constexpr int N = 1 << LOGN, M = Split<LOGN, MODE>::M;                  \
+    const int h = Split<LOGN, MODE>::S == 1 ? 0 : (int)cluster_rank();      \
+    const u32 unit = blockIdx.x / Split<LOGN, MODE>::S;                     \
     (void)N; (void)M; (void)h; (void)unit
+#define LIMB_INDEX(LOGN) LIMB_INDEX_M(LOGN, 0)
 
 // Launches a per-limb kernel over `units` limbs: Split<LOGN>::S CTAs of Split<LOGN>::NT
 // threads per limb (one two-CTA cluster per limb when S = 2), limb_smem<LOGN>() bytes of
 // dynamic shared memory unless `smem` says otherwise.
-template <int LOGN> constexpr size_t limb_smem() { return sizeof(u64) * PadSize<Split<LOGN>::M>::value; }
-template <int LOGN, class... KArgs, class... Args>
+template <int LOGN, int MODE = 0> constexpr size_t limb_smem() { return sizeof(u64) * PadSize<Split<LOGN, MODE>::M>::value; }
+template <int LOGN, int MODE = 0, class... KArgs, class... Args>
 cudaError_t launch_limbs(void (*kern)(KArgs...), size_t units, cudaStream_t st, size_t smem, Args... args) {
-    using SP = Split<LOGN>;
+    using SP = Split<LOGN, MODE>;
     if (!units) return cudaSuccess;
-    if (!smem) smem = limb_smem<LOGN>();
+    if (!smem) smem = limb_smem<LOGN, MODE>();
     cudaFuncSetAttribute((const void *)kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3((unsigned)(units * SP::S), 1, 1);

@@ -238,19 +238,21 @@ LIMB_KERNEL(LOGN) k_ks_moddown_p(const ModTab *__restrict__ mods, int L, const u
                        [&](int p, u64 v) { dst[p] = add_mod(v, T.phalf, T.q); });
 }
 
-// Limb unit (g, c, l): C[g][c][l] += (U[g][c][l] + NTT_l(floor(P/2) - r)) * P^-1.
+// Limb unit (g, c, l): C[g][c][l] += (U[g][c][l] + NTT_l(floor(P/2) - r)) * P^-1. Split mode 1:
+// two 256-thread CTAs per limb at N = 16384 (the first stage folded into the loads).
+constexpr int kModDownMode = 1;
 template <int LOGN>
-LIMB_KERNEL(LOGN) k_ks_moddown(const ModTab *__restrict__ mods, int L, const u64 *__restrict__ U,
-                               const u64 *__restrict__ R, u64 *C) {
+LIMB_KERNEL_M(LOGN, kModDownMode) k_ks_moddown(const ModTab *__restrict__ mods, int L, const u64 *__restrict__ U,
+                                               const u64 *__restrict__ R, u64 *C) {
     extern __shared__ u64 sm[];
-    LIMB_INDEX(LOGN);
-    constexpr int NT = Split<LOGN>::NT;
+    LIMB_INDEX_M(LOGN, kModDownMode);
+    constexpr int NT = Split<LOGN, kModDownMode>::NT;
     const int nqp = L + 1;
     const int l = (int)(unit % L), c = (int)((unit / L) % 2);
     const size_t g = unit / (2 * L);
     const ModTab T = mods[l];
     const u64 *r = R + (g * 2 + c) * (size_t)N;
-    limb_forward<LOGN, true>(sm, T, h, [&](int p) { return T.phalf + (T.q - red1(r[p], T.q)); },
+    limb_forward<LOGN, true, kModDownMode>(sm, T, h, [&](int p) { return T.phalf + (T.q - red1(r[p], T.q)); },
                        [&](int p, u64 v) { sm[padi(p & (M - 1))] = v; });
     __syncthreads();
     const u64 *u = U + ((g * 2 + c) * nqp + l) * (size_t)N + (size_t)h * M;
@@ -385,7 +387,8 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, int nreq, const u64 *const *
             { ProfScope pr(c, BFV_K_KS_MODDOWN_P, st);
               launch_limbs<LOGN>(k_ks_moddown_p<LOGN>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R); }
             { ProfScope pr(c, BFV_K_KS_MODDOWN, st);
-              launch_limbs<LOGN>(k_ks_moddown<LOGN>, ng * 2 * L, st, 0, c->dmods, L, (const u64 *)U, (const u64 *)R, C); }
+              launch_limbs<LOGN, kModDownMode>(k_ks_moddown<LOGN>, ng * 2 * L, st, 0, c->dmods, L, (const u64 *)U,
+                                               (const u64 *)R, C); }
             count_launch(c, 4);
         }
         { ProfScope pr(c, BFV_K_BIAS_MASK, st);
