@@ -184,7 +184,7 @@ __device__ __forceinline__ void fwd_passes(u64 *sm, const ModTab &T, int C, int 
     constexpr int TL = M >> (S + R);
     constexpr int G = M >> R;
     const u64 q = T.q, q2 = T.q2;
-#pragma unroll (ILP2 && R == 3 && G == 2 * NT ? 2 : 1)
+#pragma unroll (ILP2 && R == 3 && G >= 2 * NT ? 2 : 1)
     for (int g = threadIdx.x; g < G; g += NT) {
         const int block = g / TL, off = g % TL;
         const int base = block * (TL << R) + off;

@@ -191,7 +191,7 @@ __global__ void __launch_bounds__(ModUpShape<LOGN>::NT, ModUpShape<LOGN>::MINB) 
             key_mac<H, NT>(tacc, k0, k1, q, [&](int p) { return c1[auto_src(h * H + p, gal, LOGN)]; });
         } else {
             const u64 *d = D + (g * L + i) * (size_t)N;   // digit i < q_i < 2 q_j
-            ntt_forward_lazy<MS::LOGH, NT, true>(         // outputs feed Shoup products only
+            ntt_forward_lazy<MS::LOGH, NT, LOGN == 14>(   // outputs feed Shoup products only
                 sm, T, 1, h,
                 [&](int p) {
                     u64 v[2] = {d[p], d[p + H]};
