@@ -78,6 +78,10 @@ LIMB_KERNEL(LOGN) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 gal, u64
     u64 *limb = C + ((g * 2 + c) * L + l) * (size_t)N;
     if (c == 1) {
         u64 *dst = D + (g * L + l) * (size_t)N;
+        // the permuted reads below touch the whole limb in random order: bring it into L2 with
+        // coalesced line prefetches first
+        for (int i = threadIdx.x; i < N / 16; i += Split<LOGN>::NT)
+            asm volatile("prefetch.global.L2 [%0];" ::"l"(limb + 16 * i));
         limb_inverse<LOGN>(sm, T, h, [&](int p) { return limb[auto_src(p, gal, LOGN)]; },
                            [&](int p, u64 v) { dst[p] = v; });
     } else if constexpr (Split<LOGN>::S == 1) {
