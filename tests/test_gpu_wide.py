@@ -2,7 +2,7 @@
 t = 786433), the ring of the mixed-parameter batch. A limb of this ring (256 KB) is larger
 than one CTA's shared memory, so every limb transform runs on a two-CTA cluster (the forward
 transform's first stage folded into the loads, the inverse transform's last stage through
-distributed shared memory) and ModUp splits each target limb four ways. Everything is
+distributed shared memory) and ModUp keeps its key sums in tensor memory. Everything is
 compared with the oracle bit for bit, and decrypted scores with the closed form."""
 import numpy as np
 import pytest
