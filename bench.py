@@ -67,6 +67,8 @@ def parse_args(argv=None):
     p.add_argument("--uneven", action="store_true",
                    help="the uneven batch: 64 models on the N = 16384 and N = 32768 sets in one CUDA graph")
     p.add_argument("--uneven-divisor", type=int, default=1, help="divide the drawn batch sizes by this")
+    p.add_argument("--paper8k", action="store_true",
+                   help="the paper's own workload and parameters: 543 x 40,960 x 11, N = 8192, CRT pair")
     p.add_argument("--only-standard", action="store_true",
                    help="profiling case: time only the standard product on the first --features features")
     p.add_argument("--features", type=int, default=40000)
@@ -694,6 +696,81 @@ def run_uneven(args):
     return 0 if ok else 1
 
 
+def run_paper8k(args):
+    """The paper's own configuration (Section 5.2.3): 543 patients x 40,960 features x 11 classes,
+    N = 8192, plaintext moduli t0 = 1073872897 and t1 = 114689 (CRT pair), fixed-point inputs
+    (2^6) and weights (2^14). Real-valued synthetic inputs (synth.paper_realvalued). Timed with
+    CUDA events per phase, like the paper's figure: encryption (encode + encrypt, both rings),
+    computation (packed product, both rings), decryption (decrypt + decode + CRT). Every score
+    is checked against the exact integer product. The standard product runs on the same data."""
+    import torch
+    import paper_2204_05496_gb300 as bfv
+    from paper_2204_05496_gb300 import crt_pair
+    bfv.build()
+    torch.cuda.set_device(0)
+    nX, f, nY = 543, 40960, 11
+    X, W, b = synth.paper_realvalued(701, nX, f, nY)
+    Xi, Wi, bi = crt_pair.to_fixed(X, crt_pair.S_X), crt_pair.to_fixed(W, crt_pair.S_W), \
+        crt_pair.to_fixed(b, crt_pair.S_X + crt_pair.S_W)
+    exact = Xi @ Wi + bi[None, :]
+    pair = crt_pair.CrtPair(8192, 4, 43)
+    keys = pair.keygen(702)
+    models = pair.model_prepare(Wi, bi)
+    Xd = torch.from_numpy(Xi).cuda()
+
+    def ev():
+        e = torch.cuda.Event(enable_timing=True)
+        e.record()
+        return e
+
+    def once(seed):
+        e0 = ev()
+        X_cts = pair.encrypt_rows(keys, Xd, seed=seed)
+        e1 = ev()
+        Y = pair.scores_packed(keys, models, X_cts)
+        e2 = ev()
+        z = pair.decrypt_scores(keys, Y, nX, nY)
+        e3 = ev()
+        torch.cuda.synchronize()
+        return z, (e0.elapsed_time(e1), e1.elapsed_time(e2), e2.elapsed_time(e3))
+
+    z, _ = once(703)                                        # warm-up
+    ok = bool(np.array_equal(z.cpu().numpy(), exact))
+    runs = [once(704 + 2 * i)[1] for i in range(max(1, args.steps))]
+    enc, comp, dec = (statistics.median(r[k] for r in runs) for k in range(3))
+    total = enc + comp + dec
+    # standard product on the same data: feature columns, slot i = patient i
+    cols = torch.zeros((f, 8192), dtype=torch.int64, device="cuda")
+    cols[:, :nX] = Xd.T
+    std = []
+    for rep in range(2):
+        e0 = ev()
+        outs = []
+        for r, c in enumerate(pair.ctx):
+            X_ct = c.encrypt(keys[r], c.encode(cols), seed=800 + rep)
+            Ys = c.lr_scores_standard(models[r], X_ct, nX)
+            outs.append(c.decode(c.decrypt(keys[r], Ys))[:, :nX].T.contiguous())
+            del X_ct
+        zs = bfv.crt_combine(outs[0], pair.t[0], outs[1], pair.t[1])
+        e1 = ev()
+        torch.cuda.synchronize()
+        std.append(e0.elapsed_time(e1))
+        ok = ok and bool(np.array_equal(zs.cpu().numpy(), exact))
+    argmax_ok = bool(np.array_equal(np.argmax(exact, axis=1), np.argmax(z.cpu().numpy(), axis=1)))
+    print(json.dumps({
+        "case": "paper8k", "workload": "543 patients x 40,960 real-valued features x 11 classes; BFV N=8192, "
+        "4+1 x 43-bit primes, CRT pair t0=1073872897 / t1=114689, s_x=6, s_w=14",
+        "encryption_ms": round(enc, 2), "computation_ms": round(comp, 2), "decryption_ms": round(dec, 2),
+        "total_ms": round(total, 2), "predictions_per_s": round(nX / (total / 1e3), 1),
+        "paper_total_s": 46.77, "paper_computation_s": 35.52, "paper_encryption_s": 10.40,
+        "speedup_vs_paper_total": round(46.77e3 / total, 1),
+        "standard_total_ms": round(min(std), 2), "packed_speedup_vs_standard": round(min(std) / total, 2),
+        "paper_standard_total_s": "about 600 (10 min)",
+        "max_score_bits": round(float(np.log2(np.abs(exact).max())), 1), "correct": ok, "argmax_correct": argmax_ok}),
+        flush=True)
+    return 0 if ok else 1
+
+
 def run_only_standard(args):
     """Small profiling case: the standard product alone on the first --features features of the
     batch (same parameters and kernels), --warmup untimed then --steps timed calls."""
@@ -794,6 +871,8 @@ def main(argv=None):
         return run_only_packed(args)
     if args.uneven:
         return run_uneven(args)
+    if args.paper8k:
+        return run_paper8k(args)
     if args.only_standard:
         return run_only_standard(args)
     return run_gpu(args)

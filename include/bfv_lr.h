@@ -212,6 +212,15 @@ int bfv_lr_scores_packed_models(bfv_ctx *ctx, const bfv_keys *keys, int nreq, co
                                 const uint64_t *const *X_cts, const size_t *nXs, uint64_t *const *Y_cts, void *ws,
                                 size_t ws_bytes, size_t pair_chunk, uintptr_t stream);
 
+/* CRT plaintext pair (Section 4.2.2): scores needing more precision than one plaintext modulus
+ * are computed in two contexts with coprime moduli t0, t1 (the paper: 1073872897 and 114689)
+ * and recombined: out[i] = the x with x = r0[i] mod t0, x = r1[i] mod t1, centred in
+ * (-t0 t1 / 2, t0 t1 / 2]. r0, r1, out: DEVICE int64 arrays of n entries (residues in any
+ * representative, e.g. bfv_decode's slots); asynchronous on `stream`. BFV_ERR_INVALID_ARG if
+ * t0, t1 are not coprime or t0 t1 >= 2^62. No counterpart in the paper beyond the CRT itself. */
+int bfv_crt_combine(const int64_t *r0, uint64_t t0, const int64_t *r1, uint64_t t1, size_t n, int64_t *out,
+                    uintptr_t stream);
+
 /* The same product replayed from a CUDA graph: the first call with a given set of arguments
  * (handles, pointers, sizes, chunk, stream) captures every launch of bfv_lr_scores_packed
  * into a graph and later calls launch the instantiated graph, so the host issues one call

@@ -616,5 +616,20 @@ def unpack_packed_scores(P: Params, slots, nX: int, nY: int):
     return flat[(g // P.N) * P.N + g % P.N].reshape(nX, nY)
 
 
+def crt_combine(r0, t0: int, r1, t1: int):
+    """CRT plaintext pair (Section 4.2.2): element-wise, the integer x in (-t0 t1 / 2, t0 t1 / 2]
+    with x = r0 mod t0 and x = r1 mod t1, by the textbook formula
+    x = r0 t1 (t1^-1 mod t0) + r1 t0 (t0^-1 mod t1) mod t0 t1, in Python integers."""
+    T = t0 * t1
+    e0, e1 = t1 * pow(t1, -1, t0), t0 * pow(t0, -1, t1)
+    a0 = np.asarray(r0).reshape(-1)
+    a1 = np.asarray(r1).reshape(-1)
+    out = []
+    for u, v in zip(a0.tolist(), a1.tolist()):
+        x = (int(u) * e0 + int(v) * e1) % T
+        out.append(x - T if x > T // 2 else x)
+    return np.array(out, dtype=np.int64).reshape(np.shape(r0))
+
+
 def has_openmp() -> bool:
     return bool(lib().oc_has_openmp())

@@ -117,6 +117,7 @@ SIGNATURES = {
     "bfv_decrypt_noalloc_max_count": [_vp, ctypes.POINTER(_sz)],
     "bfv_lr_scores_packed_multi_workspace": [_vp, _vp, ctypes.c_int, _vp, _sz, ctypes.POINTER(_sz)],
     "bfv_lr_scores_packed_multi": [_vp, _vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _sz, _sz, _up],
+    "bfv_crt_combine": [_vp, ctypes.c_uint64, _vp, ctypes.c_uint64, _sz, _vp, _up],
     "bfv_lr_scores_packed_models_workspace": [_vp, ctypes.c_int, _vp, _vp, _sz, ctypes.POINTER(_sz)],
     "bfv_lr_scores_packed_models": [_vp, _vp, ctypes.c_int, _vp, _vp, _vp, _vp, _vp, _sz, _sz, _up],
     "bfv_lr_scores_packed_graph": [_vp, _vp, _vp, _vp, _sz, _vp, _vp, _sz, _sz, _up],
@@ -506,6 +507,31 @@ class Context:
 def as_u64(t) -> np.ndarray:
     """Device/host int64 tensor holding raw 64-bit words -> numpy uint64 array."""
     return t.detach().cpu().numpy().view(np.uint64)
+
+
+def crt_combine(r0, t0: int, r1, t1: int, out=None, stream=None):
+    """CRT plaintext pair (bfv_crt_combine): device int64 residue tensors r0 (mod t0) and r1
+    (mod t1) of equal shape -> the integers x = r0 mod t0, x = r1 mod t1, centred in
+    (-t0 t1 / 2, t0 t1 / 2]."""
+    import torch
+    r0, r1 = r0.contiguous(), r1.contiguous()
+    if r0.shape != r1.shape or r0.dtype != torch.int64 or r1.dtype != torch.int64:
+        raise ValueError("r0 and r1 must be int64 tensors of the same shape")
+    out = torch.empty_like(r0) if out is None else out
+    _call("bfv_crt_combine", _ptr(r0), t0, _ptr(r1), t1, r0.numel(), _ptr(out), _stream(stream))
+    return out
+
+
+def pack_rows(X, N: int):
+    """Integer feature rows X [nX][f] (device tensor) -> slot vectors [nX * ceil(f/N)][N]: row i's
+    features k N .. k N + N - 1 in plaintext i ceil(f/N) + k, zero-padded (the packing of
+    Section 4.2.2; encode() then maps them to plaintexts)."""
+    import torch
+    nX, f = X.shape
+    K = -(-f // N)
+    out = torch.zeros((nX, K * N), dtype=torch.int64, device=X.device)
+    out[:, :f] = X
+    return out.reshape(nX * K, N)
 
 
 def unpack_packed_scores(N: int, slots, nX: int, nY: int):

@@ -172,6 +172,8 @@ int launch_encrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *pt, size_t co
 int launch_decrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *ct, size_t count, u64 *pt, void *ws,
                    cudaStream_t st);
 int launch_model_weights(const bfv_ctx *c, bfv_model *m, const u64 *w_pt, cudaStream_t st);
+int launch_crt_combine(const int64_t *r0, u64 t0, const int64_t *r1, u64 t1, u64 inv, size_t n, int64_t *out,
+                       cudaStream_t st);
 
 // Requests fused into one packed product, passed to kernels by value. Every request has its
 // own model (several requests may share one).

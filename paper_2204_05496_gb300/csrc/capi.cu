@@ -642,6 +642,17 @@ int bfv_lr_scores_packed_models(bfv_ctx *ctx, const bfv_keys *keys, int nreq, co
     return launch_packed_multi(ctx, keys, nreq, (const u64 *const *)X_cts, (u64 *const *)Y_cts, ws, plan, S(stream));
 }
 
+int bfv_crt_combine(const int64_t *r0, uint64_t t0, const int64_t *r1, uint64_t t1, size_t n, int64_t *out,
+                    uintptr_t stream) {
+    if (t0 < 2 || t1 < 2 || (n && (!r0 || !r1 || !out))) return BFV_ERR_INVALID_ARG;
+    if ((u128)t0 * t1 >= ((u128)1 << 62)) return BFV_ERR_INVALID_ARG;
+    u64 g = t0, h = t1;
+    while (h) { const u64 r = g % h; g = h; h = r; }
+    if (g != 1) return BFV_ERR_INVALID_ARG;
+    const u64 inv = inv_h(t0 % t1, t1);
+    return launch_crt_combine(r0, t0, r1, t1, inv, n, out, S(stream));
+}
+
 int bfv_lr_scores_packed_graph(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint64_t *X_ct,
                                size_t nX, uint64_t *Y_ct, void *ws, size_t ws_bytes, size_t pair_chunk,
                                uintptr_t stream) {

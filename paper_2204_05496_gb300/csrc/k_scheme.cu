@@ -487,6 +487,35 @@ int launch_model_weights(const bfv_ctx *c, bfv_model *m, const u64 *w_pt, cudaSt
     return last_err();
 }
 
+// ====================================================================== CRT plaintext pair
+//
+// Section 4.2.2: scores that need more precision than one plaintext modulus are computed under
+// two coprime moduli t0, t1 and recombined by the client. Garner's form:
+// x = r0 + t0 ((r1 - r0) t0^-1 mod t1) in [0, t0 t1), returned centred in (-t0 t1 / 2, t0 t1 / 2].
+
+namespace {
+
+__global__ void k_crt_combine(const int64_t *__restrict__ r0, const int64_t *__restrict__ r1, u64 t0, u64 t1,
+                              u64 inv, size_t n, int64_t *out) {
+    const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    const int64_t s0 = (int64_t)t0, s1 = (int64_t)t1;
+    const u64 a = (u64)(((r0[i] % s0) + s0) % s0), b = (u64)(((r1[i] % s1) + s1) % s1);
+    const u64 d = (b + t1 - a % t1) % t1;               // (r1 - r0) mod t1
+    const u64 x = a + t0 * ((d * inv) % t1);            // < t0 t1 < 2^62
+    const u64 T = t0 * t1;
+    out[i] = x > T / 2 ? (int64_t)x - (int64_t)T : (int64_t)x;
+}
+
+}  // namespace
+
+int launch_crt_combine(const int64_t *r0, u64 t0, const int64_t *r1, u64 t1, u64 inv, size_t n, int64_t *out,
+                       cudaStream_t st) {
+    if (!n) return BFV_OK;
+    k_crt_combine<<<(unsigned)((n + 255) / 256), 256, 0, st>>>(r0, r1, t0, t1, inv, n, out);
+    return cudaGetLastError() == cudaSuccess ? BFV_OK : BFV_ERR_CUDA;
+}
+
 // ====================================================================== allocation-free decryption
 //
 // bfv_decrypt_noalloc: decryption whose scratch (the per-limb residues [c0 + c1 s]_{q_l})

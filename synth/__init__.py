@@ -49,6 +49,10 @@ TINY = BfvShape(N=4096, L=3, prime_bits=36, t=65537)
 PAPER16K = BfvShape(N=16384, L=7, prime_bits=54, t=786433)
 # Ring degree 32768, fifteen 55-bit primes + special prime (log QP ~ 880).
 WIDE32K = BfvShape(N=32768, L=15, prime_bits=55, t=786433)
+# the paper's own parameter set (Section 5.2.3): N = 8192 with the CRT pair of plaintext moduli;
+# 4 + 1 primes of 43 bits (log QP = 215, within the 218 bits SEAL allows at 128-bit security)
+PAPER8K_T0 = BfvShape(N=8192, L=4, prime_bits=43, t=1073872897)
+PAPER8K_T1 = BfvShape(N=8192, L=4, prime_bits=43, t=114689)
 
 WORKLOADS = {
     "tiny-1": Workload("tiny-1", TINY, 1000, 8, 1, 0.05, 101, 102, 103),
@@ -117,6 +121,29 @@ def uneven_batch(seed: int = 401, count: int = 64, x_divisor: int = 1):
         out.append(dict(params=ps, f=f, nY=y, nX=nX, X=features(sm, nX, f, 0.02), W=weights(sm, f, y),
                         b=bias(sm, y), enc_seed=1000 * seed + 500 + m))
     return out
+
+
+def paper_realvalued(seed: int, n_individuals: int, n_features: int, n_classes: int):
+    """Real-valued inputs shaped like the paper's encodings (Section 4.1.2) and a real LR model:
+    the first 57% of the columns are CNV features (integers 0..4, mostly 2), the rest SNV-impact
+    features (a gene carries 1..3 SNVs with probability 0.02, each contributing m s with m in
+    {1.0, 0.75, 0.5, 0.25} and s uniform in [0, 1)); all inputs lie in [0, 2^8). Weights are
+    uniform in (-1, 1) with 70% set to zero (a Lasso-trained model), biases uniform in (-1, 1).
+    Returns float64 (X [|X|][f], W [f][|Y|], b [|Y|])."""
+    rng = np.random.default_rng([seed, 7])
+    f_cnv = int(round(0.57 * n_features))
+    X = np.zeros((n_individuals, n_features))
+    X[:, :f_cnv] = rng.choice([0, 1, 2, 3, 4], size=(n_individuals, f_cnv), p=[0.05, 0.15, 0.6, 0.15, 0.05])
+    f_snv = n_features - f_cnv
+    present = rng.random((n_individuals, f_snv)) < 0.02
+    count = rng.integers(1, 4, size=(n_individuals, f_snv))
+    for k in range(3):
+        m = rng.choice([1.0, 0.75, 0.5, 0.25], size=(n_individuals, f_snv))
+        s = rng.random((n_individuals, f_snv))
+        X[:, f_cnv:] += np.where(present & (count > k), m * s, 0.0)
+    W = rng.uniform(-1, 1, size=(n_features, n_classes)) * (rng.random((n_features, n_classes)) < 0.3)
+    b = rng.uniform(-1, 1, size=n_classes)
+    return X, W, b
 
 
 def poisson_arrivals(seed: int, rate_per_s: float, n_requests: int,

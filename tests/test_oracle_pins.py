@@ -477,3 +477,33 @@ def test_reading_with_two_ciphertext_primes_fails(tiny):
     got = oracle.unpack_packed_scores(PA, oracle.decode(PA, oracle.decrypt(PA, kA.sk, Y)), 1, 8)
     assert not np.array_equal(got, oracle.expected_scores(X, W, b, PA.t))
     assert oracle.noise_budget_bits(PA, kA.sk, Y) < 1
+
+
+# ----------------------------------------------------------------------------- CRT plaintext pair
+
+def test_crt_combine_recovers_integers():
+    """Section 4.2.2's pair t0 = 1073872897, t1 = 114689: residues of any integer in
+    (-t0 t1 / 2, t0 t1 / 2] recombine to it; checked against sympy's CRT as well."""
+    from sympy.ntheory.modular import crt
+    t0, t1 = 1073872897, 114689
+    T = t0 * t1
+    rng = np.random.default_rng(5)
+    xs = [int(v) for v in rng.integers(-(T // 2) + 1, T // 2, size=200)] + [T // 2, -(T // 2) + 1, 0, 1, -1]
+    r0 = np.array([x % t0 for x in xs], dtype=np.int64)
+    r1 = np.array([x % t1 for x in xs], dtype=np.int64)
+    got = oracle.crt_combine(r0, t0, r1, t1)
+    assert got.tolist() == xs
+    for x, a, b in zip(xs[:20], r0, r1):
+        v, m = crt([t0, t1], [int(a), int(b)])
+        assert m == T and (v - x) % T == 0
+
+
+def test_fixed_point_precision_matches_paper():
+    """Section 4.2.2: inputs below 2^8 scaled by 2^6, weights below 1 by 2^14; at f = 40,960 the
+    scaled scores need 44 bits, which the CRT pair (about 46 bits) holds and one modulus does not."""
+    import math
+    from paper_2204_05496_gb300 import crt_pair
+    assert crt_pair.bits_needed(40960) == 44
+    assert math.log2(crt_pair.T0 * crt_pair.T1) > 44 + 1 > math.log2(crt_pair.T0)
+    assert crt_pair.to_fixed([0.5, 255.99, 3.0], crt_pair.S_X).tolist() == [32, 16383, 192]
+    assert crt_pair.to_fixed([-0.99994, 0.25], crt_pair.S_W).tolist() == [-16383, 4096]
