@@ -1,13 +1,14 @@
 """Continuous-batching request loop for encrypted LR scoring (packed product, Algorithm 1).
 
 A request carries the encrypted inputs of one or more individuals (already on the device,
-uint64[nX][ceil(f/N)][2][L][N]) and receives its own output ciphertexts. The server keeps
-the Galois keys and the encoded model resident, and:
+uint64[nX][ceil(f/N)][2][L][N]), names the model that scores it (the server may hold several,
+e.g. a bank of one-vs-rest binary models with their own feature counts) and receives its own
+output ciphertexts. The server keeps the Galois keys and the encoded models resident, and:
 
   * admits waiting requests while the workspace of the launch they would join fits the HBM
     budget next to the launches already in flight (larger requests wait for memory);
-  * fuses every admitted request (up to 64 requests / `max_pairs` pairs) into ONE packed
-    product (bfv_lr_scores_packed_multi), each request keeping its own outputs;
+  * fuses every admitted request (up to 64 requests / `max_pairs` pairs, any mix of models)
+    into ONE packed product (bfv_lr_scores_packed_models), each request keeping its own outputs;
   * runs up to `n_streams` such launches at once on separate CUDA streams, so a batch formed
     from requests that arrived while another batch was on the GPU overlaps with it;
   * with `small_pairs` > 0, keeps two classes: requests of at most `small_pairs` pairs are
@@ -32,6 +33,7 @@ class Request:
     rid: int
     X_ct: object                 # device tensor [nX][K][2][L][N]
     t_arrival: float             # seconds on the server clock
+    model: int = 0               # index of the scoring model in the server's list
     out: object = None           # device tensor of output ciphertexts, set at launch
     t_done: float | None = None  # seconds on the server clock, set at completion
     batch: int = -1
@@ -47,7 +49,8 @@ class Server:
         if torch_module is None:
             import torch as torch_module
         torch = self.torch = torch_module
-        self.ctx, self.keys, self.model = ctx, keys, model
+        self.ctx, self.keys = ctx, keys
+        self.models = list(model) if isinstance(model, (list, tuple)) else [model]
         self.budget = int(hbm_budget_bytes)
         self.max_pairs, self.pair_chunk = max_pairs, pair_chunk
         self.small_pairs = small_pairs
@@ -78,13 +81,18 @@ class Server:
     def now(self) -> float:
         return time.perf_counter() - self.t0_host
 
-    def submit(self, rid: int, X_ct, t_arrival: float | None = None) -> Request:
-        r = Request(rid, X_ct, self.now() if t_arrival is None else t_arrival)
+    def submit(self, rid: int, X_ct, t_arrival: float | None = None, model: int = 0) -> Request:
+        if not 0 <= model < len(self.models):
+            raise ValueError(f"request {rid} names model {model}; the server holds {len(self.models)}")
+        r = Request(rid, X_ct, self.now() if t_arrival is None else t_arrival, model)
         self.waiting.append(r)
         return r
 
+    def _pairs(self, r: Request) -> int:
+        return r.nX * self.models[r.model].nY
+
     def _ws_bytes(self, reqs) -> int:
-        return self.ctx.multi_workspace(self.model, [r.nX for r in reqs], self.pair_chunk)
+        return self.ctx.models_workspace([self.models[r.model] for r in reqs], [r.nX for r in reqs], self.pair_chunk)
 
     def _retire(self):
         for s, b in enumerate(self.busy):
@@ -98,7 +106,7 @@ class Server:
                 self.busy[s] = None
 
     def _class(self, r: Request) -> str:
-        return "small" if r.nX * self.model.nY <= self.small_pairs else "large"
+        return "small" if self._pairs(r) <= self.small_pairs else "large"
 
     def _launch(self):
         torch = self.torch
@@ -111,7 +119,7 @@ class Server:
             for r in self.waiting:
                 if self.classes[s] is not None and self._class(r) != self.classes[s]:
                     continue
-                p = r.nX * self.model.nY
+                p = self._pairs(r)
                 if take and (pairs + p > self.max_pairs or len(take) == 64):
                     break
                 if self.in_flight_bytes + self._ws_bytes(take + [r]) > self.budget:
@@ -124,8 +132,9 @@ class Server:
             stream = self.streams[s]
             with torch.cuda.stream(stream):
                 ws = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{self.ctx.device}")
-                outs = self.ctx.lr_scores_packed_multi(self.keys, self.model, [r.X_ct for r in take], ws=ws,
-                                                       pair_chunk=self.pair_chunk, stream=stream)
+                outs = self.ctx.lr_scores_packed_models(self.keys, [self.models[r.model] for r in take],
+                                                        [r.X_ct for r in take], ws=ws, pair_chunk=self.pair_chunk,
+                                                        stream=stream)
                 ev = torch.cuda.Event(enable_timing=True)
                 ev.record(stream)
             for r, o in zip(take, outs):
@@ -154,8 +163,9 @@ class Server:
                                       f"more than the HBM budget of {self.budget}")
 
     def run(self, arrivals, make_inputs, poll_s: float = 0.0005, max_seconds: float = 600.0):
-        """Replays an arrival trace: arrivals = [(t_seconds, nX)], make_inputs(i, nX) -> X_ct.
-        Returns the completed requests. Raises TimeoutError after max_seconds of wall time."""
+        """Replays an arrival trace: arrivals = [(t_seconds, nX)] or [(t_seconds, nX, model)],
+        make_inputs(i, nX) -> X_ct. Returns the completed requests. Raises TimeoutError after
+        max_seconds of wall time."""
         self.start()
         k = 0
         while k < len(arrivals) or not self.idle():
@@ -163,7 +173,8 @@ class Server:
             if now > max_seconds:
                 raise TimeoutError(f"trace not served within {max_seconds} s")
             while k < len(arrivals) and arrivals[k][0] <= now:
-                self.submit(k, make_inputs(k, arrivals[k][1]), arrivals[k][0])
+                a = arrivals[k]
+                self.submit(k, make_inputs(k, a[1]), a[0], a[2] if len(a) > 2 else 0)
                 k += 1
             self.step()
             self._check_admissible()

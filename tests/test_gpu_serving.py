@@ -104,3 +104,38 @@ def test_server_priority_classes_keep_results(env):
     assert not set(small) & set(large)                # the two classes never share a launch
     for r in done:
         assert torch.equal(r.out, _alone(ctx, keys, model, r.X_ct))
+
+
+def test_server_binary_bank_mixes_models(env):
+    """The paper's bank of one-vs-rest binary models (one per cancer type, each with its own
+    features): every patient is scored by all 11 models; requests of different models fuse into
+    shared launches and each output equals its model's single-request product."""
+    from paper_2204_05496_gb300 import serve
+    bfv, ctx, keys, model, X, W, b, X_ct = env
+    rng = np.random.default_rng(43)
+    fs = [int(v) for v in rng.integers(200, 3000, size=11)]
+    bank_W = [rng.integers(-127, 128, (f, 2)) for f in fs]
+    bank_b = [rng.integers(-127, 128, 2) for _ in fs]
+    bank = [ctx.model_prepare(Wm, bm) for Wm, bm in zip(bank_W, bank_b)]
+    patients = [(rng.random((1 + (p % 3), 3000)) < 0.05).astype(np.uint8) for p in range(4)]
+    inputs = {}
+    arrivals = []
+    for p, Xp in enumerate(patients):
+        for m, f in enumerate(fs):
+            k = len(arrivals)
+            Xm = Xp[:, :f]
+            pt = ctx.encode_features(torch.from_numpy(Xm).cuda())
+            inputs[k] = (ctx.encrypt(keys, pt.reshape(-1, ctx.N), seed=900 + k).reshape(Xm.shape[0], -1, 2, ctx.L, ctx.N),
+                         Xm, m)
+            arrivals.append((0.0005 * p, Xm.shape[0], m))
+    srv = serve.Server(ctx, keys, bank, hbm_budget_bytes=8 << 30, n_streams=2)
+    done = srv.run(arrivals, lambda k, n: inputs[k][0])
+    assert len(done) == len(arrivals) and srv.nbatches < len(arrivals)
+    assert any(len({r.model for r in done if r.batch == bt}) > 1 for bt in {r.batch for r in done})
+    for r in done:
+        X_k, Xm, m = inputs[r.rid]
+        assert r.model == m
+        assert torch.equal(r.out, ctx.lr_scores_packed(keys, bank[m], X_k))
+        slots = ctx.decode(ctx.decrypt(keys, r.out)).cpu().numpy()
+        got = bfv.unpack_packed_scores(ctx.N, slots, Xm.shape[0], 2)
+        assert np.array_equal(got, oracle.expected_scores(Xm, bank_W[m], bank_b[m], ctx.t))

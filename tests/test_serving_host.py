@@ -39,12 +39,14 @@ class _Ctx:
 
     def __init__(self):
         self.launches = []
+        self.models_seen = []
 
-    def multi_workspace(self, model, nXs, chunk=0):
+    def models_workspace(self, models, nXs, chunk=0):
         return 100 * sum(nXs)
 
-    def lr_scores_packed_multi(self, keys, model, xs, ws=None, pair_chunk=0, stream=None):
+    def lr_scores_packed_models(self, keys, models, xs, ws=None, pair_chunk=0, stream=None):
         self.launches.append([x.shape[0] for x in xs])
+        self.models_seen.append(list(models))
         return [object() for _ in xs]
 
 
@@ -107,3 +109,21 @@ def test_request_larger_than_budget_raises(fake_torch):
     srv, ctx = make(fake_torch, hbm_budget_bytes=150, n_streams=2)
     with pytest.raises(MemoryError):
         srv.run([(0.0, 2)], lambda k, n: _X(n), max_seconds=5)
+
+
+def test_requests_of_different_models_fuse_and_count_their_own_pairs(fake_torch):
+    # a bank of binary (2-class) models and a 16-class model: pairs = individuals x classes
+    # of each request's own model
+    ctx = _Ctx()
+    bank = [types.SimpleNamespace(nY=2, name=f"binary{k}") for k in range(3)] + [types.SimpleNamespace(nY=16)]
+    srv = serve.Server(ctx, None, bank, hbm_budget_bytes=10 ** 6, n_streams=1, max_pairs=39,
+                       torch_module=fake_torch)
+    srv.start()
+    for k, (n, m) in enumerate([(1, 0), (1, 1), (1, 2), (2, 3), (1, 0)]):
+        srv.submit(k, _X(n), model=m)
+    srv.step()
+    # 2 + 2 + 2 + 32 = 38 pairs fit the 39-pair cap; the fifth request (2 more pairs) waits
+    assert ctx.launches == [[1, 1, 1, 2]]
+    assert [getattr(m, "name", "y16") for m in ctx.models_seen[0]] == ["binary0", "binary1", "binary2", "y16"]
+    with pytest.raises(ValueError):
+        srv.submit(9, _X(1), model=7)
