@@ -175,6 +175,19 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def gather_step_ms(step_ms, world, device):
+    """Every rank's mean step time, gathered to all ranks (torch.distributed; NCCL on the GPU
+    ranks, gloo in the CPU tests). One rank: no collective."""
+    if world <= 1:
+        return [step_ms]
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(step_ms)], dtype=torch.float64, device=device)
+    allt = [torch.zeros_like(t) for _ in range(world)]
+    dist.all_gather(allt, t)
+    return [float(x.item()) for x in allt]
+
+
 def aggregate(per_rank_ms, units_per_rank):
     """Whole-job throughput from per-rank step times: every rank processes its own batch;
     the job takes as long as the slowest rank (max over ranks)."""
@@ -316,14 +329,9 @@ def run_gpu(args):
     clocks = sampler.stop()
     gpu_launches = ctx.launch_count() - launches0
     step_ms = sum(a.elapsed_time(z) for a, z in evs) / args.steps
+    per_rank = gather_step_ms(step_ms, world, dev)
     if world > 1:
-        t = torch.tensor([step_ms], device=dev)
-        allt = [torch.zeros_like(t) for _ in range(world)]
-        dist.all_gather(allt, t)
-        per_rank = [float(x.item()) for x in allt]
         dist.barrier()
-    else:
-        per_rank = [step_ms]
     value, slow_ms = aggregate(per_rank, nX)
     if not np.array_equal(scores.cpu().numpy(), want):
         raise SystemExit("benchmarked path produced wrong scores")
