@@ -1,6 +1,8 @@
 // k_packed.cu -- the packed matrix product of Algorithm 1 (Section 4.2.3) with bias.
 //
-// Pairs g = i*|Y| + j are processed in chunks. Per chunk, in evaluation form:
+// Pairs g = i*|Y| + j (numbered request by request when several requests, each with its own
+// model, share the product) are processed in chunks. Per chunk, in evaluation form:
+//   inputs       the chunk's individuals' ciphertexts -> evaluation form
 //   MAC          C[g] = sum_k X[i][k] (.) W[j][k]                         (Algorithm 1 lines 5-13)
 //   log2 N times C[g] += rot_gal(C[g])                                    (lines 14-17)
 //       rot(c) = (sigma(c0) + u0', u1'), (u0', u1') = KS(sigma(c1)):
@@ -9,7 +11,7 @@
 //       ks_modup    for target limb j of QP and half h of the evaluation points:
 //                   U_c[j] = sum_i NTT_j(d_i mod q_j) (.) key[i][c][j]; the first
 //                   Cooley-Tukey stage is folded into the load, so each CTA transforms
-//                   only its half of the points
+//                   only its half of the points; the two sums live in tensor memory
 //       ks_moddown_p  inverse NTT of U_c[P], r = [U_c[P] + floor(P/2)]_P
 //       ks_moddown  C_c[l] += (U_c[l] + NTT_l(floor(P/2) - r)) * P^-1
 //   bias+mask    C0 += Delta b_j; C *= NTT(mask_g), mask_g one-hot at slot g mod N (18-22)
