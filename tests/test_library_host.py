@@ -83,3 +83,29 @@ def test_product_code_never_touches_the_oracle():
                 assert not re.search(r"\boracle\b", src), f
     for f in ("bfv_lr.h",):
         assert "oracle" not in open(os.path.join(ROOT, "include", f)).read()
+
+
+@pytest.mark.parametrize("logn", [12, 13, 14, 15])
+def test_modup_tensor_memory_layout_is_a_partition(logn):
+    """ModUp's key sums in tensor memory: thread t of warp w owns points t + e NT (e < PTS) and
+    keeps each in lane 32 (w % 4) + t % 32, columns 4 PTS (w / 4) + 4 e .. + 3. For every ring
+    the cells of all threads must tile the allocation (128 lanes x H/32 columns, a power of two
+    in 32..512) exactly once, every point must be owned once, and a warp's accesses (16 columns
+    at a time) must stay inside its 32-lane quarter and the allocation."""
+    H = 1 << (logn - 1)
+    nt = {11: 128, 12: 256, 13: 256, 14: 512}[logn - 1]     # threads per ModUp CTA
+    pts, cols = H // nt, H // 32
+    assert pts % 4 == 0 and 32 <= cols <= 512 and cols & (cols - 1) == 0
+    cells, points = set(), set()
+    for t in range(nt):
+        w, lane = t // 32, 32 * ((t // 32) % 4) + t % 32
+        base = 4 * pts * (w // 4)
+        for e in range(pts):
+            points.add(t + e * nt)
+            for k in range(4):
+                cells.add((lane, base + 4 * e + k))
+        for e0 in range(0, pts, 4):
+            first = base + 4 * e0
+            assert first % 16 == 0 and first + 15 < cols
+    assert points == set(range(H))
+    assert cells == {(ln, c) for ln in range(128) for c in range(cols)}

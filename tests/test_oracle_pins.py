@@ -122,7 +122,7 @@ def test_gaussian_table_against_float_evaluation():
 
 # ----------------------------------------------------------------------------- parameters
 
-@pytest.mark.parametrize("bits,N,count", [(30, 16, 4), (36, 4096, 4), (54, 16384, 8), (55, 32768, 16)])
+@pytest.mark.parametrize("bits,N,count", [(30, 16, 4), (36, 4096, 4), (43, 8192, 5), (54, 16384, 8), (55, 32768, 16)])
 def test_prime_rule(bits, N, count):
     ps = oracle.ntt_primes(bits, N, count)
     assert len(ps) == count and ps == sorted(ps, reverse=True)
