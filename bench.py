@@ -103,16 +103,24 @@ def modmuls_per_pair(kind, N, L, K):
     }[kind]
 
 
-def source_hash(*paths):
+# The source that defines ModUp: its region of k_packed.cu (shape, key products, kernel) and the
+# device header (transforms, arithmetic, tensor memory).
+MODUP_REGION = ("paper_2204_05496_gb300/csrc/k_packed.cu", "// ModUp works on halves", "// Limb unit (g, c): R[g][c]")
+
+
+def modup_source_hash():
+    path, start, end = MODUP_REGION
+    txt = open(os.path.join(ROOT, path)).read()
     h = hashlib.sha256()
-    for p in paths:
-        with open(os.path.join(ROOT, p), "rb") as f:
-            h.update(f.read())
+    h.update(txt[txt.index(start):txt.index(end)].encode())
+    with open(os.path.join(ROOT, "paper_2204_05496_gb300/csrc/bfv_device.cuh"), "rb") as f:
+        h.update(f.read())
     return h.hexdigest()[:16]
 
 
 def recorded_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the current source."""
+    """DRAM bytes per launch from the committed ncu summary, if taken on the kernel's current
+    source (null otherwise)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.md")
     try:
         txt = open(path).read()
@@ -122,8 +130,7 @@ def recorded_traffic(kernel):
     h = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
     if not m or not h:
         return None
-    cur = source_hash("paper_2204_05496_gb300/csrc/k_packed.cu", "paper_2204_05496_gb300/csrc/bfv_device.cuh")
-    return float(m.group(1)) if h.group(1) == cur else None
+    return float(m.group(1)) if h.group(1) == modup_source_hash() else None
 
 
 class ClockSampler:

@@ -69,11 +69,12 @@ __global__ void __launch_bounds__(256) k_mac(const ModTab *__restrict__ mods, in
 // ------------------------------------------------------------------ key switching
 
 // Limb unit (g, c, l). c = 1: digit D[g][l] = INTT(sigma(C1[g][l])); c = 0: C0 += sigma(C0).
-template <int LOGN>
-LIMB_KERNEL(LOGN) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 gal, u64 *C, u64 *D) {
+// (MODE 1, two 256-thread CTAs per limb at N = 16384, was measured slower at every chunk size.)
+template <int LOGN, int MODE>
+LIMB_KERNEL_M(LOGN, MODE) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 gal, u64 *C, u64 *D) {
     extern __shared__ u64 sm[];
-    LIMB_INDEX(LOGN);
-    constexpr int NT = Split<LOGN>::NT;
+    LIMB_INDEX_M(LOGN, MODE);
+    constexpr int NT = Split<LOGN, MODE>::NT;
     const int l = (int)(unit % L), c = (int)((unit / L) % 2);
     const size_t g = unit / (2 * L);
     const ModTab T = mods[l];
@@ -82,11 +83,11 @@ LIMB_KERNEL(LOGN) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 gal, u64
         u64 *dst = D + (g * L + l) * (size_t)N;
         // the permuted reads below touch the whole limb in random order: bring it into L2 with
         // coalesced line prefetches first
-        for (int i = threadIdx.x; i < N / 16; i += Split<LOGN>::NT)
+        for (int i = threadIdx.x; i < N / 16; i += NT)
             asm volatile("prefetch.global.L2 [%0];" ::"l"(limb + 16 * i));
-        limb_inverse<LOGN>(sm, T, h, [&](int p) { return limb[auto_src(p, gal, LOGN)]; },
-                           [&](int p, u64 v) { dst[p] = v; });
-    } else if constexpr (Split<LOGN>::S == 1) {
+        limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return limb[auto_src(p, gal, LOGN)]; },
+                                 [&](int p, u64 v) { dst[p] = v; });
+    } else if constexpr (Split<LOGN, MODE>::S == 1) {
         for (int p = threadIdx.x; p < N; p += NT) sm[p] = limb[p];
         __syncthreads();
         for (int p = threadIdx.x; p < N; p += NT) limb[p] = add_mod(sm[p], sm[auto_src(p, gal, LOGN)], T.q);
@@ -230,18 +231,19 @@ __global__ void __launch_bounds__(ModUpShape<LOGN>::NT, ModUpShape<LOGN>::MINB) 
     if (warp == 0) tmem_dealloc(tbase, MS::COLS);
 }
 
-// Limb unit (g, c): R[g][c] = [INTT_P(U[g][c][P]) + floor(P/2)]_P.
-template <int LOGN>
-LIMB_KERNEL(LOGN) k_ks_moddown_p(const ModTab *__restrict__ mods, int L, const u64 *__restrict__ U, u64 *R) {
+// Limb unit (g, c): R[g][c] = [INTT_P(U[g][c][P]) + floor(P/2)]_P. MODE 1 (two 256-thread CTAs
+// per limb at N = 16384) on small pair chunks.
+template <int LOGN, int MODE>
+LIMB_KERNEL_M(LOGN, MODE) k_ks_moddown_p(const ModTab *__restrict__ mods, int L, const u64 *__restrict__ U, u64 *R) {
     extern __shared__ u64 sm[];
-    LIMB_INDEX(LOGN);
+    LIMB_INDEX_M(LOGN, MODE);
     const int nqp = L + 1;
     const size_t gc = unit;
     const ModTab T = mods[L];
     const u64 *src = U + (gc * nqp + L) * (size_t)N;
     u64 *dst = R + gc * N;
-    limb_inverse<LOGN>(sm, T, h, [&](int p) { return src[p]; },
-                       [&](int p, u64 v) { dst[p] = add_mod(v, T.phalf, T.q); });
+    limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return src[p]; },
+                             [&](int p, u64 v) { dst[p] = add_mod(v, T.phalf, T.q); });
 }
 
 // Limb unit (g, c, l): C[g][c][l] += (U[g][c][l] + NTT_l(floor(P/2) - r)) * P^-1. Split mode 1:
@@ -387,11 +389,15 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, int nreq, const u64 *const *
             const u32 gal = (u32)c->galois[s];
             const shoup_t *key = k->gk_eval + (size_t)s * keyblock;
             { ProfScope pr(c, BFV_K_KS_PREP, st);
-              launch_limbs<LOGN>(k_ks_prep<LOGN>, ng * 2 * L, st, 0, c->dmods, L, gal, C, D); }
+              launch_limbs<LOGN, 0>(k_ks_prep<LOGN, 0>, ng * 2 * L, st, 0, c->dmods, L, gal, C, D); }
             { ProfScope pr(c, BFV_K_KS_MODUP, st);
               k_ks_modup<LOGN><<<(unsigned)(ng * nqp * 2), MS::NT, MS::smem, st>>>(c->dmods, L, gal, C, D, key, U); }
+            // two limbs per pair leave most SMs idle on small chunks: split each over two CTAs
+            // there (measured: 41 -> 33 us per launch at 16 pairs; slower on full chunks)
             { ProfScope pr(c, BFV_K_KS_MODDOWN_P, st);
-              launch_limbs<LOGN>(k_ks_moddown_p<LOGN>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R); }
+              if (ng * 2 < (size_t)2 * c->sms)
+                  launch_limbs<LOGN, 1>(k_ks_moddown_p<LOGN, 1>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R);
+              else launch_limbs<LOGN, 0>(k_ks_moddown_p<LOGN, 0>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R); }
             { ProfScope pr(c, BFV_K_KS_MODDOWN, st);
               launch_limbs<LOGN, kModDownMode>(k_ks_moddown<LOGN>, ng * 2 * L, st, 0, c->dmods, L, (const u64 *)U,
                                                (const u64 *)R, C); }
