@@ -331,14 +331,15 @@ constexpr int nt_for(int logm) { return logm >= 13 ? 512 : (logm == 12 ? 256 : 1
 //    stage (distance N/2, with N^-1) reads the partner's half from distributed shared memory.
 // For N <= 16384, S = 1 and these are the single-CTA transforms.
 // MODE 1 also splits an N = 16384 limb over two CTAs of 256 threads (68 KB of shared memory
-// each), so that two CTAs share an SM and one's barrier waits overlap the other's work.
+// each), three of which share an SM (80 registers each) so that one's barrier waits overlap the
+// others' work.
 template <int LOGN, int MODE = 0> struct Split {
     static constexpr bool PAIR16K = MODE == 1 && LOGN == 14;
     static constexpr int S = (LOGN > 14 || PAIR16K) ? 2 : 1;
     static constexpr int LOGM = LOGN - (S == 2 ? 1 : 0);
     static constexpr int M = 1 << LOGM;
     static constexpr int NT = PAIR16K ? 256 : nt_for(LOGM);
-    static constexpr int MINB = PAIR16K ? 2 : 1;
+    static constexpr int MINB = PAIR16K ? 3 : 1;
 };
 
 __device__ __forceinline__ u32 cluster_rank() {
