@@ -29,7 +29,16 @@ paper fixes none of its internal conventions, so this module takes these reading
     rounding; encryption randomness: ChaCha20 (RFC 8439) blocks, key = the 64-bit
     seed, nonce = (purpose, object, limb), block counter = coefficient index.
 
-Parity pins for every function are in tests/test_oracle_*.py.
+The CRT plaintext pair of Section 4.2.2 is recombined by the textbook CRT formula
+(crt_combine).
+
+Pins (tests/test_oracle_pins.py) tie every function to something other than itself: RFC 8439
+vectors, schoolbook convolution, direct evaluation, sympy's primality and CRT, closed forms,
+invariants (decryption invariance of key switching, ModDown(P x) = x, the rotate-and-sum slot
+total) and the exact result x.W + b of every product. What the paper does not fix -- the exact
+ciphertext bits, which follow from the readings above (the generator, the slot map, the
+key-switching conventions) -- is "parity unpinned" by the paper: those bits are pinned only by
+the readings, which the CUDA library implements independently.
 """
 from __future__ import annotations
 
