@@ -219,27 +219,34 @@ __global__ void k_enc_sample(const u64 *__restrict__ cdt, int cdt_len, u64 seed,
     dst[2 * N + k] = (int8_t)gauss_of(w[4], w[5], w[6], cdt, cdt_len);
 }
 
-// Limb unit (c, comp, l): comp 0 -> pk0 u + e1 + Delta m, comp 1 -> pk1 u + e2 (limb l).
+// Limb unit (c, l): both components of ciphertext c on limb l from one transform of u:
+// comp 0 -> pk0 u + e1 + Delta m, comp 1 -> pk1 u + e2. The product pk1 u waits in comp 1's
+// output limb (evaluation form) while comp 0 is inverted; the second inverse reads it in its
+// first pass and overwrites it only in its last.
 template <int LOGN>
 LIMB_KERNEL(LOGN) k_enc_main(const ModTab *__restrict__ mods, int L, const shoup_t *__restrict__ pk,
                              const int8_t *__restrict__ rnd, const u64 *__restrict__ pt, u64 *ct) {
     extern __shared__ u64 sm[];
     LIMB_INDEX(LOGN);
-    const int l = (int)(unit % L), comp = (int)((unit / L) % 2);
-    const size_t c = unit / (2 * L);
+    const int l = (int)(unit % L);
+    const size_t c = unit / L;
     const ModTab T = mods[l];
-    const int8_t *u = rnd + c * 3 * N, *e = rnd + c * 3 * N + (size_t)(1 + comp) * N;
-    const shoup_t *key = pk + ((size_t)comp * L + l) * N;
+    const int8_t *u = rnd + c * 3 * N, *e1 = u + N, *e2 = u + 2 * (size_t)N;
+    const shoup_t *k0 = pk + (size_t)l * N, *k1 = pk + ((size_t)L + l) * N;
     const u64 *m = pt + c * N;
-    u64 *out = ct + ((c * 2 + comp) * L + l) * (size_t)N;
-    limb_forward<LOGN, true>(sm, T, h, [&](int p) { return lift_small(u[p], T.q); },
-                       [&](int p, u64 v) { sm[padi(p & (M - 1))] = mul_shoup(v, key[p], T.q); });
+    u64 *out0 = ct + ((c * 2 + 0) * L + l) * (size_t)N, *out1 = ct + ((c * 2 + 1) * L + l) * (size_t)N;
+    limb_forward<LOGN, true>(sm, T, h, [&](int p) { return lift_small(u[p], T.q); }, [&](int p, u64 v) {
+        sm[padi(p & (M - 1))] = mul_shoup(v, k0[p], T.q);
+        out1[p] = mul_shoup(v, k1[p], T.q);
+    });
     __syncthreads();
     limb_inverse<LOGN>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) {
-        u64 r = add_mod(v, lift_small(e[p], T.q), T.q);
-        if (comp == 0) r = add_mod(r, mul_barrett(T.delta, m[p] % T.q, T.q, T.mu, T.bits), T.q);
-        out[p] = r;
+        const u64 r = add_mod(v, lift_small(e1[p], T.q), T.q);
+        out0[p] = add_mod(r, mul_barrett(T.delta, m[p] % T.q, T.q, T.mu, T.bits), T.q);
     });
+    __syncthreads();
+    limb_inverse<LOGN>(sm, T, h, [&](int p) { return out1[p]; },
+                       [&](int p, u64 v) { out1[p] = add_mod(v, lift_small(e2[p], T.q), T.q); });
 }
 
 // ------------------------------------------------------------------ decryption
@@ -457,7 +464,7 @@ int launch_encrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *pt, size_t co
     const size_t total = count * c->N;
     if (!total) return BFV_OK;
     k_enc_sample<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(c->dcdt, c->cdt_len, seed, obj0, c->N, total, rnd);
-#define L_(LG) launch_limbs<LG>(k_enc_main<LG>, count * 2 * c->L, st, 0, c->dmods, c->L, (const shoup_t *)k->pk_eval, \
+#define L_(LG) launch_limbs<LG>(k_enc_main<LG>, count * c->L, st, 0, c->dmods, c->L, (const shoup_t *)k->pk_eval, \
                                 (const int8_t *)rnd, pt, ct)
     DISPATCH_LOGN(c, L_)
 #undef L_
