@@ -76,6 +76,8 @@ def parse_args(argv=None):
                    help="serving case: Poisson request traces through the continuous-batching loop")
     p.add_argument("--rates", type=str, default="1,2,5,20,100,500")
     p.add_argument("--serve-cap", type=int, default=1024, help="predictions offered per rate")
+    p.add_argument("--serve-bank", action="store_true",
+                   help="serving with the bank of 11 binary one-vs-rest models: every arrival queries all 11")
     return p.parse_args(argv)
 
 
@@ -876,8 +878,89 @@ def run_serve(args):
     return 0
 
 
+def run_serve_bank(args):
+    """Serving the paper's bank of one-vs-rest binary models (Section 4.2.1): 11 models with 2
+    classes each and their own feature counts (seeded draws from {5k, 10k, 20k, 40k}) at
+    N = 16384. Every Poisson arrival (70% one individual, 30% 16..512) queries all 11 models;
+    the server fuses requests across models (priority class for requests of <= 16 individuals)
+    against the same requests served one at a time. Latency of an arrival = until its last
+    model's scores are done."""
+    import torch
+    import paper_2204_05496_gb300 as bfv
+    from paper_2204_05496_gb300 import serve
+    bfv.build()
+    torch.cuda.set_device(0)
+    w = synth.WORKLOADS[WORKLOAD]
+    X, _, _ = synth.workload_inputs(w)
+    N, L = w.params.N, w.params.L
+    ctx = bfv.Context.from_shape(w.params)
+    keys = ctx.keygen(w.seed_keys)
+    rng = np.random.default_rng([503, 1])
+    fs = [int(v) for v in rng.choice([5000, 10000, 20000, 40000], size=11)]
+    bank = [ctx.model_prepare(synth.weights(503 + m, f, 2), synth.bias(503 + m, 2)) for m, f in enumerate(fs)]
+    pt = ctx.encode_features(torch.from_numpy(X).cuda())
+    pool = ctx.encrypt(keys, pt.reshape(-1, N), seed=w.seed_enc).reshape(len(X), -1, 2, L, N)
+    del pt
+    trace_of = {}
+
+    def inputs(k, n):
+        i0, m = trace_of[k]
+        return pool[i0:i0 + n, :bank[m].K]      # model m reads the first ceil(f_m / N) plaintexts
+
+    ctx.lr_scores_packed_models(keys, bank[:2], [pool[:1, :bank[0].K], pool[1:17, :bank[1].K]])
+    torch.cuda.synchronize()
+    results = {}
+    for rate in [float(r) for r in args.rates.split(",")]:
+        trace, offered = [], 0
+        for a, (t, n) in enumerate(synth.poisson_arrivals(502, rate, 100000)):
+            if offered >= args.serve_cap:
+                break
+            i0 = (a * 131) % (len(X) - n + 1)
+            for m in range(11):
+                trace_of[len(trace)] = (i0, m)
+                trace.append((t, n, m))
+            offered += n
+        out = {}
+        for mode, kw in (("batched_priority", dict(small_pairs=16 * 2)), ("batched", {})):
+            srv = serve.Server(ctx, keys, bank, hbm_budget_bytes=64 << 30, n_streams=2, **kw)
+            done = srv.run(trace, inputs)
+            out[mode] = bank_report(done, srv.nbatches)
+            torch.cuda.empty_cache()
+        out["one_by_one"] = bank_report(serve.run_unbatched(ctx, keys, bank, trace, inputs), None)
+        results[str(rate)] = out
+        print(json.dumps({"rate": rate, **out}), flush=True)
+    print(json.dumps({"case": "serve-bank", "models": 11, "features": fs,
+                      "workload": "11 binary models, every arrival queries all (70% x1, 30% x16..512)",
+                      "results": results}), flush=True)
+    return 0
+
+
+def bank_report(done, launches):
+    """Per-arrival latency (until the last of its 11 model requests is done) and throughput."""
+    by_arrival = {}
+    for r in done:
+        key = (r.t_arrival, r.rid // 11)
+        lat = r.t_done - r.t_arrival
+        prev = by_arrival.get(key)
+        by_arrival[key] = (max(prev[0], lat) if prev else lat, r.nX)
+    lat = np.array([v[0] for v in by_arrival.values()])
+    single = np.array([v[0] for v in by_arrival.values() if v[1] == 1])
+    span = max(r.t_done for r in done) - min(r.t_arrival for r in done)
+    preds = sum(v[1] for v in by_arrival.values())
+    out = {"arrivals": len(by_arrival), "predictions_x11_models": preds,
+           "p50_ms": float(np.percentile(lat, 50) * 1e3), "p99_ms": float(np.percentile(lat, 99) * 1e3),
+           "single_p50_ms": float(np.percentile(single, 50) * 1e3) if len(single) else None,
+           "single_p99_ms": float(np.percentile(single, 99) * 1e3) if len(single) else None,
+           "patients_per_s": preds / span if span > 0 else 0.0}
+    if launches is not None:
+        out["launches"] = launches
+    return out
+
+
 def main(argv=None):
     args = parse_args(argv)
+    if args.serve_bank:
+        return run_serve_bank(args)
     if args.serve:
         return run_serve(args)
     if args.impl == "reference":

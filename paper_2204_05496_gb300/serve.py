@@ -204,23 +204,27 @@ def latency_report(reqs, nY: int) -> dict:
 
 
 def run_unbatched(ctx, keys, model, arrivals, make_inputs, pair_chunk: int = 0):
-    """The same trace served one request at a time (FIFO, one stream, no fusion)."""
+    """The same trace served one request at a time (FIFO, one stream, no fusion). `model` may be
+    a list indexed by the arrivals' third field, as for Server.run."""
     import torch
+    models = list(model) if isinstance(model, (list, tuple)) else [model]
     torch.cuda.synchronize()
     t0 = torch.cuda.Event(enable_timing=True)
     t0.record()
     torch.cuda.synchronize()
     h0 = time.perf_counter()
     done = []
-    for k, (ta, nX) in enumerate(arrivals):
+    for k, a in enumerate(arrivals):
+        ta, nX = a[0], a[1]
+        m = a[2] if len(a) > 2 else 0
         while time.perf_counter() - h0 < ta:
             time.sleep(0.0005)
         X = make_inputs(k, nX)
-        ctx.lr_scores_packed(keys, model, X, pair_chunk=pair_chunk)
+        ctx.lr_scores_packed(keys, models[m], X, pair_chunk=pair_chunk)
         ev = torch.cuda.Event(enable_timing=True)
         ev.record()
         ev.synchronize()
-        r = Request(k, X, ta)
+        r = Request(k, X, ta, m)
         r.t_done = t0.elapsed_time(ev) / 1e3
         done.append(r)
     return done
