@@ -164,6 +164,65 @@ def _ptr(t):
     return ctypes.c_void_p(t.data_ptr()) if t is not None else None
 
 
+# The C calls trust the sizes they are given and read or write exactly the bytes those imply, so
+# the binding checks every caller tensor against them before a pointer is passed on.
+def _dev_in(t, name, itemsize, numel=None, block=None):
+    """A device tensor the library reads: element size and count checked, returned contiguous."""
+    if not getattr(t, "is_cuda", False):
+        raise ValueError(f"{name}: a CUDA tensor is expected")
+    if t.element_size() != itemsize:
+        raise ValueError(f"{name}: {itemsize}-byte elements expected, got {t.dtype}")
+    if numel is not None and t.numel() != numel:
+        raise ValueError(f"{name}: {numel} elements expected, got {t.numel()}")
+    if block is not None and t.numel() % block:
+        raise ValueError(f"{name}: a whole number of {block}-element blocks expected, got {t.numel()}")
+    return t.contiguous()
+
+
+def _dev_out(t, name, itemsize, numel):
+    """A caller-supplied output: written in place, so contiguous and exactly the written size."""
+    if not getattr(t, "is_cuda", False) or not t.is_contiguous():
+        raise ValueError(f"{name}: a contiguous CUDA tensor is expected")
+    if t.element_size() != itemsize or t.numel() != numel:
+        raise ValueError(f"{name}: {numel} elements of {itemsize} bytes expected, got {t.numel()} of "
+                         f"{t.element_size()}")
+    return t
+
+
+def _host_buf(a, name, itemsize, shape, out=False):
+    """A host array (numpy or CPU torch tensor) passed by address: dtype size and shape checked;
+    inputs are made contiguous, outputs must already be."""
+    if hasattr(a, "is_cuda"):
+        if a.is_cuda:
+            raise ValueError(f"{name}: a host buffer is expected")
+        size, shp, contig = a.element_size(), tuple(a.shape), a.is_contiguous()
+    else:
+        a = np.asarray(a) if not out else a
+        size, shp, contig = a.itemsize, a.shape, a.flags.c_contiguous
+    if size != itemsize or shp != tuple(shape):
+        raise ValueError(f"{name}: shape {tuple(shape)} of {itemsize}-byte elements expected, got {shp} of {size}")
+    if not contig:
+        if out:
+            raise ValueError(f"{name}: a contiguous buffer is expected")
+        a = a.contiguous() if hasattr(a, "is_cuda") else np.ascontiguousarray(a)
+    return a
+
+
+def _addr(a):
+    return a.data_ptr() if hasattr(a, "data_ptr") else a.ctypes.data
+
+
+def _workspace(ws, need, device):
+    """The caller's workspace if it is a large enough device buffer, else a fresh one; returns
+    (tensor, size in bytes)."""
+    import torch
+    if ws is None or ws.numel() * ws.element_size() < need:
+        ws = torch.empty(max(need, 1), dtype=torch.uint8, device=device)
+    elif not ws.is_cuda or not ws.is_contiguous():
+        raise ValueError("ws: a contiguous CUDA tensor is expected")
+    return ws, ws.numel() * ws.element_size()
+
+
 def _stream(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
@@ -262,29 +321,33 @@ class Context:
 
     # -- client
     def encode(self, slots, stream=None):
+        slots = _dev_in(slots, "slots", 8, block=self.N)
         count = slots.numel() // self.N
         pt = self._empty_u64(*slots.shape)
-        _call("bfv_encode", self.handle, _ptr(slots.contiguous()), count, _ptr(pt), _stream(stream))
+        _call("bfv_encode", self.handle, _ptr(slots), count, _ptr(pt), _stream(stream))
         return pt
 
     def decode(self, pt, stream=None):
         import torch
+        pt = _dev_in(pt, "pt", 8, block=self.N)
         count = pt.numel() // self.N
         out = torch.empty(pt.shape, dtype=torch.int64, device=pt.device)
-        _call("bfv_decode", self.handle, _ptr(pt.contiguous()), count, _ptr(out), _stream(stream))
+        _call("bfv_decode", self.handle, _ptr(pt), count, _ptr(out), _stream(stream))
         return out
 
     def encode_features(self, X, stream=None):
         nX, f = X.shape
+        X = _dev_in(X, "X", 1)
         K = -(-f // self.N)
         pt = self._empty_u64(nX, K, self.N)
-        _call("bfv_encode_features", self.handle, _ptr(X.contiguous()), nX, f, _ptr(pt), _stream(stream))
+        _call("bfv_encode_features", self.handle, _ptr(X), nX, f, _ptr(pt), _stream(stream))
         return pt
 
     def encode_feature_columns(self, X, stream=None):
         nX, f = X.shape
+        X = _dev_in(X, "X", 1)
         pt = self._empty_u64(f, self.N)
-        _call("bfv_encode_feature_columns", self.handle, _ptr(X.contiguous()), nX, f, _ptr(pt), _stream(stream))
+        _call("bfv_encode_feature_columns", self.handle, _ptr(X), nX, f, _ptr(pt), _stream(stream))
         return pt
 
     def encrypt_workspace(self, count: int) -> int:
@@ -293,14 +356,13 @@ class Context:
         return n.value
 
     def encrypt(self, keys: Keys, pt, seed: int, obj0: int = 0, out=None, ws=None, stream=None):
-        import torch
+        pt = _dev_in(pt, "pt", 8, block=self.N)
         count = pt.numel() // self.N
-        ct = out if out is not None else self._empty_u64(*pt.shape[:-1], 2, self.L, self.N)
-        need = self.encrypt_workspace(count)
-        if ws is None or ws.numel() < need:
-            ws = torch.empty(max(need, 1), dtype=torch.uint8, device=pt.device)
-        _call("bfv_encrypt", self.handle, keys.handle, _ptr(pt.contiguous()), count, seed, obj0, _ptr(ct), _ptr(ws),
-              ws.numel(), _stream(stream))
+        ct = (_dev_out(out, "out", 8, count * 2 * self.L * self.N) if out is not None
+              else self._empty_u64(*pt.shape[:-1], 2, self.L, self.N))
+        ws, nb = _workspace(ws, self.encrypt_workspace(count), pt.device)
+        _call("bfv_encrypt", self.handle, keys.handle, _ptr(pt), count, seed, obj0, _ptr(ct), _ptr(ws), nb,
+              _stream(stream))
         return ct
 
     def decrypt_workspace(self, count: int) -> int:
@@ -309,14 +371,12 @@ class Context:
         return n.value
 
     def decrypt(self, keys: Keys, ct, out=None, ws=None, stream=None):
-        import torch
+        ct = _dev_in(ct, "ct", 8, block=2 * self.L * self.N)
         count = ct.numel() // (2 * self.L * self.N)
-        pt = out if out is not None else self._empty_u64(*ct.shape[:-3], self.N)
-        need = self.decrypt_workspace(count)
-        if ws is None or ws.numel() < need:
-            ws = torch.empty(max(need, 1), dtype=torch.uint8, device=ct.device)
-        _call("bfv_decrypt", self.handle, keys.handle, _ptr(ct.contiguous()), count, _ptr(pt), _ptr(ws), ws.numel(),
-              _stream(stream))
+        pt = (_dev_out(out, "out", 8, count * self.N) if out is not None
+              else self._empty_u64(*ct.shape[:-3], self.N))
+        ws, nb = _workspace(ws, self.decrypt_workspace(count), ct.device)
+        _call("bfv_decrypt", self.handle, keys.handle, _ptr(ct), count, _ptr(pt), _ptr(ws), nb, _stream(stream))
         return pt
 
     # -- server
@@ -334,16 +394,22 @@ class Context:
         _call("bfv_lr_scores_packed_workspace", self.handle, model.handle, nX, pair_chunk, ctypes.byref(n))
         return n.value
 
-    def lr_scores_packed(self, keys: Keys, model: Model, X_ct, out=None, ws=None, pair_chunk: int = 0, stream=None):
-        import torch
+    def _packed_args(self, model: Model, X_ct, out, name="X_ct"):
+        """Input ciphertexts uint64[nX][K][2][L][N] and the output buffer uint64[nout][2][L][N]."""
         nX = X_ct.shape[0]
+        ctw = 2 * self.L * self.N
+        X_ct = _dev_in(X_ct, name, 8, numel=nX * model.K * ctw)
         nout = -(-nX * model.nY // self.N)
-        Y = out if out is not None else self._empty_u64(nout, 2, self.L, self.N)
-        need = self.packed_workspace(model, nX, pair_chunk)
-        if ws is None or ws.numel() < need:
-            ws = torch.empty(need, dtype=torch.uint8, device=X_ct.device)
-        _call("bfv_lr_scores_packed", self.handle, keys.handle, model.handle, _ptr(X_ct.contiguous()), nX, _ptr(Y),
-              _ptr(ws), ws.numel(), pair_chunk, _stream(stream))
+        Y = _dev_out(out, "out", 8, nout * ctw) if out is not None else self._empty_u64(nout, 2, self.L, self.N)
+        return nX, X_ct, Y
+
+    def lr_scores_packed(self, keys: Keys, model: Model, X_ct, out=None, ws=None, pair_chunk: int = 0, stream=None):
+        nX, X_ct, Y = self._packed_args(model, X_ct, out)
+        if nX == 0:
+            return Y
+        ws, nb = _workspace(ws, self.packed_workspace(model, nX, pair_chunk), X_ct.device)
+        _call("bfv_lr_scores_packed", self.handle, keys.handle, model.handle, _ptr(X_ct), nX, _ptr(Y), _ptr(ws), nb,
+              pair_chunk, _stream(stream))
         return Y
 
     def standard_workspace(self, model: Model) -> int:
@@ -362,20 +428,28 @@ class Context:
                                stream=None):
         """Several requests (a list of input-ciphertext tensors) in one fused packed product; returns
         one output tensor per request, each identical to its single-request result."""
-        import torch
-        nXs = [x.shape[0] for x in X_cts]
-        if outs is None:
-            outs = [self._empty_u64(-(-n * model.nY // self.N), 2, self.L, self.N) for n in nXs]
-        need = self.multi_workspace(model, nXs, pair_chunk)
-        if ws is None or ws.numel() < need:
-            ws = torch.empty(need, dtype=torch.uint8, device=f"cuda:{self.device}")
-        xs = [x.contiguous() for x in X_cts]
+        xs, outs = self._models_args([model] * len(X_cts), X_cts, outs)
+        nXs = [x.shape[0] for x in xs]
+        ws, nb = _workspace(ws, self.multi_workspace(model, nXs, pair_chunk), f"cuda:{self.device}")
         xp = (ctypes.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
         yp = (ctypes.c_void_p * len(outs))(*[y.data_ptr() for y in outs])
         na = (ctypes.c_size_t * len(nXs))(*nXs)
         _call("bfv_lr_scores_packed_multi", self.handle, keys.handle, model.handle, len(xs), ctypes.cast(xp, _vp),
-              ctypes.cast(na, _vp), ctypes.cast(yp, _vp), _ptr(ws), ws.numel(), pair_chunk, _stream(stream))
+              ctypes.cast(na, _vp), ctypes.cast(yp, _vp), _ptr(ws), nb, pair_chunk, _stream(stream))
         return outs
+
+    def _models_args(self, models, X_cts, outs):
+        """Per request: its input ciphertexts and its output buffer, checked like lr_scores_packed's."""
+        if len(models) != len(X_cts) or (outs is not None and len(outs) != len(X_cts)):
+            raise ValueError("one model and one output per request expected")
+        if not X_cts:
+            raise ValueError("at least one request expected")
+        xs, ys = [], []
+        for r, (m, x) in enumerate(zip(models, X_cts)):
+            _, x, y = self._packed_args(m, x, outs[r] if outs is not None else None, name=f"X_cts[{r}]")
+            xs.append(x)
+            ys.append(y)
+        return xs, ys
 
     def models_workspace(self, models, nXs, pair_chunk: int = 0) -> int:
         mp = (ctypes.c_void_p * len(models))(*[m.handle for m in models])
@@ -390,56 +464,46 @@ class Context:
         """Requests of different models (request r: inputs X_cts[r], model models[r]) in one fused
         packed product; returns one output tensor per request, each identical to its
         single-request result."""
-        import torch
-        nXs = [x.shape[0] for x in X_cts]
-        if outs is None:
-            outs = [self._empty_u64(-(-n * m.nY // self.N), 2, self.L, self.N) for n, m in zip(nXs, models)]
-        need = self.models_workspace(models, nXs, pair_chunk)
-        if ws is None or ws.numel() < need:
-            ws = torch.empty(need, dtype=torch.uint8, device=f"cuda:{self.device}")
-        xs = [x.contiguous() for x in X_cts]
+        xs, outs = self._models_args(models, X_cts, outs)
+        nXs = [x.shape[0] for x in xs]
+        ws, nb = _workspace(ws, self.models_workspace(models, nXs, pair_chunk), f"cuda:{self.device}")
         mp = (ctypes.c_void_p * len(models))(*[m.handle for m in models])
         xp = (ctypes.c_void_p * len(xs))(*[x.data_ptr() for x in xs])
         yp = (ctypes.c_void_p * len(outs))(*[y.data_ptr() for y in outs])
         na = (ctypes.c_size_t * len(nXs))(*nXs)
         _call("bfv_lr_scores_packed_models", self.handle, keys.handle, len(xs), ctypes.cast(mp, _vp),
-              ctypes.cast(xp, _vp), ctypes.cast(na, _vp), ctypes.cast(yp, _vp), _ptr(ws), ws.numel(), pair_chunk,
+              ctypes.cast(xp, _vp), ctypes.cast(na, _vp), ctypes.cast(yp, _vp), _ptr(ws), nb, pair_chunk,
               _stream(stream))
         return outs
 
     def lr_scores_packed_graph(self, keys: Keys, model: Model, X_ct, out=None, ws=None, pair_chunk: int = 0,
                                stream=None):
         """lr_scores_packed replayed from a cached CUDA graph (one host call per product)."""
-        import torch
-        nX = X_ct.shape[0]
-        nout = -(-nX * model.nY // self.N)
-        Y = out if out is not None else self._empty_u64(nout, 2, self.L, self.N)
-        need = self.packed_workspace(model, nX, pair_chunk)
-        if ws is None or ws.numel() < need:
-            ws = torch.empty(need, dtype=torch.uint8, device=X_ct.device)
-        _call("bfv_lr_scores_packed_graph", self.handle, keys.handle, model.handle, _ptr(X_ct.contiguous()), nX,
-              _ptr(Y), _ptr(ws), ws.numel(), pair_chunk, _stream(stream))
+        nX, X_ct, Y = self._packed_args(model, X_ct, out)
+        if nX == 0:
+            return Y
+        ws, nb = _workspace(ws, self.packed_workspace(model, nX, pair_chunk), X_ct.device)
+        _call("bfv_lr_scores_packed_graph", self.handle, keys.handle, model.handle, _ptr(X_ct), nX, _ptr(Y),
+              _ptr(ws), nb, pair_chunk, _stream(stream))
         return Y
 
     def autotune_packed(self, keys: Keys, model: Model, X_ct, ws, out=None, stream=None):
         """Times pair-chunk sizes that fit in `ws` and makes the fastest the default for this
         number of pairs. Returns (chunk, ms)."""
-        nX = X_ct.shape[0]
-        nout = -(-nX * model.nY // self.N)
-        Y = out if out is not None else self._empty_u64(nout, 2, self.L, self.N)
+        nX, X_ct, Y = self._packed_args(model, X_ct, out)
+        ws = _dev_in(ws, "ws", ws.element_size())
         ch, ms = _sz(), ctypes.c_double()
-        _call("bfv_autotune_packed", self.handle, keys.handle, model.handle, _ptr(X_ct.contiguous()), nX, _ptr(Y),
-              _ptr(ws), ws.numel(), _stream(stream), ctypes.byref(ch), ctypes.byref(ms))
+        _call("bfv_autotune_packed", self.handle, keys.handle, model.handle, _ptr(X_ct), nX, _ptr(Y), _ptr(ws),
+              ws.numel() * ws.element_size(), _stream(stream), ctypes.byref(ch), ctypes.byref(ms))
         return ch.value, ms.value
 
     def lr_scores_standard(self, model: Model, X_ct, nX: int, out=None, ws=None, stream=None):
-        import torch
-        Y = out if out is not None else self._empty_u64(model.nY, 2, self.L, self.N)
-        need = self.standard_workspace(model)
-        if ws is None or ws.numel() < need:
-            ws = torch.empty(max(need, 1), dtype=torch.uint8, device=X_ct.device)
-        _call("bfv_lr_scores_standard", self.handle, model.handle, _ptr(X_ct.contiguous()), nX, _ptr(Y), _ptr(ws),
-              ws.numel(), _stream(stream))
+        ctw = 2 * self.L * self.N
+        X_ct = _dev_in(X_ct, "X_ct", 8, numel=model.f * ctw)
+        Y = _dev_out(out, "out", 8, model.nY * ctw) if out is not None else self._empty_u64(model.nY, 2, self.L, self.N)
+        ws, nb = _workspace(ws, self.standard_workspace(model), X_ct.device)
+        _call("bfv_lr_scores_standard", self.handle, model.handle, _ptr(X_ct), nX, _ptr(Y), _ptr(ws), nb,
+              _stream(stream))
         return Y
 
     def check_error(self) -> int:
@@ -460,29 +524,30 @@ class Context:
         """Whole protocol on device buffers: X uint8[nX][f] -> scores int64[nX][nY] (mod t)."""
         import torch
         nX = X.shape[0]
-        scores = out if out is not None else torch.empty((nX, model.nY), dtype=torch.int64, device=X.device)
-        need = self.predict_workspace(model, nX, pair_chunk)
-        if ws is None or ws.numel() < need:
-            ws = torch.empty(need, dtype=torch.uint8, device=X.device)
-        _call("bfv_lr_predict_packed", self.handle, keys.handle, model.handle, _ptr(X.contiguous()), nX, seed,
-              _ptr(scores), _ptr(ws), ws.numel(), pair_chunk, _stream(stream))
+        X = _dev_in(X, "X", 1, numel=nX * model.f)
+        scores = (_dev_out(out, "out", 8, nX * model.nY) if out is not None
+                  else torch.empty((nX, model.nY), dtype=torch.int64, device=X.device))
+        if nX == 0:
+            return scores
+        ws, nb = _workspace(ws, self.predict_workspace(model, nX, pair_chunk), X.device)
+        _call("bfv_lr_predict_packed", self.handle, keys.handle, model.handle, _ptr(X), nX, seed, _ptr(scores),
+              _ptr(ws), nb, pair_chunk, _stream(stream))
         return scores
 
     def predict_packed_host(self, keys: Keys, model: Model, X_host, seed: int, out=None, ws=None,
                             pair_chunk: int = 0, stream=None):
         """Whole protocol with HOST buffers (the copies happen inside the C call): X_host uint8
         [nX][f] (numpy or pinned torch) -> scores int64[nX][nY] on the host."""
-        import torch
         nX = X_host.shape[0]
+        X_host = _host_buf(X_host, "X_host", 1, (nX, model.f))
         if out is None:
             out = np.empty((nX, model.nY), dtype=np.int64)
-        xp = X_host.data_ptr() if hasattr(X_host, "data_ptr") else X_host.ctypes.data
-        op = out.data_ptr() if hasattr(out, "data_ptr") else out.ctypes.data
-        need = self.predict_workspace(model, nX, pair_chunk)
-        if ws is None or ws.numel() < need:
-            ws = torch.empty(need, dtype=torch.uint8, device=f"cuda:{self.device}")
-        _call("bfv_lr_predict_packed_host", self.handle, keys.handle, model.handle, ctypes.c_void_p(xp), nX, seed,
-              ctypes.c_void_p(op), _ptr(ws), ws.numel(), pair_chunk, _stream(stream))
+        out = _host_buf(out, "out", 8, (nX, model.nY), out=True)
+        if nX == 0:
+            return out
+        ws, nb = _workspace(ws, self.predict_workspace(model, nX, pair_chunk), f"cuda:{self.device}")
+        _call("bfv_lr_predict_packed_host", self.handle, keys.handle, model.handle, ctypes.c_void_p(_addr(X_host)), nX,
+              seed, ctypes.c_void_p(_addr(out)), _ptr(ws), nb, pair_chunk, _stream(stream))
         return out
 
     def profile(self, enable: bool):
@@ -498,6 +563,11 @@ class Context:
         return out
 
     def packed_pair_from_workspace(self, model: Model, nX: int, pair_chunk: int, ws, g: int, stream=None):
+        if not 0 <= g < nX * model.nY:
+            raise ValueError(f"pair {g} outside 0..{nX * model.nY - 1}")
+        ws = _dev_in(ws, "ws", ws.element_size())
+        if ws.numel() * ws.element_size() < self.packed_workspace(model, nX, pair_chunk):
+            raise ValueError("ws is smaller than this product's workspace")
         out = self._empty_u64(2, self.L, self.N)
         _call("bfv_lr_packed_pair_from_workspace", self.handle, model.handle, nX, pair_chunk, _ptr(ws), g, _ptr(out),
               _stream(stream))
@@ -514,10 +584,10 @@ def crt_combine(r0, t0: int, r1, t1: int, out=None, stream=None):
     (mod t1) of equal shape -> the integers x = r0 mod t0, x = r1 mod t1, centred in
     (-t0 t1 / 2, t0 t1 / 2]."""
     import torch
-    r0, r1 = r0.contiguous(), r1.contiguous()
     if r0.shape != r1.shape or r0.dtype != torch.int64 or r1.dtype != torch.int64:
         raise ValueError("r0 and r1 must be int64 tensors of the same shape")
-    out = torch.empty_like(r0) if out is None else out
+    r0, r1 = _dev_in(r0, "r0", 8), _dev_in(r1, "r1", 8)
+    out = torch.empty_like(r0) if out is None else _dev_out(out, "out", 8, r0.numel())
     _call("bfv_crt_combine", _ptr(r0), t0, _ptr(r1), t1, r0.numel(), _ptr(out), _stream(stream))
     return out
 

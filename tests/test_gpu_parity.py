@@ -285,8 +285,64 @@ def test_invalid_arguments_are_rejected(tiny):
         bfv._call("bfv_lr_scores_packed", ctx.handle, keys.handle, model.handle, bfv._ptr(X_ct), 1,
                   bfv._ptr(X_ct), bfv._ptr(tiny_ws), 16, 0, 0)
     assert e.value.code == bfv.BFV_ERR_OVER_BUDGET
+    cols = torch.zeros((10, 2, P.L, P.N), dtype=torch.int64, device="cuda")
     with pytest.raises(bfv.BfvError):
-        ctx.lr_scores_standard(model, X_ct[0, 0], P.N + 1)   # more individuals than slots
+        ctx.lr_scores_standard(model, cols, P.N + 1)         # more individuals than slots
+
+
+def test_binding_checks_buffers_before_the_call(tiny):
+    """The C calls read and write exactly the bytes their sizes imply; the binding refuses a
+    caller tensor of the wrong shape, element size or memory before any pointer is passed on."""
+    ctx, keys, P, _ = tiny
+    model = ctx.model_prepare(np.ones((10, 2), dtype=np.int64), np.zeros(2, dtype=np.int64))
+    X = torch.zeros((3, 10), dtype=torch.uint8, device="cuda")
+    with pytest.raises(ValueError):
+        ctx.predict_packed(keys, model, X[:, :9], seed=1)                       # one feature short
+    with pytest.raises(ValueError):
+        ctx.predict_packed(keys, model, X.to(torch.int64), seed=1)              # 8-byte features
+    with pytest.raises(ValueError):
+        ctx.predict_packed(keys, model, X, seed=1, out=torch.empty((3, 1), dtype=torch.int64, device="cuda"))
+    with pytest.raises(ValueError):
+        ctx.predict_packed_host(keys, model, np.zeros((3, 9), dtype=np.uint8), seed=1)
+    with pytest.raises(ValueError):
+        ctx.predict_packed_host(keys, model, X, seed=1)                         # device memory
+    X_ct = torch.zeros((1, 1, 2, P.L, P.N), dtype=torch.int64, device="cuda")
+    with pytest.raises(ValueError):
+        ctx.lr_scores_packed(keys, model, X_ct[:, :, :, :2])                    # two limbs of three
+    with pytest.raises(ValueError):
+        ctx.lr_scores_packed(keys, model, X_ct, out=torch.empty((2, 2, P.L, P.N), dtype=torch.int64, device="cuda"))
+    with pytest.raises(ValueError):                                             # host workspace
+        ctx.lr_scores_packed(keys, model, X_ct, ws=torch.empty(ctx.packed_workspace(model, 1), dtype=torch.uint8))
+    with pytest.raises(ValueError):
+        ctx.packed_pair_from_workspace(model, 1, 0, torch.empty(16, dtype=torch.uint8, device="cuda"), 0)
+    with pytest.raises(ValueError):
+        ctx.encrypt(keys, torch.zeros(P.N + 1, dtype=torch.int64, device="cuda"), seed=1)
+    with pytest.raises(ValueError):
+        ctx.decrypt(keys, X_ct[0, 0, :, :2])
+    torch.cuda.synchronize()
+    assert ctx.predict_packed(keys, model, X[:0], seed=1).shape == (0, 2)
+    assert ctx.lr_scores_packed(keys, model, X_ct[:0]).shape[0] == 0
+
+
+def test_predict_packed_whole_protocol_tiny(tiny):
+    """The whole-protocol calls (encode, encrypt, Algorithm 1, decrypt, decode in one C call), on
+    device and on host buffers, over 700 individuals x 5,000 features x 8 classes: 5,600 pairs
+    in two output ciphertexts and two plaintexts per individual. Every score against the closed
+    form, for two encryption seeds and a chunked plan."""
+    ctx, keys, P, _ = tiny
+    rng = np.random.default_rng(97)
+    nX, f, nY = 700, 5000, 8
+    X = (rng.random((nX, f)) < 0.05).astype(np.uint8)
+    W = rng.integers(-127, 128, (f, nY))
+    b = rng.integers(-127, 128, nY)
+    model = ctx.model_prepare(W, b)
+    want = oracle.expected_scores(X, W, b, P.t)
+    assert np.array_equal(ctx.predict_packed(keys, model, dev(X), seed=98).cpu().numpy(), want)
+    assert np.array_equal(ctx.predict_packed_host(keys, model, X, seed=99, pair_chunk=1024), want)
+    pinned = torch.from_numpy(X).pin_memory()
+    out = torch.empty((nX, nY), dtype=torch.int64).pin_memory()
+    ctx.predict_packed_host(keys, model, pinned, seed=100, out=out)
+    assert np.array_equal(out.numpy(), want)
 
 
 # ----------------------------------------------------------------------------- paper scale (N = 16384, L = 7)

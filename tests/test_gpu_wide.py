@@ -88,6 +88,18 @@ def test_wide_single_individual_packed_bit_exact(wide):
     assert np.array_equal(scores, oracle.expected_scores(X, W, b, P.t))
 
 
+def test_wide_whole_protocol(wide):
+    # bfv_lr_predict_packed at N = 32768: three individuals x 40,000 features x 16 classes
+    ctx, keys, P, _ = wide
+    rng = np.random.default_rng(410)
+    X = (rng.random((3, 40000)) < 0.02).astype(np.uint8)
+    W = rng.integers(-127, 128, (40000, 16))
+    b = rng.integers(-127, 128, 16)
+    model = ctx.model_prepare(W, b)
+    got = ctx.predict_packed(keys, model, dev(X), seed=411).cpu().numpy()
+    assert np.array_equal(got, oracle.expected_scores(X, W, b, P.t))
+
+
 def test_wide_binary_model_batch(wide):
     # a binary one-vs-rest model over 300 individuals (600 pairs, ragged chunks of 256):
     # every score against the closed form, one pair of the last chunk bit-exact

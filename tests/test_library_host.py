@@ -72,6 +72,26 @@ def test_setup_without_gpu_fails_loudly(bfv):
         bfv.Context(4096, 3, 36, 65537)
 
 
+def test_binding_refuses_buffers_the_library_would_overrun(bfv):
+    """The binding's buffer checks, on host memory: a host buffer must have the element size and
+    shape the C call reads, an output must already be contiguous, and a device argument must be
+    in device memory."""
+    import numpy as np
+    import torch
+    x = np.zeros((3, 10), dtype=np.uint8)
+    assert bfv._host_buf(x, "X", 1, (3, 10)) is x
+    assert bfv._host_buf(x.T.copy().T, "X", 1, (3, 10)).flags.c_contiguous      # copied contiguous
+    for bad, size, shape in ((x[:, :9], 1, (3, 10)), (x.astype(np.int64), 1, (3, 10)), (x, 8, (3, 10))):
+        with pytest.raises(ValueError):
+            bfv._host_buf(bad, "X", size, shape)
+    with pytest.raises(ValueError):
+        bfv._host_buf(np.zeros((10, 3), dtype=np.int64).T, "out", 8, (3, 10), out=True)
+    assert bfv._host_buf(torch.zeros((3, 10), dtype=torch.int64), "out", 8, (3, 10), out=True).shape == (3, 10)
+    for f in (lambda t: bfv._dev_in(t, "X", 8), lambda t: bfv._dev_out(t, "out", 8, 30)):
+        with pytest.raises(ValueError):
+            f(torch.zeros((3, 10), dtype=torch.int64))                          # host memory
+
+
 def test_product_code_never_touches_the_oracle():
     pkg = os.path.join(ROOT, "paper_2204_05496_gb300")
     for dirpath, _, files in os.walk(pkg):
