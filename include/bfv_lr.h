@@ -138,6 +138,18 @@ int bfv_decrypt_workspace(const bfv_ctx *ctx, size_t count, size_t *bytes);
 int bfv_decrypt(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *ct, size_t count, uint64_t *pt,
                 void *ws, size_t ws_bytes, uintptr_t stream);
 
+/* Invariant noise budget, a diagnostic (Section 4.2.2 sizes the plaintext modulus by the noise
+ * budget a ciphertext must keep). Per ciphertext, z = [t [c0 + c1 s]_Q]_Q centred in
+ * (-Q/2, Q/2] coefficient by coefficient. Since t x = t e - (Q mod t) m mod Q, z / Q is the
+ * invariant noise v of (t/Q)(c0 + c1 s) = m + v mod t. The budget is
+ * max(0, bitlen(Q) - bitlen(max_k |z_k|) - 1) bits. A positive budget gives |v| < 1/2, so
+ * rounding recovers the message. ct: device uint64[count][2][L][N]; budgets: HOST int[count];
+ * ws: device workspace of at least bfv_noise_budget_workspace(count) bytes. Synchronises
+ * `stream`. */
+int bfv_noise_budget_workspace(const bfv_ctx *ctx, size_t count, size_t *bytes);
+int bfv_noise_budget(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *ct, size_t count, int *budgets,
+                     void *ws, size_t ws_bytes, uintptr_t stream);
+
 /* Decryption that allocates nothing (no paper counterpart; a library convenience). Some
  * callers cannot call cudaMalloc: it may synchronise the whole device and can fail under a
  * fixed memory reservation, so latency-critical serving threads, code that runs while a

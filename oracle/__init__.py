@@ -492,6 +492,26 @@ def noise_budget_bits(P: Params, sk, ct) -> float:
     return math.log2(Q) - math.log2(2 * worst)
 
 
+def noise_budget(P: Params, sk, ct) -> list[int]:
+    """Invariant noise budget of each ciphertext in whole bits. With x = [c0 + c1 s]_Q, the
+    integer z = [t x]_Q taken in (-Q/2, Q/2] equals t e - (Q mod t) m for x = Delta m + e, and
+    z / Q is the invariant noise v in (t/Q) x = m + v (mod t); decryption rounds correctly while
+    |v| < 1/2. Budget = max(0, bitlen(Q) - bitlen(max_k |z_k|) - 1); a positive budget means
+    max |z| < 2^(bitlen(Q) - 2) <= Q/2."""
+    xs = decrypt_residues(P, sk, ct)
+    Q, t = P.Q, P.t
+    out = []
+    for c in range(xs.shape[0]):
+        worst = 0
+        for v in _crt(P, xs[c]):
+            z = (t * v) % Q
+            if z > Q // 2:
+                z -= Q
+            worst = max(worst, abs(z))
+        out.append(max(0, Q.bit_length() - worst.bit_length() - 1))
+    return out
+
+
 def keyswitch(P: Params, gk_eval_g, d):
     """KS of d (coefficient form [L][N]) with one Galois element's evaluation-form key."""
     d = _u64(d)

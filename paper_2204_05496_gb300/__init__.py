@@ -106,6 +106,8 @@ SIGNATURES = {
     "bfv_encrypt": [_vp, _vp, _vp, _sz, _u64, ctypes.c_uint32, _vp, _vp, _sz, _up],
     "bfv_decrypt_workspace": [_vp, _sz, ctypes.POINTER(_sz)],
     "bfv_decrypt": [_vp, _vp, _vp, _sz, _vp, _vp, _sz, _up],
+    "bfv_noise_budget_workspace": [_vp, _sz, ctypes.POINTER(_sz)],
+    "bfv_noise_budget": [_vp, _vp, _vp, _sz, _vp, _vp, _sz, _up],
     "bfv_model_prepare": [_vp, _vp, _vp, _sz, _sz, _up, ctypes.POINTER(_vp)],
     "bfv_model_free": [_vp],
     "bfv_lr_scores_packed_workspace": [_vp, _vp, _sz, _sz, ctypes.POINTER(_sz)],
@@ -378,6 +380,21 @@ class Context:
         ws, nb = _workspace(ws, self.decrypt_workspace(count), ct.device)
         _call("bfv_decrypt", self.handle, keys.handle, _ptr(ct), count, _ptr(pt), _ptr(ws), nb, _stream(stream))
         return pt
+
+    def noise_budget(self, keys: Keys, ct, ws=None, stream=None) -> list[int]:
+        """Invariant noise budget in bits of each ciphertext of ct [..][2][L][N] (bfv_noise_budget;
+        synchronises)."""
+        ct = _dev_in(ct, "ct", 8, block=2 * self.L * self.N)
+        count = ct.numel() // (2 * self.L * self.N)
+        if count == 0:
+            return []
+        n = _sz()
+        _call("bfv_noise_budget_workspace", self.handle, count, ctypes.byref(n))
+        ws, nb = _workspace(ws, n.value, ct.device)
+        out = (ctypes.c_int * count)()
+        _call("bfv_noise_budget", self.handle, keys.handle, _ptr(ct), count, ctypes.cast(out, _vp), _ptr(ws), nb,
+              _stream(stream))
+        return list(out)
 
     # -- server
     def model_prepare(self, W, b, stream=None) -> Model:

@@ -42,6 +42,7 @@ struct Profiler {
 struct bfv_ctx {
     int device = 0;
     int N = 0, logN = 0, L = 0, nqp = 0, bits = 0;
+    int qbits = 0;                   // bit length of Q
     u64 t = 0, omega = 0;
     uint32_t sigma_num = 16, sigma_den = 5;
     std::vector<u64> primes;         // L+1 (index L = P)
@@ -171,6 +172,8 @@ int launch_encrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *pt, size_t co
                    u64 *ct, void *ws, cudaStream_t st);
 int launch_decrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *ct, size_t count, u64 *pt, void *ws,
                    cudaStream_t st);
+int launch_noise_bits(const bfv_ctx *c, const bfv_keys *k, const u64 *ct, size_t count, u64 *x, int *bits,
+                      cudaStream_t st);
 int launch_model_weights(const bfv_ctx *c, bfv_model *m, const u64 *w_pt, cudaStream_t st);
 int launch_crt_combine(const int64_t *r0, u64 t0, const int64_t *r1, u64 t1, u64 inv, size_t n, int64_t *out,
                        cudaStream_t st);

@@ -115,6 +115,15 @@ u64 mw_divmod_small(MW &a, u64 d) {  // a <- floor(a / d), returns remainder
     while (a.size() > 1 && a.back() == 0) a.pop_back();
     return (u64)rem;
 }
+int mw_bits(const MW &a) {   // bit length
+    for (size_t n = a.size(); n-- > 0;)
+        if (a[n]) {
+            int b = 0;
+            for (u64 x = a[n]; x; x >>= 1) ++b;
+            return (int)(64 * n) + b;
+        }
+    return 0;
+}
 u64 mw_mod_small(const MW &a, u64 d) {
     u128 rem = 0;
     for (int i = (int)a.size() - 1; i >= 0; --i) rem = ((rem << 64) | a[i]) % d;
@@ -260,6 +269,7 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
     // Q, floor(Q/t), floor(Q/2) as multi-word integers
     MW Q{1};
     for (int l = 0; l < c->L; ++l) mw_mul_small(Q, c->primes[l]);
+    c->qbits = mw_bits(Q);
     MW Qdt = Q;
     mw_divmod_small(Qdt, c->t);
 
@@ -495,6 +505,33 @@ int bfv_decrypt(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *ct, size_t c
     bfv_decrypt_workspace(ctx, count, &need);
     if (ws_bytes < need) return BFV_ERR_OVER_BUDGET;
     return launch_decrypt(ctx, keys, (const u64 *)ct, count, (u64 *)pt, ws, S(stream));
+}
+
+int bfv_noise_budget_workspace(const bfv_ctx *ctx, size_t count, size_t *bytes) {
+    if (!ctx || !bytes) return BFV_ERR_INVALID_ARG;
+    *bytes = align256(count * (size_t)ctx->L * ctx->N * 8) + align256(count * sizeof(int));
+    return BFV_OK;
+}
+
+int bfv_noise_budget(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *ct, size_t count, int *budgets, void *ws,
+                     size_t ws_bytes, uintptr_t stream) {
+    if (!ctx || !keys || keys->ctx != ctx) return BFV_ERR_INVALID_ARG;
+    if (!count) return BFV_OK;
+    if (!ct || !budgets || !ws) return BFV_ERR_INVALID_ARG;
+    size_t need;
+    bfv_noise_budget_workspace(ctx, count, &need);
+    if (ws_bytes < need) return BFV_ERR_OVER_BUDGET;
+    u64 *x = (u64 *)ws;
+    int *bits = (int *)((char *)ws + align256(count * (size_t)ctx->L * ctx->N * 8));
+    cudaStream_t st = S(stream);
+    int rc = launch_noise_bits(ctx, keys, (const u64 *)ct, count, x, bits, st);
+    if (rc) return rc;
+    std::vector<int> hb(count);
+    if (cudaMemcpyAsync(hb.data(), bits, count * sizeof(int), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+        return BFV_ERR_CUDA;
+    for (size_t c = 0; c < count; ++c) budgets[c] = std::max(0, ctx->qbits - hb[c] - 1);
+    return BFV_OK;
 }
 
 int bfv_model_prepare(bfv_ctx *ctx, const int64_t *W, const int64_t *b, size_t f, size_t nY, uintptr_t stream,

@@ -270,26 +270,20 @@ LIMB_KERNEL(LOGN) k_dec_inner(const ModTab *__restrict__ mods, int L, const shou
                        [&](int p, u64 v) { dst[p] = add_mod(v, c0[p], T.q); });
 }
 
-// m = floor((t x + floor(Q/2)) / Q) mod t per coefficient, x = CRT(x_0..x_{L-1}) in [0, Q):
-// Garner mixed-radix digits, Horner to a multi-word integer, binary long division.
-__global__ void k_dec_round(const ModTab *__restrict__ mods, const DecConst *__restrict__ dc, const u64 *__restrict__ x,
-                            int N, size_t total, u64 *pt) {
-    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (idx >= total) return;
-    const size_t c = idx / N;
-    const int k = (int)(idx % N);
+// Residues v_0..v_{L-1} (v_i < q_i, overwritten) -> the integer x in [0, Q) with x = v_i mod q_i
+// as W 64-bit words: Garner's mixed-radix digits, then Horner's rule from the top digit.
+__device__ __forceinline__ void crt_words(const ModTab *__restrict__ mods, const DecConst *__restrict__ dc,
+                                          u64 (&v)[BFV_MAXP], u64 (&w)[BFV_MAXW]) {
     const int L = dc->L, W = dc->W;
-    u64 v[BFV_MAXP];
     for (int i = 0; i < L; ++i) {
         const u64 qi = mods[i].q;
-        u64 a = x[(c * L + i) * (size_t)N + k];
+        u64 a = v[i];
         for (int j = 0; j < i; ++j) {
             a = sub_mod(a, red1(v[j], qi), qi);
             a = red1(mul_shoup(a, dc->inv[j][i], dc->invp[j][i], qi), qi);
         }
         v[i] = a;
     }
-    u64 w[BFV_MAXW];
     for (int i = 0; i < W; ++i) w[i] = 0;
     w[0] = v[L - 1];
     for (int i = L - 2; i >= 0; --i) {            // w = w * q_i + v_i
@@ -302,6 +296,21 @@ __global__ void k_dec_round(const ModTab *__restrict__ mods, const DecConst *__r
             w[n] = s;
         }
     }
+}
+
+// m = floor((t x + floor(Q/2)) / Q) mod t per coefficient, x = CRT(x_0..x_{L-1}) in [0, Q):
+// Garner mixed-radix digits, Horner to a multi-word integer, binary long division.
+__global__ void k_dec_round(const ModTab *__restrict__ mods, const DecConst *__restrict__ dc, const u64 *__restrict__ x,
+                            int N, size_t total, u64 *pt) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const size_t c = idx / N;
+    const int k = (int)(idx % N);
+    const int L = dc->L, W = dc->W;
+    u64 v[BFV_MAXP];
+    for (int i = 0; i < L; ++i) v[i] = x[(c * L + i) * (size_t)N + k];
+    u64 w[BFV_MAXW];
+    crt_words(mods, dc, v, w);
     {                                             // w = w * t + floor(Q/2)
         u64 carry = 0;
         for (int n = 0; n < W; ++n) {
@@ -331,6 +340,49 @@ __global__ void k_dec_round(const ModTab *__restrict__ mods, const DecConst *__r
         }
     }
     pt[idx] = m % dc->t;
+}
+
+// Invariant noise of coefficient k of ciphertext c: z = [t x]_Q centred in (-Q/2, Q/2], x = [c0 +
+// c1 s]_Q from k_dec_inner (t x = t Delta m + t e = t e - (Q mod t) m mod Q, so z / Q is the noise v
+// of (t/Q)(c0 + c1 s) = m + v mod t). bits[c] = max over the ciphertext's coefficients of the bit
+// length of |z| (bits[] zeroed by the caller).
+__global__ void k_noise_bits(const ModTab *__restrict__ mods, const DecConst *__restrict__ dc,
+                             const u64 *__restrict__ x, int N, size_t total, int *bits) {
+    const size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (idx >= total) return;
+    const size_t c = idx / N;
+    const int k = (int)(idx % N);
+    const int L = dc->L, W = dc->W;
+    u64 v[BFV_MAXP];
+    for (int i = 0; i < L; ++i) {                  // [t x]_{q_i}; t < q_i
+        const ModTab &T = mods[i];
+        v[i] = mul_barrett(x[(c * L + i) * (size_t)N + k], dc->t, T.q, T.mu, T.bits);
+    }
+    u64 w[BFV_MAXW];
+    crt_words(mods, dc, v, w);                     // y = [t x]_Q in [0, Q)
+    int cmp = 0;
+    for (int n = W - 1; n >= 0 && cmp == 0; --n) cmp = (w[n] > dc->qhalf[n]) - (w[n] < dc->qhalf[n]);
+    if (cmp > 0) {
+        // y > floor(Q/2): |z| = Q - y = floor(Q/2) - d with d = y - floor(Q/2) - 1 (Q is odd)
+        u64 borrow = 1;
+        for (int n = 0; n < W; ++n) {             // w = y - floor(Q/2) - 1
+            const u64 a = w[n], b = dc->qhalf[n];
+            const u64 d = a - b - borrow;
+            borrow = (a < b) || (a == b && borrow) ? 1 : 0;
+            w[n] = d;
+        }
+        borrow = 0;
+        for (int n = 0; n < W; ++n) {             // w = floor(Q/2) - w
+            const u64 a = dc->qhalf[n], b = w[n];
+            const u64 d = a - b - borrow;
+            borrow = (a < b) || (a == b && borrow) ? 1 : 0;
+            w[n] = d;
+        }
+    }
+    int b = 0;
+    for (int n = W - 1; n >= 0; --n)
+        if (w[n]) { b = 64 * n + 64 - __clzll((long long)w[n]); break; }
+    if (b) atomicMax(bits + c, b);
 }
 
 // ------------------------------------------------------------------ model weights
@@ -481,6 +533,19 @@ int launch_decrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *ct, size_t co
     DISPATCH_LOGN(c, L_)
 #undef L_
     k_dec_round<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(c->dmods, c->ddec, x, c->N, total, pt);
+    count_launch(c, 2);
+    return last_err();
+}
+
+int launch_noise_bits(const bfv_ctx *c, const bfv_keys *k, const u64 *ct, size_t count, u64 *x, int *bits,
+                      cudaStream_t st) {
+    const size_t total = count * c->N;
+    if (!total) return BFV_OK;
+    if (cudaMemsetAsync(bits, 0, count * sizeof(int), st) != cudaSuccess) return BFV_ERR_CUDA;
+#define L_(LG) launch_limbs<LG>(k_dec_inner<LG>, count * c->L, st, 0, c->dmods, c->L, (const shoup_t *)k->sk_eval, ct, x)
+    DISPATCH_LOGN(c, L_)
+#undef L_
+    k_noise_bits<<<(unsigned)((total + 127) / 128), 128, 0, st>>>(c->dmods, c->ddec, x, c->N, total, bits);
     count_launch(c, 2);
     return last_err();
 }

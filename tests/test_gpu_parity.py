@@ -248,6 +248,21 @@ def test_standard_wide_weights_parity(tiny):
     assert np.array_equal(slots[:, :9].T, oracle.expected_scores(X, W, b, P.t))
 
 
+def test_noise_budget_parity_tiny(tiny):
+    """bfv_noise_budget against the oracle: fresh encryptions, the outputs of a packed product
+    (the oracle's own pipeline) and arbitrary residues, whose noise fills the modulus."""
+    ctx, keys, P, okeys = tiny
+    w = synth.WORKLOADS["tiny-16"]
+    X, W, b = synth.workload_inputs(w)
+    oX_ct, _, oY = oracle.packed_pipeline(P, okeys, X, W, b, w.seed_enc)
+    rng = np.random.default_rng(12)
+    junk = np.stack([np.stack([rng.integers(0, q, P.N, dtype=np.uint64) for q in P.q]) for _ in range(2)])[None]
+    cts = np.concatenate([oX_ct.reshape(-1, 2, P.L, P.N)[:5], oY, junk])
+    got = ctx.noise_budget(keys, dev(cts))
+    assert got == oracle.noise_budget(P, okeys.sk, cts)
+    assert got[-1] == 0 and min(got[:-1]) > 0 and got[5] < got[0]
+
+
 def test_stream_stall_reports_timeout_and_context_recovers(tiny):
     # failure injection on the host side: the first pipeline stage waits for 16 bytes that are
     # never sent; the bounded wait runs out, the kernel sets the error word and returns
@@ -364,6 +379,18 @@ def test_paper_keys_match(paper):
     assert np.array_equal(sk.cpu().numpy(), okeys.sk)
     assert np.array_equal(host(pk), okeys.pk)
     assert np.array_equal(host(gk), okeys.gk_coeff)
+
+
+def test_noise_budget_paper_scale(paper):
+    # fresh encryptions at N = 16384, L = 7: the GPU's ciphertexts equal the oracle's, and so
+    # do their budgets
+    ctx, keys, P, okeys = paper
+    m = oracle.encode(P, synth.slots(41, 2, P.N, P.t))
+    ct = ctx.encrypt(keys, dev(m), seed=42)
+    oct_ = oracle.encrypt(P, okeys, m, seed=42)
+    assert np.array_equal(host(ct), oct_)
+    got = ctx.noise_budget(keys, ct)
+    assert got == oracle.noise_budget(P, okeys.sk, oct_) and min(got) > 300
 
 
 def test_single_individual_packed_bit_exact(paper):

@@ -70,6 +70,16 @@ def test_wide_encode_encrypt_decrypt_match(wide):
     assert np.array_equal(host(dec)[:3], oracle.encode(P, v))
 
 
+def test_wide_noise_budget(wide):
+    # L = 15: the noise integer spans 14 64-bit words
+    ctx, keys, P, okeys = wide
+    m = oracle.encode(P, synth.slots(43, 1, P.N, P.t))
+    ct = ctx.encrypt(keys, dev(m), seed=44, obj0=9)
+    oct_ = oracle.encrypt(P, okeys, m, seed=44, obj0=9)
+    assert np.array_equal(host(ct), oct_)
+    assert ctx.noise_budget(keys, ct) == oracle.noise_budget(P, okeys.sk, oct_)
+
+
 def test_wide_single_individual_packed_bit_exact(wide):
     # 40,000 features at N = 32768: K = 2 plaintexts per individual; 16 classes
     ctx, keys, P, okeys = wide

@@ -310,6 +310,46 @@ def test_encrypt_decrypt_roundtrip(tiny, tiny_keys):
     assert oracle.noise_budget_bits(tiny, tiny_keys.sk, ct) > 70
 
 
+def test_noise_budget_closed_form(small):
+    """A ciphertext (Delta m + e, 0) has x = Delta m + e exactly, so t x = t e - (Q mod t) m
+    modulo Q: the noise integer z follows from the chosen e and m without any CRT. The budget
+    is the bit-length formula on max |z|, and every case still decrypts to m."""
+    sk = np.zeros(16, dtype=np.int8)                    # c1 = 0: the secret plays no part
+    rng = np.random.default_rng(19)
+    Q, t = small.Q, small.t
+    delta, r = Q // t, Q % t
+    for e_mag in (0, 1, 1000, 2 ** 40, Q // (4 * t)):
+        m = [int(v) for v in rng.integers(0, t, 16)]
+        e = [int(rng.integers(-2 ** 62, 2 ** 62)) * e_mag // 2 ** 62 for _ in range(16)]
+        e[3] = e_mag                                    # the extreme value occurs
+        ct = np.zeros((1, 2, small.L, 16), dtype=np.uint64)
+        for k in range(16):
+            for l, q in enumerate(small.q):
+                ct[0, 0, l, k] = (delta * m[k] + e[k]) % q
+        z = [t * e[k] - r * m[k] for k in range(16)]
+        assert max(abs(v) for v in z) < Q // 2          # no wrap: z is the centred residue
+        want = max(0, Q.bit_length() - max(abs(v) for v in z).bit_length() - 1)
+        assert oracle.noise_budget(small, sk, ct) == [want]
+        assert [int(v) for v in oracle.decrypt(small, sk, ct)[0]] == m
+    assert oracle.noise_budget(small, sk, np.zeros((1, 2, small.L, 16), dtype=np.uint64)) == [Q.bit_length() - 1]
+
+
+def test_noise_budget_falls_with_each_operation(tiny, tiny_keys):
+    """Fresh encryption, then a ciphertext-plaintext product, then the whole packed product:
+    the budget falls at each step, stays positive while decryption is right, and agrees with
+    the real-valued budget to within one bit."""
+    w = synth.WORKLOADS["tiny-16"]
+    X, W, b = synth.workload_inputs(w)
+    X_ct, _, Y = oracle.packed_pipeline(tiny, tiny_keys, X, W, b, w.seed_enc)
+    x0 = X_ct[0, 0]
+    wpt = oracle.encode(tiny, oracle.pack_weights(tiny, W)[0, 0])
+    prod = oracle.mul_plain(tiny, x0, wpt)
+    b0, b1, b2 = (oracle.noise_budget(tiny, tiny_keys.sk, c[None])[0] for c in (x0, prod, Y[0]))
+    assert b0 > b1 > b2 > 0
+    for c, bud in ((x0, b0), (prod, b1), (Y[0], b2)):
+        assert abs(bud - oracle.noise_budget_bits(tiny, tiny_keys.sk, c[None])) < 1
+
+
 def test_decrypt_rounds_to_nearest(small):
     # a ciphertext (x, 0) decrypts to round(t x / Q) mod t for any x in [0, Q)
     sk = np.zeros(16, dtype=np.int8)
