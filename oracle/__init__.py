@@ -30,7 +30,8 @@ paper fixes none of its internal conventions, so this module takes these reading
     seed, nonce = (purpose, object, limb), block counter = coefficient index.
 
 The CRT plaintext pair of Section 4.2.2 is recombined by the textbook CRT formula
-(crt_combine).
+(crt_combine). The invariant noise budget (noise_budget, a diagnostic; Section 4.2.2 sizes t by
+the budget a ciphertext must keep) is the textbook BFV definition, in whole bits.
 
 Pins (tests/test_oracle_pins.py) tie every function to something other than itself: RFC 8439
 vectors, schoolbook convolution, direct evaluation, sympy's primality and CRT, closed forms,
