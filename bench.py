@@ -59,6 +59,8 @@ def parse_args(argv=None):
     p.add_argument("--latency-reps", type=int, default=20)
     p.add_argument("--no-standard", action="store_true")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--cpu-threads", type=int, default=0,
+                   help="threads of the CPU oracle in the cpu_baseline / reference leg (0 = all host cores)")
     p.add_argument("--sweep", action="store_true", help="also time the server product at several pair chunks")
     p.add_argument("--only-packed", action="store_true",
                    help="profiling case: time only the packed product on --individuals of the batch")
@@ -206,13 +208,14 @@ def aggregate(per_rank_ms, units_per_rank):
 
 # ----------------------------------------------------------------------------- CPU oracle (baseline / reference)
 
-def oracle_sample(n_individuals, steps=1, warmup=0):
+def oracle_sample(n_individuals, steps=1, warmup=0, threads=0):
     """The CPU oracle, as it stands, on `n_individuals` of the headline batch: encode, encrypt,
-    Algorithm 1, decrypt, decode. Returns (predictions/s, cores, seconds per step)."""
+    Algorithm 1, decrypt, decode, on `threads` host threads (0 = all). Returns (predictions/s,
+    threads used, seconds per step)."""
     import oracle
     w = synth.WORKLOADS[WORKLOAD]
     X, W, b = synth.workload_inputs(w)
-    P = oracle.Params.from_shape(w.params)
+    P = oracle.Params.from_shape(w.params, nthreads=threads or None)
     keys = oracle.keygen(P, w.seed_keys)
     W_pt = oracle.encode(P, oracle.pack_weights(P, W).reshape(-1, P.N)).reshape(W.shape[1], -1, P.N)
     times = []
@@ -238,7 +241,7 @@ def run_reference(args):
     if rank != 0:
         return 0
     sample = 1
-    v, cores, sec = oracle_sample(sample, steps=args.steps, warmup=args.warmup)
+    v, cores, sec = oracle_sample(sample, steps=args.steps, warmup=args.warmup, threads=args.cpu_threads)
     line = {
         "impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
@@ -513,10 +516,11 @@ def gpu_extras(args, ctx, keys, model, X, W, b, ws, chunk, dev, kern, step_ms):
     if not args.no_standard:
         out["standard"] = standard_leg(args, ctx, keys, model, X, W, b, dev, step_ms, lat[len(lat) // 2])
     if not args.no_cpu_baseline and int(os.environ.get("WORLD_SIZE", "1")) == 1:
-        v, cores, sec = oracle_sample(4)
+        n = 4 if not args.cpu_threads or args.cpu_threads > 4 else 1    # ~10-40 s of CPU work
+        v, cores, sec = oracle_sample(n, threads=args.cpu_threads)
         out["cpu_baseline"] = {"value": round(v, 4), "unit": UNIT, "cores": cores, "kind": "oracle",
-                               "sample": "4 individuals (64 pairs) of the 512-individual batch, whole protocol "
-                                         f"({sec:.1f} s)"}
+                               "sample": f"{n} individual(s) ({n * W.shape[1]} pairs) of the 512-individual batch, "
+                                         f"whole protocol ({sec:.1f} s)"}
     return out
 
 
