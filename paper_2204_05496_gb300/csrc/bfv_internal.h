@@ -60,6 +60,7 @@ struct bfv_ctx {
     int *derr = nullptr;             // device error word (bounded waits that ran out set bit 0)
     int inject_extra_tx = 0;         // failure injection: bytes a streaming stage waits for in vain
     std::map<size_t, size_t> tuned_chunk;   // pairs -> pair chunk chosen by bfv_autotune_packed
+    mutable std::mutex tune_mu;              // guards tuned_chunk (read by every packed plan)
     // CUDA graphs of whole packed products, keyed by every argument of the call
     typedef std::tuple<const void *, const void *, const void *, size_t, void *, void *, size_t, cudaStream_t> GraphKey;
     std::map<GraphKey, std::pair<cudaGraphExec_t, uint64_t>> graphs;   // exec, kernel launches it holds

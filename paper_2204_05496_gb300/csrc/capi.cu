@@ -339,7 +339,7 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
         }
     }
     if ((rc = dalloc(&c->dslot, N))) { free_ctx(c); return rc; }
-    cudaMemcpy(c->dslot, slot.data(), N * 4, cudaMemcpyHostToDevice);
+    if (cudaMemcpy(c->dslot, slot.data(), N * 4, cudaMemcpyHostToDevice) != cudaSuccess) { free_ctx(c); return BFV_ERR_CUDA; }
     // N^-1 omega^i mod t, i < 2N (one-hot mask coefficients)
     std::vector<u32> mp(2 * N);
     {
@@ -348,14 +348,14 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
         for (u64 i = 0; i < 2 * N; ++i) { mp[i] = (u32)w; w = mulmod_h(w, c->omega, c->t); }
     }
     if ((rc = dalloc(&c->dmaskpow, 2 * N))) { free_ctx(c); return rc; }
-    cudaMemcpy(c->dmaskpow, mp.data(), 2 * N * 4, cudaMemcpyHostToDevice);
+    if (cudaMemcpy(c->dmaskpow, mp.data(), 2 * N * 4, cudaMemcpyHostToDevice) != cudaSuccess) { free_ctx(c); return BFV_ERR_CUDA; }
 
     // Gaussian thresholds
     u64 cdt[32];
     c->cdt_len = gaussian_table_h(c->sigma_num, c->sigma_den, cdt);
     if (c->cdt_len < 0) { free_ctx(c); return BFV_ERR_BAD_PARAMS; }
     if ((rc = dalloc(&c->dcdt, 32))) { free_ctx(c); return rc; }
-    cudaMemcpy(c->dcdt, cdt, 32 * 8, cudaMemcpyHostToDevice);
+    if (cudaMemcpy(c->dcdt, cdt, 32 * 8, cudaMemcpyHostToDevice) != cudaSuccess) { free_ctx(c); return BFV_ERR_CUDA; }
 
     // decryption constants
     DecConst dc;
@@ -382,8 +382,11 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
     }
     if ((rc = dalloc(&c->ddec, 1))) { free_ctx(c); return rc; }
     if ((rc = dalloc(&c->derr, 1))) { free_ctx(c); return rc; }
-    cudaMemset(c->derr, 0, sizeof(int));
-    cudaMemcpy(c->ddec, &dc, sizeof dc, cudaMemcpyHostToDevice);
+    if (cudaMemset(c->derr, 0, sizeof(int)) != cudaSuccess ||
+        cudaMemcpy(c->ddec, &dc, sizeof dc, cudaMemcpyHostToDevice) != cudaSuccess) {
+        free_ctx(c);
+        return BFV_ERR_CUDA;
+    }
 
     // rotate-and-sum Galois elements: 2N-1, then 3^(N/4), ..., 3^1 mod 2N
     c->galois.push_back(2 * N - 1);
@@ -742,7 +745,8 @@ int bfv_autotune_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *mod
     const size_t npairs = nX * model->nY;
     const size_t cands[] = {128, 256, 512, 1024, 2048, 4096, 8192, 16384};
     cudaEvent_t a = nullptr, b = nullptr;
-    if (cudaEventCreate(&a) != cudaSuccess || cudaEventCreate(&b) != cudaSuccess) return BFV_ERR_CUDA;
+    if (cudaEventCreate(&a) != cudaSuccess) return BFV_ERR_CUDA;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return BFV_ERR_CUDA; }
     size_t best = 0, last = 0;
     float best_t = 0;
     int rc = BFV_OK;
@@ -758,14 +762,17 @@ int bfv_autotune_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *mod
         cudaEventRecord(b, st);
         if (cudaEventSynchronize(b) != cudaSuccess) { rc = BFV_ERR_CUDA; break; }
         float t = 0;
-        cudaEventElapsedTime(&t, a, b);
+        if (cudaEventElapsedTime(&t, a, b) != cudaSuccess) { rc = BFV_ERR_CUDA; break; }
         if (!best || t < best_t) { best = eff; best_t = t; }
     }
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (rc) return rc;
     if (!best) return BFV_ERR_OVER_BUDGET;
-    ctx->tuned_chunk[npairs] = best;
+    {
+        std::lock_guard<std::mutex> g(ctx->tune_mu);
+        ctx->tuned_chunk[npairs] = best;
+    }
     *best_chunk = best;
     if (best_ms) *best_ms = best_t;
     return BFV_OK;

@@ -458,6 +458,7 @@ PackedPlan packed_plan_models(const bfv_ctx *c, int nreq, const bfv_model *const
     p.npairs = pairs;
     p.nout = outs;
     if (!chunk) {
+        std::lock_guard<std::mutex> g(c->tune_mu);
         auto it = c->tuned_chunk.find(p.npairs);
         chunk = it != c->tuned_chunk.end() ? it->second : 2048;
     }

@@ -470,7 +470,11 @@ int launch_encode_columns(const bfv_ctx *c, const uint8_t *X, size_t nX, size_t 
 int launch_keygen(const bfv_ctx *c, bfv_keys *k, u64 seed, cudaStream_t st) {
     u64 *dgal = nullptr;
     if (cudaMalloc(&dgal, sizeof(u64) * c->galois.size()) != cudaSuccess) return BFV_ERR_OOM;
-    cudaMemcpyAsync(dgal, c->galois.data(), sizeof(u64) * c->galois.size(), cudaMemcpyHostToDevice, st);
+    if (cudaMemcpyAsync(dgal, c->galois.data(), sizeof(u64) * c->galois.size(), cudaMemcpyHostToDevice, st) !=
+        cudaSuccess) {
+        cudaFree(dgal);
+        return BFV_ERR_CUDA;
+    }
     k_keygen_sk<<<(c->N + 255) / 256, 256, 0, st>>>(seed, c->N, k->sk);
 #define L_(LG)                                                                                                  \
     {                                                                                                           \
@@ -491,7 +495,7 @@ int launch_keygen(const bfv_ctx *c, bfv_keys *k, u64 seed, cudaStream_t st) {
 #undef L_
     count_launch(c, 4);
     if (!rc) rc = last_err();
-    cudaStreamSynchronize(st);
+    if (cudaStreamSynchronize(st) != cudaSuccess && !rc) rc = BFV_ERR_CUDA;
     cudaFree(dgal);
     return rc;
 }
