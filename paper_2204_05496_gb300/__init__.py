@@ -12,6 +12,8 @@ Section 4.2.2 (protocol), Section 4.2.3 / Algorithm 1 (packed product), Section 
 from __future__ import annotations
 
 import ctypes
+import functools
+import inspect
 import os
 import subprocess
 import threading
@@ -591,11 +593,35 @@ class Context:
         return out
 
 
+def _on_call_stream(fn):
+    """Runs a binding call with its `stream` argument as the current CUDA stream. What the call
+    allocates (outputs, workspaces, contiguous copies of inputs) then comes from, and returns to,
+    the pool of the stream its kernels run on, so the caching allocator cannot hand that memory
+    to other work while those kernels may still use it."""
+    sig = inspect.signature(fn)
+
+    @functools.wraps(fn)
+    def call(*args, **kwargs):
+        stream = sig.bind(*args, **kwargs).arguments.get("stream")
+        if stream is None:
+            return fn(*args, **kwargs)
+        import torch
+        with torch.cuda.stream(stream):
+            return fn(*args, **kwargs)
+    return call
+
+
+for _name, _fn in list(vars(Context).items()):
+    if inspect.isfunction(_fn) and "stream" in inspect.signature(_fn).parameters:
+        setattr(Context, _name, _on_call_stream(_fn))
+
+
 def as_u64(t) -> np.ndarray:
     """Device/host int64 tensor holding raw 64-bit words -> numpy uint64 array."""
     return t.detach().cpu().numpy().view(np.uint64)
 
 
+@_on_call_stream
 def crt_combine(r0, t0: int, r1, t1: int, out=None, stream=None):
     """CRT plaintext pair (bfv_crt_combine): device int64 residue tensors r0 (mod t0) and r1
     (mod t1) of equal shape -> the integers x = r0 mod t0, x = r1 mod t1, centred in

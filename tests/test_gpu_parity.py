@@ -248,6 +248,29 @@ def test_standard_wide_weights_parity(tiny):
     assert np.array_equal(slots[:, :9].T, oracle.expected_scores(X, W, b, P.t))
 
 
+def test_calls_on_a_side_stream_tiny(tiny):
+    """Encrypt, packed product and decrypt on a non-default stream with every output and
+    workspace allocated by the binding: each call's allocations follow that stream, and the
+    results equal the oracle's."""
+    ctx, keys, P, okeys = tiny
+    w = synth.WORKLOADS["tiny-16"]
+    X, W, b = synth.workload_inputs(w)
+    oX_ct, _, oY = oracle.packed_pipeline(P, okeys, X, W, b, w.seed_enc)
+    model = ctx.model_prepare(W, b)
+    pt = ctx.encode_features(dev(X).to(torch.uint8))
+    torch.cuda.synchronize()
+    s = torch.cuda.Stream()
+    X_ct = ctx.encrypt(keys, pt.reshape(-1, P.N), seed=w.seed_enc, stream=s).reshape(X.shape[0], -1, 2, P.L, P.N)
+    Y = ctx.lr_scores_packed(keys, model, X_ct, stream=s)
+    m = ctx.decrypt(keys, Y, stream=s)
+    junk = torch.empty(64 << 20, dtype=torch.uint8, device="cuda").fill_(0xA5)   # default-stream traffic
+    s.synchronize()
+    torch.cuda.synchronize()
+    del junk
+    assert np.array_equal(host(X_ct), oX_ct) and np.array_equal(host(Y), oY)
+    assert np.array_equal(host(m), oracle.decrypt(P, okeys.sk, oY))
+
+
 def test_noise_budget_parity_tiny(tiny):
     """bfv_noise_budget against the oracle: fresh encryptions, the outputs of a packed product
     (the oracle's own pipeline) and arbitrary residues, whose noise fills the modulus."""

@@ -92,6 +92,36 @@ def test_binding_refuses_buffers_the_library_would_overrun(bfv):
             f(torch.zeros((3, 10), dtype=torch.int64))                          # host memory
 
 
+def test_binding_calls_run_on_their_stream(bfv, monkeypatch):
+    """Every binding call that takes a stream runs with it as the current stream (so its own
+    allocations follow that stream), whether the stream is passed by keyword or by position;
+    without one it runs on the current stream unchanged."""
+    import contextlib
+    import inspect
+    import torch
+    for name, fn in vars(bfv.Context).items():
+        if inspect.isfunction(fn) and "stream" in inspect.signature(fn).parameters:
+            assert hasattr(fn, "__wrapped__"), name
+    entered = []
+
+    @contextlib.contextmanager
+    def fake_stream(s):
+        entered.append(s)
+        yield s
+    monkeypatch.setattr(torch.cuda, "stream", fake_stream)
+    seen = []
+
+    @bfv._on_call_stream
+    def call(a, b=None, stream=None):
+        seen.append((a, b, stream))
+        return a
+
+    assert call(1) == 1 and entered == []
+    assert call(2, stream="s1") == 2 and entered == ["s1"]
+    assert call(3, 4, "s2") == 3 and entered == ["s1", "s2"]
+    assert seen == [(1, None, None), (2, None, "s1"), (3, 4, "s2")]
+
+
 def test_product_code_never_touches_the_oracle():
     pkg = os.path.join(ROOT, "paper_2204_05496_gb300")
     for dirpath, _, files in os.walk(pkg):
