@@ -384,7 +384,10 @@ def test_moddown_divides_by_p_with_rounding(small):
 
 
 def test_keyswitch_preserves_the_secret_relation(tiny, tiny_keys):
-    # (u0, u1) = KS_g(d): u0 + u1 s = d sigma_g(s) + small error (mod Q)
+    # (u0, u1) = KS_g(d): u0 + u1 s = d sigma_g(s) + err (mod Q). Over QP the key product gives
+    # P d sigma_g(s) + sum_i d_i e_i, so after rounding by P, |err| <= sum_i |d_i e_i| / P + |eps0 +
+    # eps1 s| <= L N max(q) B / P + (1 + N) / 2, with B = floor(6 sigma) the error cutoff and
+    # |eps| <= 1/2 the two roundings
     rng = np.random.default_rng(12)
     d = np.stack([rng.integers(0, q, tiny.N, dtype=np.uint64) for q in tiny.q])
     for gi in (0, 3):
@@ -399,7 +402,9 @@ def test_keyswitch_preserves_the_secret_relation(tiny, tiny_keys):
             res[l] = ((lhs - rhs) % q).astype(np.uint64)
         errs = oracle._crt(tiny, res)
         worst = max(min(v, tiny.Q - v) for v in errs)
-        assert worst < 2 ** 20
+        B = int(6 * Fraction(16, 5))
+        bound = tiny.L * tiny.N * max(tiny.q) * B // tiny.P + (1 + tiny.N) // 2 + 1
+        assert 0 < worst <= bound < 2 ** 18
 
 
 def test_rotation_decrypts_to_rotated_slots(tiny, tiny_keys):
