@@ -127,3 +127,40 @@ def test_requests_of_different_models_fuse_and_count_their_own_pairs(fake_torch)
     assert [getattr(m, "name", "y16") for m in ctx.models_seen[0]] == ["binary0", "binary1", "binary2", "y16"]
     with pytest.raises(ValueError):
         srv.submit(9, _X(1), model=7)
+
+
+def test_priority_class_keeps_small_requests_off_the_large_stream(fake_torch):
+    # small_pairs = 4 with 2-class models: requests of <= 2 individuals are "small" and go to
+    # the high-priority stream 0, larger ones to the normal stream 1, never mixed
+    srv, ctx = make(fake_torch, hbm_budget_bytes=10 ** 6, n_streams=2, small_pairs=4)
+    assert srv.classes == ["small", "large"] and srv.streams[0].priority < srv.streams[1].priority
+    srv.start()
+    for k, n in enumerate([5, 1, 9, 2]):
+        srv.submit(k, _X(n))
+    srv.step()
+    assert sorted(ctx.launches) == [[1, 2], [5, 9]]
+    small = [b for b in srv.busy if b is not None and all(r.nX <= 2 for r in b[1])]
+    assert len(small) == 1 and srv.busy.index(small[0]) == 0
+
+
+def test_run_replays_a_trace_and_reports_latency(fake_torch):
+    srv, ctx = make(fake_torch, hbm_budget_bytes=10 ** 6, n_streams=2)
+    trace = [(0.0, 1), (0.0, 3), (0.001, 1), (0.002, 2, 0)]
+    done = srv.run(trace, lambda k, n: _X(n), poll_s=0.0001, max_seconds=5)
+    assert [r.rid for r in done] == [0, 1, 2, 3] and all(r.t_done is not None for r in done)
+    assert sum(len(x) for x in ctx.launches) == 4 and srv.idle()
+    rep = serve.latency_report(done, 2)
+    assert rep["requests"] == 4 and rep["predictions"] == 7
+    assert {"p50_ms", "p99_ms", "predictions_per_s", "single_p50_ms", "single_p99_ms"} <= set(rep)
+
+
+def test_run_gives_up_after_max_seconds(fake_torch):
+    class _Never(FakeEvent):
+        def query(self):
+            return False
+
+    torch_never = types.SimpleNamespace(cuda=types.SimpleNamespace(**{**vars(fake_torch.cuda), "Event": _Never}),
+                                        empty=fake_torch.empty, uint8=None)
+    srv, _ = make(torch_never, hbm_budget_bytes=10 ** 6, n_streams=1)
+    with pytest.raises(TimeoutError):
+        srv.run([(0.0, 1)], lambda k, n: _X(n), poll_s=0.0001, max_seconds=0.05)
