@@ -60,6 +60,26 @@ def test_bad_parameters_rejected_on_host(bfv):
     assert list(out)[:4] == oracle.ntt_primes(59, 4096, 4)
 
 
+def test_null_handles_rejected_before_any_device_work(bfv):
+    """Every entry point checks its handles and pointers first: with null handles each returns
+    BFV_ERR_INVALID_ARG and touches no device (this runs without a GPU)."""
+    L = bfv.lib()
+    n = ctypes.c_size_t()
+    budgets = (ctypes.c_int * 2)()
+    assert L.bfv_noise_budget_workspace(None, 2, ctypes.byref(n)) == bfv.BFV_ERR_INVALID_ARG
+    assert L.bfv_noise_budget(None, None, None, 2, ctypes.cast(budgets, ctypes.c_void_p), None, 0,
+                              0) == bfv.BFV_ERR_INVALID_ARG
+    assert L.bfv_decrypt_workspace(None, 2, ctypes.byref(n)) == bfv.BFV_ERR_INVALID_ARG
+    assert L.bfv_lr_scores_packed_workspace(None, None, 1, 0, ctypes.byref(n)) == bfv.BFV_ERR_INVALID_ARG
+    assert L.bfv_lr_predict_packed_workspace(None, None, 1, 0, ctypes.byref(n)) == bfv.BFV_ERR_INVALID_ARG
+    assert L.bfv_lr_predict_packed(None, None, None, None, 1, 0, None, None, 0, 0, 0) == bfv.BFV_ERR_INVALID_ARG
+    assert L.bfv_lr_scores_packed(None, None, None, None, 1, None, None, 0, 0, 0) == bfv.BFV_ERR_INVALID_ARG
+    assert L.bfv_crt_combine(None, 5, None, 9, 4, None, 0) == bfv.BFV_ERR_INVALID_ARG     # null arrays
+    assert L.bfv_crt_combine(None, 6, None, 9, 0, None, 0) == bfv.BFV_ERR_INVALID_ARG     # gcd(6, 9) = 3
+    assert L.bfv_crt_combine(None, 1 << 31, None, (1 << 31) + 1, 0, None, 0) == bfv.BFV_ERR_INVALID_ARG  # >= 2^62
+    assert L.bfv_crt_combine(None, 5, None, 9, 0, None, 0) == bfv.BFV_OK                  # nothing to do
+
+
 def test_setup_without_gpu_fails_loudly(bfv):
     import torch
     if torch.cuda.is_available():
