@@ -13,7 +13,8 @@ value     : predictions/s with the features resident in device memory (CUDA even
 e2e       : the same through the C ABI with HOST buffers (bfv_lr_predict_packed_host:
             pinned features copied in, scores copied out, inside the timed call).
 roofline  : the dominant kernel's algorithmic 64-bit modular multiplications per launch over
-            its live CUDA-event launch time, against the integer-pipe peak.
+            its live CUDA-event launch time, against the integer-pipe peak (SMs x 64 32-bit
+            multiply-adds per clock x the sampled SM clock / 15 per 64-bit Shoup product).
 Also reported: 1-individual latency (p50/p99), the server product alone, the standard
 per-element product at the same parameters, per-kernel time shares, and the CPU oracle on a
 bounded sample (cpu_baseline). `--impl reference` times the CPU oracle itself.
@@ -41,11 +42,22 @@ UNIT = "predictions/s"
 WORKLOAD = "batch512-40k"
 LATENCY_WORKLOAD = "single-40k"
 
-# Integer-pipe peak for 64-bit modular multiplication (derivation in the design doc): 152 SMs x
-# 64 32-bit multiply-adds per clock per SM x 2.07 GHz, 15 32-bit half-products per Shoup
-# product (7 for the high 64 bits of x*w', 4 + 4 for the low 64 bits of x*w and q^*q).
-SMS, IMAD_PER_CLK_SM, SM_MAX_HZ, IMAD_PER_MODMUL = 152, 64, 2.07e9, 15
-ALU_PEAK_GMODMUL = SMS * IMAD_PER_CLK_SM * SM_MAX_HZ / IMAD_PER_MODMUL / 1e9
+# Integer-pipe peak for 64-bit modular multiplication (the packed path's roofline). An SM issues
+# at most 64 32-bit multiply-adds (IMAD) per clock (sm_100-class SMs: 4 sub-partitions x 16 IMAD
+# lanes; 59.9 per SM per clock measured in registers on this GPU). A Shoup product x w mod q of
+# 64-bit words is 15 32-bit half-products: 7 for the high 64 bits of x * w' (3 full 32x32
+# products of the high word pairs plus the carries of the partial sums), 4 for the low 64 bits of
+# x * w and 4 for the low 64 bits of floor(x w' / 2^64) * q. So the peak in 64-bit modular
+# multiplications per second is SMs x 64 x SM clock / 15, with the SM count of the device and the
+# median SM clock sampled during the timed region.
+IMAD_PER_CLK_SM, IMAD_PER_MODMUL = 64, 15
+SM_MAX_MHZ_NOMINAL = 2070.0
+
+
+def alu_peak_gmodmul(sms, sm_mhz):
+    return sms * IMAD_PER_CLK_SM * sm_mhz * 1e6 / IMAD_PER_MODMUL / 1e9
+
+
 HBM_FALLBACK_GBS = 6800.0
 
 
@@ -65,6 +77,10 @@ def parse_args(argv=None):
     p.add_argument("--only-packed", action="store_true",
                    help="profiling case: time only the packed product on --individuals of the batch")
     p.add_argument("--individuals", type=int, default=512)
+    p.add_argument("--sched-sweep", action="store_true",
+                   help="with --only-packed: time every split combination of the key-switching kernels")
+    p.add_argument("--autotune", action="store_true",
+                   help="with --only-packed: run the schedule autotuner and report its choice")
     p.add_argument("--ring", choices=["16k", "32k"], default="16k", help="parameter set of --only-packed")
     p.add_argument("--uneven", action="store_true",
                    help="the uneven batch: 64 models on the N = 16384 and N = 32768 sets in one CUDA graph")
@@ -98,8 +114,8 @@ def modmuls_per_pair(kind, N, L, K):
     switching kinds). B = butterflies of one length-N NTT."""
     B = (N // 2) * int(round(np.log2(N)))
     return {
-        "ks_modup": L * L * B + 2 * L * (L + 1) * N,       # L^2 digit NTTs + key inner product
-        "ks_prep": L * B,                                   # inverse NTT of the L digits
+        "ks_modup": L * L * B + 2 * L * (L + 1) * N + L * N,   # L^2 digit NTTs + key inner product + P sigma(c0)
+        "ks_prep": L * B,                                       # inverse NTT of the L digits
         "ks_moddown_p": 2 * B,                              # inverse NTT of the two P limbs
         "ks_moddown": 2 * L * B + 2 * L * N,                # NTT of the corrections + P^-1 product
         "mac": 2 * L * K * N,
@@ -109,7 +125,7 @@ def modmuls_per_pair(kind, N, L, K):
 
 # The source that defines ModUp: its region of k_packed.cu (shape, key products, kernel) and the
 # device header (transforms, arithmetic, tensor memory).
-MODUP_REGION = ("paper_2204_05496_gb300/csrc/k_packed.cu", "// ModUp works on halves", "// Limb unit (g, c): R[g][c]")
+MODUP_REGION = ("paper_2204_05496_gb300/csrc/k_packed.cu", "// ModUp works on parts", "// Limb unit (g, c): R[g][c]")
 
 
 def modup_source_hash():
@@ -122,19 +138,20 @@ def modup_source_hash():
     return h.hexdigest()[:16]
 
 
-def recorded_traffic(kernel):
-    """DRAM bytes per launch from the committed ncu summary, if taken on the kernel's current
-    source (null otherwise)."""
+def recorded_counters(kernel):
+    """(DRAM bytes per launch, FMA-heavy pipe % of peak) from the committed ncu summary, if it was
+    taken on the kernel's current source (None otherwise)."""
     path = os.path.join(ROOT, "profiles", f"{kernel}_traffic.md")
     try:
         txt = open(path).read()
     except OSError:
-        return None
+        return None, None
     m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    f = re.search(r"fmaheavy_pct:\s*([0-9.]+)", txt)
     h = re.search(r"source_hash:\s*([0-9a-f]+)", txt)
-    if not m or not h:
-        return None
-    return float(m.group(1)) if h.group(1) == modup_source_hash() else None
+    if not h or h.group(1) != modup_source_hash():
+        return None, None
+    return (float(m.group(1)) if m else None), (float(f.group(1)) if f else None)
 
 
 class ClockSampler:
@@ -350,7 +367,7 @@ def run_gpu(args):
 
     extras = {}
     if rank == 0:
-        extras = gpu_extras(args, ctx, keys, model, X, W, b, ws, chunk, dev, kern, step_ms)
+        extras = gpu_extras(args, ctx, keys, model, X, W, b, ws, chunk, dev, kern, step_ms, clocks)
     if world > 1:
         dist.barrier()
         dist.destroy_process_group()
@@ -371,7 +388,7 @@ def run_gpu(args):
     return 0
 
 
-def gpu_extras(args, ctx, keys, model, X, W, b, ws, chunk, dev, kern, step_ms):
+def gpu_extras(args, ctx, keys, model, X, W, b, ws, chunk, dev, kern, step_ms, clocks):
     import torch
     w = synth.WORKLOADS[WORKLOAD]
     N, L, K = w.params.N, w.params.L, model.K
@@ -399,12 +416,18 @@ def gpu_extras(args, ctx, keys, model, X, W, b, ws, chunk, dev, kern, step_ms):
     if top in work:
         per_launch = work[top] / n
         achieved = per_launch / (ms / n / 1e3) / 1e9
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
+        mhz = clocks.get("sm_mhz") or SM_MAX_MHZ_NOMINAL
+        peak = alu_peak_gmodmul(sms, mhz)
+        traffic, fma = recorded_counters(top) if top == "ks_modup" else (None, None)
         out["roofline"] = {"kernel": top, "bound": "alu", "achieved": round(achieved, 1),
-                           "peak": round(ALU_PEAK_GMODMUL, 1), "unit": "Gmodmul/s",
-                           "frac": round(achieved / ALU_PEAK_GMODMUL, 4), "traffic": recorded_traffic(top),
+                           "peak": round(peak, 1), "unit": "Gmodmul/s",
+                           "frac": round(achieved / peak, 4), "traffic": traffic,
+                           "ncu_fmaheavy_pipe_pct": fma,
                            "work_per_launch": f"{per_launch:.4g} 64-bit modular multiplications "
                                               f"({plan_chunk} pairs x one key switch)",
-                           "peak_basis": "152 SMs x 64 IMAD/clk x 2.07 GHz / 15 32-bit half-products per Shoup product"}
+                           "peak_basis": f"{sms} SMs x 64 IMAD/clk x {mhz:.0f} MHz (median sampled SM clock) / "
+                                         f"15 32-bit half-products per Shoup product"}
 
     # server product alone (inputs already encrypted)
     pt = ctx.encode_features(torch.from_numpy(X).to(dev))
@@ -620,20 +643,62 @@ def run_only_packed(args):
     z.record()
     torch.cuda.synchronize()
     ms = a.elapsed_time(z) / args.steps
+    # per-kernel device time of one call (an event pair around every launch) against the call's
+    # own time: the rest is the gap between dependent launches
     ctx.profile(True)
     ctx.profile_read()
+    a.record()
     ctx.lr_scores_packed(keys, model, X_ct, out=Y, ws=ws, pair_chunk=args.pair_chunk)
+    z.record()
     torch.cuda.synchronize()
     ctx.profile(False)
+    prof_call_ms = a.elapsed_time(z)
     kern = {k: round(v[1], 3) for k, v in ctx.profile_read().items() if v[0]}
     slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
     got = bfv.unpack_packed_scores(N, slots, len(X), W.shape[1])
     ok = bool(np.array_equal(got, (X.astype(np.int64) @ W + b[None, :]) % shape.t))
     pairs = len(X) * W.shape[1]
-    print(json.dumps({"case": "only-packed", "ring": N, "individuals": len(X), "pairs": pairs,
-                      "pair_chunk": args.pair_chunk, "ms_per_call": round(ms, 3),
-                      "us_per_pair": round(ms * 1e3 / pairs, 2), "kernel_ms": kern, "correct": ok}), flush=True)
-    return 0 if ok else 1
+    # the same product from a CUDA graph
+    ctx.lr_scores_packed_graph(keys, model, X_ct, out=Y, ws=ws, pair_chunk=args.pair_chunk)
+    torch.cuda.synchronize()
+    a.record()
+    for _ in range(args.steps):
+        ctx.lr_scores_packed_graph(keys, model, X_ct, out=Y, ws=ws, pair_chunk=args.pair_chunk)
+    z.record()
+    torch.cuda.synchronize()
+    graph_ms = a.elapsed_time(z) / args.steps
+    res = {"case": "only-packed", "ring": N, "individuals": len(X), "pairs": pairs,
+           "schedule": ctx.packed_schedule(pairs).as_dict() if not args.pair_chunk else {"pair_chunk": args.pair_chunk},
+           "ms_per_call": round(ms, 3), "graph_ms_per_call": round(graph_ms, 3),
+           "us_per_pair": round(ms * 1e3 / pairs, 2), "kernel_ms": kern,
+           "launch_gap_frac": round(1 - sum(kern.values()) / prof_call_ms, 4), "correct": ok}
+    if args.sched_sweep:
+        # every split combination at the plan's chunk (bit-identical results; times only)
+        chunk = args.pair_chunk or ctx.packed_schedule(pairs).pair_chunk
+        sweep = {}
+        for p_, m_, mp_, md_ in [(p_, m_, mp_, md_) for p_ in (1, 2) for m_ in (2, 4) for mp_ in (1, 2)
+                                 for md_ in (1, 2)]:
+            sc = bfv.Schedule(chunk, p_, m_, mp_, md_)
+            Ys = ctx.lr_scores_packed_sched(keys, model, X_ct, sc, ws=ws)
+            ok = ok and bool(torch.equal(Ys, Y))
+            a.record()
+            for _ in range(args.steps):
+                ctx.lr_scores_packed_sched(keys, model, X_ct, sc, out=Ys, ws=ws)
+            z.record()
+            torch.cuda.synchronize()
+            sweep[f"p{p_}m{m_}dp{mp_}d{md_}"] = round(a.elapsed_time(z) / args.steps, 3)
+        res["sched_sweep_ms"] = sweep
+        best = min(sweep, key=sweep.get)
+        res["sched_best"] = best
+        res["correct"] = ok
+    if args.autotune:
+        big = torch.empty(ctx.packed_workspace(model, len(X), 16384), dtype=torch.uint8, device="cuda") \
+            if not args.pair_chunk else ws
+        best, bms = ctx.autotune_packed_schedule(keys, model, X_ct, big)
+        res["autotuned"] = {"schedule": best.as_dict(), "ms": round(bms, 3)}
+        del big
+    print(json.dumps(res), flush=True)
+    return 0 if res["correct"] else 1
 
 
 def run_uneven(args):

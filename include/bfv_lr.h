@@ -161,9 +161,10 @@ int bfv_noise_budget(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *ct, siz
  *  - count may be at most bfv_decrypt_noalloc_max_count() ciphertexts, that is
  *    floor(4 MiB / (L N 8)) (4 at N = 16384, L = 7); larger counts return
  *    BFV_ERR_OVER_BUDGET and nothing is launched — split the batch.
- *  - The first call on a device resolves the array's device address (a runtime query, no
- *    allocation); make that first call before any stream capture. The current device must be
- *    the context's device.
+ *  - The array's device address is resolved when the context is created (bfv_setup, with
+ *    the context's device current; a runtime query, no allocation), so the call itself queries
+ *    nothing; a context created after a device reset resolves it again. The current device
+ *    must be the context's device.
  *  - Every call shares the one array and it keeps the last call's contents. Nothing in it
  *    needs to start at zero (each call writes every word it reads), but calls whose work
  *    overlaps on the GPU race on it: issue them on one stream or otherwise serialise them.
@@ -243,6 +244,50 @@ int bfv_lr_scores_packed_graph(bfv_ctx *ctx, const bfv_keys *keys, const bfv_mod
                                size_t nX, uint64_t *Y_ct, void *ws, size_t ws_bytes, size_t pair_chunk,
                                uintptr_t stream);
 
+/* Schedule of the packed product: how many pairs are in flight at once and how each of the
+ * four key-switching kernels of a rotation step splits a limb over CTAs. Every schedule gives
+ * bit-identical results; they differ only in speed (small pair chunks, one individual, favour
+ * finer splits that fill the SMs). A split of 2 CTAs per limb takes effect at N = 16384 only:
+ * at N = 32768 every limb kernel already runs on a two-CTA cluster, at N <= 8192 on one CTA.
+ *   pair_chunk       pairs in flight at once, >= 1 (workspace grows with it)
+ *   prep_split       1 | 2: CTAs per digit in the inverse transform of the key-switch input
+ *   modup_split      2 | 4: CTAs per target limb in ModUp (each folds log2 of it stages into its loads)
+ *   moddown_p_split  0 | 1 | 2: CTAs per P limb in ModDown's inverse transform (0: 2 when the
+ *                    chunk has fewer than the SM count of pairs, else 1)
+ *   moddown_split    1 | 2: CTAs per limb in ModDown's forward transform and P^-1 product
+ * No counterpart in the paper (a GPU launch configuration). */
+typedef struct bfv_packed_schedule {
+    uint64_t pair_chunk;
+    uint32_t prep_split;
+    uint32_t modup_split;
+    uint32_t moddown_p_split;
+    uint32_t moddown_split;
+} bfv_packed_schedule;
+
+/* The schedule a product of `npairs` pairs uses when called with pair_chunk = 0: the one recorded
+ * for that pair count (bfv_packed_schedule_set or an autotuner), else the one recorded for
+ * npairs = 0, else the library default {2048, 1, 2, 0, 2}. */
+int bfv_packed_schedule_get(const bfv_ctx *ctx, size_t npairs, bfv_packed_schedule *out);
+/* Records `sched` for products of `npairs` pairs (0: every pair count without its own entry);
+ * later calls and workspace queries with pair_chunk = 0 use it. BFV_ERR_INVALID_ARG if a field is
+ * outside the values listed above. */
+int bfv_packed_schedule_set(bfv_ctx *ctx, size_t npairs, const bfv_packed_schedule *sched);
+/* bfv_lr_scores_packed with an explicit schedule (workspace: bfv_lr_scores_packed_workspace with
+ * pair_chunk = sched->pair_chunk). */
+int bfv_lr_scores_packed_sched(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint64_t *X_ct,
+                               size_t nX, uint64_t *Y_ct, void *ws, size_t ws_bytes,
+                               const bfv_packed_schedule *sched, uintptr_t stream);
+
+/* Autotuner for the whole schedule: first the pair chunk as bfv_autotune_packed does (with the
+ * default splits), then each split in turn (coordinate descent over prep_split, modup_split,
+ * moddown_p_split, moddown_split), every candidate timed with CUDA events after a warm-up run on
+ * the caller's inputs. The fastest schedule is recorded for this number of pairs (as
+ * bfv_packed_schedule_set would) and returned in *best with its time in *best_ms. Y_ct receives
+ * the product. Synchronises `stream`. No counterpart in the paper. */
+int bfv_autotune_packed_schedule(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint64_t *X_ct,
+                                 size_t nX, uint64_t *Y_ct, void *ws, size_t ws_bytes, uintptr_t stream,
+                                 bfv_packed_schedule *best, double *best_ms);
+
 /* Autotuner for the packed product's pair chunk (how many pairs are in flight at once):
  * runs the product on the caller's inputs for chunk sizes 128 .. 16384 that fit in ws_bytes,
  * times each with CUDA events after a warm-up run, and records the fastest for this number
@@ -265,6 +310,14 @@ int bfv_lr_scores_standard(bfv_ctx *ctx, const bfv_model *model, const uint64_t 
 /* Synchronises the device, returns the context's device error word in *flags (bit 0: a
  * bounded wait in a kernel ran out) and clears it. Returns BFV_ERR_TIMEOUT if it was set. */
 int bfv_check_error(bfv_ctx *ctx, int *flags);
+
+/* Launch options of a context (no counterpart in the paper; speed only, every value gives the
+ * same bits). BFV_OPT_ENCRYPT_SPLIT: CTAs per limb of the encryption kernel at N = 16384, 1 (one
+ * 512-thread CTA) or 2 (a cluster of two 256-thread CTAs, three of which share an SM; the
+ * default); other rings ignore it. bfv_get_option writes the current value to *value. */
+#define BFV_OPT_ENCRYPT_SPLIT 1
+int bfv_set_option(bfv_ctx *ctx, int option, int value);
+int bfv_get_option(const bfv_ctx *ctx, int option, int *value);
 
 /* Failure injection for tests (host-side switch, no fault): with what =
  * BFV_INJECT_STREAM_STALL and value = n > 0 (a multiple of 16), the first pipeline stage of

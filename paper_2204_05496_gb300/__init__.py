@@ -14,6 +14,7 @@ from __future__ import annotations
 import ctypes
 import functools
 import inspect
+import json
 import os
 import subprocess
 import threading
@@ -31,6 +32,7 @@ SOURCES = ["capi.cu", "k_scheme.cu", "k_packed.cu", "k_standard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 BFV_OK, BFV_ERR_INVALID_ARG, BFV_ERR_BAD_PARAMS, BFV_ERR_OOM = 0, -1, -2, -3
+BFV_OPT_ENCRYPT_SPLIT = 1
 BFV_ERR_OVER_BUDGET, BFV_ERR_TIMEOUT, BFV_ERR_CUDA = -4, -5, -6
 _ERRS = {-1: "INVALID_ARG", -2: "BAD_PARAMS", -3: "OOM", -4: "OVER_BUDGET", -5: "TIMEOUT", -6: "CUDA"}
 
@@ -85,6 +87,20 @@ class Params(ctypes.Structure):
                 ("sigma_den", ctypes.c_uint32)]
 
 
+class Schedule(ctypes.Structure):
+    """bfv_packed_schedule: pair chunk and the CTAs per limb of each key-switching kernel."""
+    _fields_ = [("pair_chunk", ctypes.c_uint64), ("prep_split", ctypes.c_uint32), ("modup_split", ctypes.c_uint32),
+                ("moddown_p_split", ctypes.c_uint32), ("moddown_split", ctypes.c_uint32)]
+    FIELDS = ("pair_chunk", "prep_split", "modup_split", "moddown_p_split", "moddown_split")
+
+    def as_dict(self):
+        return {k: int(getattr(self, k)) for k in self.FIELDS}
+
+    @classmethod
+    def from_dict(cls, d):
+        return cls(*(int(d[k]) for k in cls.FIELDS))
+
+
 _lib = None
 _lock = threading.Lock()
 _vp, _u64, _sz, _up = ctypes.c_void_p, ctypes.c_uint64, ctypes.c_size_t, ctypes.c_size_t
@@ -128,6 +144,13 @@ SIGNATURES = {
     "bfv_autotune_packed": [_vp, _vp, _vp, _vp, _sz, _vp, _vp, _sz, _up, ctypes.POINTER(_sz),
                             ctypes.POINTER(ctypes.c_double)],
     "bfv_decrypt_noalloc": [_vp, _vp, _vp, _sz, _vp, _up],
+    "bfv_set_option": [_vp, ctypes.c_int, ctypes.c_int],
+    "bfv_get_option": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
+    "bfv_packed_schedule_get": [_vp, _sz, ctypes.POINTER(Schedule)],
+    "bfv_packed_schedule_set": [_vp, _sz, ctypes.POINTER(Schedule)],
+    "bfv_lr_scores_packed_sched": [_vp, _vp, _vp, _vp, _sz, _vp, _vp, _sz, ctypes.POINTER(Schedule), _up],
+    "bfv_autotune_packed_schedule": [_vp, _vp, _vp, _vp, _sz, _vp, _vp, _sz, _up, ctypes.POINTER(Schedule),
+                                     ctypes.POINTER(ctypes.c_double)],
     "bfv_lr_packed_pair_from_workspace": [_vp, _vp, _sz, _sz, _vp, _sz, _vp, _up],
     "bfv_launch_count": [_vp, ctypes.POINTER(_u64)],
     "bfv_lr_predict_packed_workspace": [_vp, _vp, _sz, _sz, ctypes.POINTER(_sz)],
@@ -231,6 +254,21 @@ def _stream(stream=None):
     import torch
     s = stream if stream is not None else torch.cuda.current_stream()
     return s.cuda_stream
+
+
+def load_schedule_file(path: str) -> dict:
+    """{key: schedule fields} of a schedule file written by Context.save_schedules ({} if absent)."""
+    try:
+        with open(path) as f:
+            data = json.load(f)
+    except FileNotFoundError:
+        return {}
+    if not isinstance(data, dict):
+        raise ValueError(f"{path}: a JSON object of schedules expected")
+    for k, d in data.items():
+        if set(d) != set(Schedule.FIELDS):
+            raise ValueError(f"{path}: schedule {k} must have exactly the fields {Schedule.FIELDS}")
+    return data
 
 
 def primes(N: int, L: int, prime_bits: int, t: int) -> list[int]:
@@ -515,6 +553,71 @@ class Context:
         _call("bfv_autotune_packed", self.handle, keys.handle, model.handle, _ptr(X_ct), nX, _ptr(Y), _ptr(ws),
               ws.numel() * ws.element_size(), _stream(stream), ctypes.byref(ch), ctypes.byref(ms))
         return ch.value, ms.value
+
+    # -- launch options (bfv_set_option)
+    def set_option(self, option: int, value: int):
+        _call("bfv_set_option", self.handle, option, value)
+
+    def get_option(self, option: int) -> int:
+        v = ctypes.c_int()
+        _call("bfv_get_option", self.handle, option, ctypes.byref(v))
+        return v.value
+
+    # -- schedules of the packed product (bfv_packed_schedule)
+    def packed_schedule(self, npairs: int) -> Schedule:
+        """The schedule a product of npairs pairs uses with pair_chunk = 0."""
+        s = Schedule()
+        _call("bfv_packed_schedule_get", self.handle, npairs, ctypes.byref(s))
+        return s
+
+    def set_packed_schedule(self, npairs: int, sched: Schedule):
+        """Records sched for products of npairs pairs (0: every pair count without its own entry)."""
+        _call("bfv_packed_schedule_set", self.handle, npairs, ctypes.byref(sched))
+
+    def lr_scores_packed_sched(self, keys: Keys, model: Model, X_ct, sched: Schedule, out=None, ws=None,
+                               stream=None):
+        """lr_scores_packed with an explicit schedule."""
+        nX, X_ct, Y = self._packed_args(model, X_ct, out)
+        if nX == 0:
+            return Y
+        ws, nb = _workspace(ws, self.packed_workspace(model, nX, sched.pair_chunk), X_ct.device)
+        _call("bfv_lr_scores_packed_sched", self.handle, keys.handle, model.handle, _ptr(X_ct), nX, _ptr(Y),
+              _ptr(ws), nb, ctypes.byref(sched), _stream(stream))
+        return Y
+
+    def autotune_packed_schedule(self, keys: Keys, model: Model, X_ct, ws, out=None, stream=None):
+        """Tunes the pair chunk, then each kernel split (coordinate descent), records the fastest
+        schedule for this number of pairs and returns (Schedule, ms)."""
+        nX, X_ct, Y = self._packed_args(model, X_ct, out)
+        ws = _dev_in(ws, "ws", ws.element_size())
+        best, ms = Schedule(), ctypes.c_double()
+        _call("bfv_autotune_packed_schedule", self.handle, keys.handle, model.handle, _ptr(X_ct), nX, _ptr(Y),
+              _ptr(ws), ws.numel() * ws.element_size(), _stream(stream), ctypes.byref(best), ctypes.byref(ms))
+        return best, ms.value
+
+    def schedule_key(self, npairs: int) -> str:
+        """Key of a tuned schedule in a schedule file: ring degree, ciphertext primes, pairs."""
+        return f"N={self.N},L={self.L},pairs={npairs}"
+
+    def save_schedules(self, path: str, npairs_list):
+        """Writes the schedules of the given pair counts to a JSON file (merged with what it holds)."""
+        data = load_schedule_file(path)
+        for n in npairs_list:
+            data[self.schedule_key(n)] = self.packed_schedule(n).as_dict()
+        tmp = path + f".tmp{os.getpid()}"
+        with open(tmp, "w") as f:
+            json.dump(data, f, indent=1, sort_keys=True)
+        os.replace(tmp, path)
+
+    def load_schedules(self, path: str) -> int:
+        """Records every schedule of a JSON file that belongs to this ring (N, L); returns how many."""
+        n = 0
+        for key, d in load_schedule_file(path).items():
+            parts = dict(kv.split("=") for kv in key.split(","))
+            if int(parts["N"]) == self.N and int(parts["L"]) == self.L:
+                self.set_packed_schedule(int(parts["pairs"]), Schedule.from_dict(d))
+                n += 1
+        return n
 
     def lr_scores_standard(self, model: Model, X_ct, nX: int, out=None, ws=None, stream=None):
         ctw = 2 * self.L * self.N

@@ -31,6 +31,7 @@ struct ModTab {
     int bits;               // bit length of q
     int pad_;
     u64 pinv, pinvp;        // P^-1 mod q and companion (ciphertext primes only)
+    u64 pmod, pmodp;        // P mod q and companion (ciphertext primes only)
     u64 phalf;              // floor(P/2) mod q
     u64 delta;              // floor(Q/t) mod q
     u64 r64, r64p;          // 2^64 mod q and companion

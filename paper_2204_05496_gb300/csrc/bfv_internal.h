@@ -59,10 +59,13 @@ struct bfv_ctx {
     int sms = 0;                     // streaming multiprocessors of the device
     int *derr = nullptr;             // device error word (bounded waits that ran out set bit 0)
     int inject_extra_tx = 0;         // failure injection: bytes a streaming stage waits for in vain
-    std::map<size_t, size_t> tuned_chunk;   // pairs -> pair chunk chosen by bfv_autotune_packed
-    mutable std::mutex tune_mu;              // guards tuned_chunk (read by every packed plan)
+    u64 *noalloc_scratch = nullptr;  // device address of bfv_decrypt_noalloc's fixed array
+    int enc_split = 2;               // CTAs per limb of the encryption kernel at N = 16384 (BFV_OPT_ENCRYPT_SPLIT)
+    std::map<size_t, bfv_packed_schedule> tuned;   // pairs -> schedule (0: any other pair count)
+    mutable std::mutex tune_mu;                    // guards tuned (read by every packed plan)
     // CUDA graphs of whole packed products, keyed by every argument of the call
-    typedef std::tuple<const void *, const void *, const void *, size_t, void *, void *, size_t, cudaStream_t> GraphKey;
+    typedef std::tuple<const void *, const void *, const void *, size_t, void *, void *, size_t, size_t, cudaStream_t>
+        GraphKey;   // keys, model, inputs, individuals, outputs, workspace, pair chunk, splits, stream
     std::map<GraphKey, std::pair<cudaGraphExec_t, uint64_t>> graphs;   // exec, kernel launches it holds
     std::mutex graph_mu;
     cudaStream_t capture_stream = nullptr;   // graphs are captured here, then launched on the caller's stream
@@ -176,6 +179,8 @@ int launch_decrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *ct, size_t co
 int launch_noise_bits(const bfv_ctx *c, const bfv_keys *k, const u64 *ct, size_t count, u64 *x, int *bits,
                       cudaStream_t st);
 int launch_model_weights(const bfv_ctx *c, bfv_model *m, const u64 *w_pt, cudaStream_t st);
+// Device address of bfv_decrypt_noalloc's fixed scratch array on the current device (k_scheme.cu).
+int noalloc_scratch_address(u64 **out);
 int launch_crt_combine(const int64_t *r0, u64 t0, const int64_t *r1, u64 t1, u64 inv, size_t n, int64_t *out,
                        cudaStream_t st);
 
@@ -196,7 +201,8 @@ struct ReqTable {
 
 struct PackedPlan {
     size_t nX, nY, K;                // single-model products: individuals, classes, plaintexts per individual
-    size_t npairs, nout, chunk;
+    size_t npairs, nout, chunk;      // chunk = sched.pair_chunk, at most npairs
+    bfv_packed_schedule sched;       // how the key-switching kernels split their limbs
     size_t xcts_chunk;               // most input ciphertexts any pair chunk needs in evaluation form
     size_t off_xntt, off_yacc, off_state, off_digits, off_u, off_r, total;
     int nreq;
@@ -213,10 +219,17 @@ inline void chunk_window(const PackedPlan &p, int r, size_t g0, size_t ng, size_
     ib = (b - 1 - pa) / nY + 1;
 }
 
-PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t chunk);
-PackedPlan packed_plan_multi(const bfv_ctx *c, const bfv_model *m, int nreq, const size_t *nXs, size_t chunk);
+// The schedule of a product: `sched` if given, else the one recorded for its pair count (or the
+// default), with the pair chunk replaced by `chunk` when non-zero.
+bfv_packed_schedule default_schedule();
+bool schedule_ok(const bfv_packed_schedule &s);
+bfv_packed_schedule schedule_for(const bfv_ctx *c, size_t npairs, size_t chunk);
+PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t chunk,
+                       const bfv_packed_schedule *sched = nullptr);
+PackedPlan packed_plan_multi(const bfv_ctx *c, const bfv_model *m, int nreq, const size_t *nXs, size_t chunk,
+                             const bfv_packed_schedule *sched = nullptr);
 PackedPlan packed_plan_models(const bfv_ctx *c, int nreq, const bfv_model *const *models, const size_t *nXs,
-                              size_t chunk);
+                              size_t chunk, const bfv_packed_schedule *sched = nullptr);
 int launch_packed_multi(const bfv_ctx *c, const bfv_keys *k, int nreq, const u64 *const *X_ct, u64 *const *Y_ct,
                         void *ws, const PackedPlan &plan, cudaStream_t st);
 int launch_packed(const bfv_ctx *c, const bfv_keys *k, const u64 *X_ct, u64 *Y_ct, void *ws, const PackedPlan &plan,

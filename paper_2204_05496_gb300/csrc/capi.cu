@@ -311,6 +311,8 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
         if (j < c->L) {
             T.pinv = inv_h(P % q, q);
             T.pinvp = shoup_h(T.pinv, q);
+            T.pmod = P % q;
+            T.pmodp = shoup_h(T.pmod, q);
             T.phalf = (P / 2) % q;
             T.delta = mw_mod_small(Qdt, q);
             c->delta_host[j] = T.delta;
@@ -391,6 +393,9 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
     // rotate-and-sum Galois elements: 2N-1, then 3^(N/4), ..., 3^1 mod 2N
     c->galois.push_back(2 * N - 1);
     for (u64 s = N / 4; s >= 1; s >>= 1) c->galois.push_back(powmod_h(3, s, 2 * N));
+
+    // the device address of bfv_decrypt_noalloc's fixed scratch array, with this device current
+    if ((rc = noalloc_scratch_address(&c->noalloc_scratch))) { free_ctx(c); return rc; }
 
     if (cudaDeviceSynchronize() != cudaSuccess) { free_ctx(c); return BFV_ERR_CUDA; }
     *out = c;
@@ -704,7 +709,9 @@ int bfv_lr_scores_packed_graph(bfv_ctx *ctx, const bfv_keys *keys, const bfv_mod
     cudaStream_t st = S(stream);
     if (ctx->prof.on)   // per-launch event timing needs direct launches
         return launch_packed(ctx, keys, (const u64 *)X_ct, (u64 *)Y_ct, ws, plan, st);
-    bfv_ctx::GraphKey key(keys, model, X_ct, nX, Y_ct, ws, plan.chunk, st);
+    const size_t splits = plan.sched.prep_split | plan.sched.modup_split << 4 | plan.sched.moddown_p_split << 8 |
+                          plan.sched.moddown_split << 12;
+    bfv_ctx::GraphKey key(keys, model, X_ct, nX, Y_ct, ws, plan.chunk, splits, st);
     std::lock_guard<std::mutex> g(ctx->graph_mu);
     auto it = ctx->graphs.find(key);
     if (it == ctx->graphs.end()) {
@@ -736,45 +743,137 @@ int bfv_lr_scores_packed_graph(bfv_ctx *ctx, const bfv_keys *keys, const bfv_mod
     return BFV_OK;
 }
 
+int bfv_packed_schedule_get(const bfv_ctx *ctx, size_t npairs, bfv_packed_schedule *out) {
+    if (!ctx || !out) return BFV_ERR_INVALID_ARG;
+    *out = schedule_for(ctx, npairs, 0);
+    return BFV_OK;
+}
+
+int bfv_packed_schedule_set(bfv_ctx *ctx, size_t npairs, const bfv_packed_schedule *sched) {
+    if (!ctx || !sched || !schedule_ok(*sched)) return BFV_ERR_INVALID_ARG;
+    std::lock_guard<std::mutex> g(ctx->tune_mu);
+    ctx->tuned[npairs] = *sched;
+    return BFV_OK;
+}
+
+int bfv_lr_scores_packed_sched(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint64_t *X_ct,
+                               size_t nX, uint64_t *Y_ct, void *ws, size_t ws_bytes, const bfv_packed_schedule *sched,
+                               uintptr_t stream) {
+    if (!ctx || !keys || !model || keys->ctx != ctx || model->ctx != ctx || !sched) return BFV_ERR_INVALID_ARG;
+    if (!schedule_ok(*sched)) return BFV_ERR_INVALID_ARG;
+    if (nX == 0) return BFV_OK;
+    if (!X_ct || !Y_ct || !ws) return BFV_ERR_INVALID_ARG;
+    PackedPlan plan = packed_plan(ctx, model, nX, 0, sched);
+    if (ws_bytes < plan.total) return BFV_ERR_OVER_BUDGET;
+    return launch_packed(ctx, keys, (const u64 *)X_ct, (u64 *)Y_ct, ws, plan, S(stream));
+}
+
+namespace {
+// Times one product with the given schedule (a warm-up run, then a timed run); *ms = its time.
+int time_schedule(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint64_t *X_ct, size_t nX,
+                  uint64_t *Y_ct, void *ws, const bfv_packed_schedule &sc, cudaStream_t st, cudaEvent_t a,
+                  cudaEvent_t b, float *ms) {
+    PackedPlan plan = packed_plan(ctx, model, nX, 0, &sc);
+    int rc;
+    if ((rc = launch_packed(ctx, keys, (const u64 *)X_ct, (u64 *)Y_ct, ws, plan, st))) return rc;   // warm-up
+    cudaEventRecord(a, st);
+    if ((rc = launch_packed(ctx, keys, (const u64 *)X_ct, (u64 *)Y_ct, ws, plan, st))) return rc;
+    cudaEventRecord(b, st);
+    if (cudaEventSynchronize(b) != cudaSuccess) return BFV_ERR_CUDA;
+    return cudaEventElapsedTime(ms, a, b) == cudaSuccess ? BFV_OK : BFV_ERR_CUDA;
+}
+
+// The pair-chunk search of both autotuners: chunk sizes 128 .. 16384 that fit in ws_bytes, with
+// the splits of `base`; returns the fastest in *best (BFV_ERR_OVER_BUDGET if none fits).
+int tune_chunk(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint64_t *X_ct, size_t nX,
+               uint64_t *Y_ct, void *ws, size_t ws_bytes, cudaStream_t st, cudaEvent_t a, cudaEvent_t b,
+               bfv_packed_schedule *best, float *best_t) {
+    const size_t npairs = nX * model->nY;
+    const size_t cands[] = {128, 256, 512, 1024, 2048, 4096, 8192, 16384};
+    bfv_packed_schedule base = *best;
+    size_t last = 0;
+    bool found = false;
+    for (size_t ch : cands) {
+        const size_t eff = std::min(ch, npairs);
+        if (eff == last) continue;               // larger candidates all mean "every pair at once"
+        last = eff;
+        bfv_packed_schedule sc = base;
+        sc.pair_chunk = eff;
+        if (packed_plan(ctx, model, nX, 0, &sc).total > ws_bytes) break;
+        float t = 0;
+        int rc = time_schedule(ctx, keys, model, X_ct, nX, Y_ct, ws, sc, st, a, b, &t);
+        if (rc) return rc;
+        if (!found || t < *best_t) { *best = sc; *best_t = t; found = true; }
+    }
+    return found ? BFV_OK : BFV_ERR_OVER_BUDGET;
+}
+}  // namespace
+
+int bfv_autotune_packed_schedule(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint64_t *X_ct,
+                                 size_t nX, uint64_t *Y_ct, void *ws, size_t ws_bytes, uintptr_t stream,
+                                 bfv_packed_schedule *best, double *best_ms) {
+    if (!ctx || !keys || !model || keys->ctx != ctx || model->ctx != ctx || !best) return BFV_ERR_INVALID_ARG;
+    if (nX == 0 || !X_ct || !Y_ct || !ws) return BFV_ERR_INVALID_ARG;
+    cudaStream_t st = S(stream);
+    cudaEvent_t a = nullptr, b = nullptr;
+    if (cudaEventCreate(&a) != cudaSuccess) return BFV_ERR_CUDA;
+    if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return BFV_ERR_CUDA; }
+    bfv_packed_schedule sc = default_schedule();
+    float t = 0;
+    int rc = tune_chunk(ctx, keys, model, X_ct, nX, Y_ct, ws, ws_bytes, st, a, b, &sc, &t);
+    // coordinate descent over the splits, at the chosen chunk
+    uint32_t bfv_packed_schedule::*fields[] = {&bfv_packed_schedule::prep_split, &bfv_packed_schedule::modup_split,
+                                               &bfv_packed_schedule::moddown_p_split,
+                                               &bfv_packed_schedule::moddown_split};
+    const uint32_t values[4][3] = {{1, 2, 0}, {2, 4, 0}, {1, 2, 0}, {1, 2, 0}};   // 0 ends a list
+    for (int f = 0; f < 4 && !rc; ++f) {
+        for (int v = 0; v < 3 && values[f][v] && !rc; ++v) {
+            bfv_packed_schedule cand = sc;
+            cand.*fields[f] = values[f][v];
+            if (cand.*fields[f] == sc.*fields[f]) continue;
+            float tc = 0;
+            rc = time_schedule(ctx, keys, model, X_ct, nX, Y_ct, ws, cand, st, a, b, &tc);
+            if (!rc && tc < t) { sc = cand; t = tc; }
+        }
+    }
+    cudaEventDestroy(a);
+    cudaEventDestroy(b);
+    if (rc) return rc;
+    {
+        std::lock_guard<std::mutex> g(ctx->tune_mu);
+        ctx->tuned[nX * model->nY] = sc;
+    }
+    // leave Y_ct holding the product of the recorded schedule
+    PackedPlan plan = packed_plan(ctx, model, nX, 0, &sc);
+    if ((rc = launch_packed(ctx, keys, (const u64 *)X_ct, (u64 *)Y_ct, ws, plan, st))) return rc;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return BFV_ERR_CUDA;
+    *best = sc;
+    if (best_ms) *best_ms = t;
+    return BFV_OK;
+}
+
 int bfv_autotune_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *model, const uint64_t *X_ct, size_t nX,
                         uint64_t *Y_ct, void *ws, size_t ws_bytes, uintptr_t stream, size_t *best_chunk,
                         double *best_ms) {
     if (!ctx || !keys || !model || keys->ctx != ctx || model->ctx != ctx || !best_chunk) return BFV_ERR_INVALID_ARG;
     if (nX == 0 || !X_ct || !Y_ct || !ws) return BFV_ERR_INVALID_ARG;
     cudaStream_t st = S(stream);
-    const size_t npairs = nX * model->nY;
-    const size_t cands[] = {128, 256, 512, 1024, 2048, 4096, 8192, 16384};
     cudaEvent_t a = nullptr, b = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess) return BFV_ERR_CUDA;
     if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return BFV_ERR_CUDA; }
-    size_t best = 0, last = 0;
-    float best_t = 0;
-    int rc = BFV_OK;
-    for (size_t ch : cands) {
-        const size_t eff = std::min(ch, npairs);
-        if (eff == last) continue;               // larger candidates all mean "every pair at once"
-        last = eff;
-        PackedPlan plan = packed_plan(ctx, model, nX, eff);
-        if (plan.total > ws_bytes) break;
-        if ((rc = launch_packed(ctx, keys, (const u64 *)X_ct, (u64 *)Y_ct, ws, plan, st))) break;  // warm-up
-        cudaEventRecord(a, st);
-        if ((rc = launch_packed(ctx, keys, (const u64 *)X_ct, (u64 *)Y_ct, ws, plan, st))) break;
-        cudaEventRecord(b, st);
-        if (cudaEventSynchronize(b) != cudaSuccess) { rc = BFV_ERR_CUDA; break; }
-        float t = 0;
-        if (cudaEventElapsedTime(&t, a, b) != cudaSuccess) { rc = BFV_ERR_CUDA; break; }
-        if (!best || t < best_t) { best = eff; best_t = t; }
-    }
+    const size_t npairs = nX * model->nY;
+    bfv_packed_schedule sc = schedule_for(ctx, npairs, 0);   // its splits; the chunk is searched
+    float t = 0;
+    int rc = tune_chunk(ctx, keys, model, X_ct, nX, Y_ct, ws, ws_bytes, st, a, b, &sc, &t);
     cudaEventDestroy(a);
     cudaEventDestroy(b);
     if (rc) return rc;
-    if (!best) return BFV_ERR_OVER_BUDGET;
     {
         std::lock_guard<std::mutex> g(ctx->tune_mu);
-        ctx->tuned_chunk[npairs] = best;
+        ctx->tuned[npairs] = sc;
     }
-    *best_chunk = best;
-    if (best_ms) *best_ms = best_t;
+    *best_chunk = sc.pair_chunk;
+    if (best_ms) *best_ms = t;
     return BFV_OK;
 }
 
@@ -795,6 +894,25 @@ int bfv_lr_scores_standard(bfv_ctx *ctx, const bfv_model *model, const uint64_t 
     if (model->wmax >= (1ll << 31) || (long double)model->wmax * model->f * (long double)(1ull << wide) >= 9.2e18L)
         return BFV_ERR_BAD_PARAMS;
     return launch_standard(ctx, model, (const u64 *)X_ct, (u64 *)Y_ct, ws, pl, S(stream));
+}
+
+int bfv_set_option(bfv_ctx *ctx, int option, int value) {
+    if (!ctx) return BFV_ERR_INVALID_ARG;
+    switch (option) {
+        case BFV_OPT_ENCRYPT_SPLIT:
+            if (value != 1 && value != 2) return BFV_ERR_INVALID_ARG;
+            ctx->enc_split = value;
+            return BFV_OK;
+        default: return BFV_ERR_INVALID_ARG;
+    }
+}
+
+int bfv_get_option(const bfv_ctx *ctx, int option, int *value) {
+    if (!ctx || !value) return BFV_ERR_INVALID_ARG;
+    switch (option) {
+        case BFV_OPT_ENCRYPT_SPLIT: *value = ctx->enc_split; return BFV_OK;
+        default: return BFV_ERR_INVALID_ARG;
+    }
 }
 
 int bfv_debug_inject(bfv_ctx *ctx, int what, int value) {

@@ -6,17 +6,22 @@
 //   MAC          C[g] = sum_k X[i][k] (.) W[j][k]                         (Algorithm 1 lines 5-13)
 //   log2 N times C[g] += rot_gal(C[g])                                    (lines 14-17)
 //       rot(c) = (sigma(c0) + u0', u1'), (u0', u1') = KS(sigma(c1)):
-//       ks_prep     c1 limb l -> sigma -> inverse NTT -> digit d_l (coefficients);
-//                   c0 limb l -> c0 + sigma(c0)
-//       ks_modup    for target limb j of QP and half h of the evaluation points:
-//                   U_c[j] = sum_i NTT_j(d_i mod q_j) (.) key[i][c][j]; the first
-//                   Cooley-Tukey stage is folded into the load, so each CTA transforms
-//                   only its half of the points; the two sums live in tensor memory
+//       ks_prep     c1 limb l -> sigma -> inverse NTT -> digit d_l (coefficients)
+//       ks_modup    for target limb j of QP and part h of the evaluation points:
+//                   U_c[j] = sum_i NTT_j(d_i mod q_j) (.) key[i][c][j]; the first one or two
+//                   Cooley-Tukey stages are folded into the load, so each CTA transforms
+//                   only its part of the points; the two sums live in tensor memory. For
+//                   j < L the permuted addend sigma(c0) enters as U_0[j] += P sigma(c0)[j]
+//                   (ModDown multiplies by P^-1 and adds to c0, which gives c0 + sigma(c0)
+//                   + KS(...)_0 exactly)
 //       ks_moddown_p  inverse NTT of U_c[P], r = [U_c[P] + floor(P/2)]_P
 //       ks_moddown  C_c[l] += (U_c[l] + NTT_l(floor(P/2) - r)) * P^-1
 //   bias+mask    C0 += Delta b_j; C *= NTT(mask_g), mask_g one-hot at slot g mod N (18-22)
 //   compress     Yacc[g / N] += C[g]                                       (25-42)
 // and finally Y = inverse NTT(Yacc).
+//
+// How each key-switching kernel splits a limb over CTAs (the schedule) is a run-time choice
+// (bfv_packed_schedule): every schedule computes the same bits.
 #include <algorithm>
 
 #include "bfv_internal.h"
@@ -68,85 +73,83 @@ __global__ void __launch_bounds__(256) k_mac(const ModTab *__restrict__ mods, in
 
 // ------------------------------------------------------------------ key switching
 
-// Limb unit (g, c, l). c = 1: digit D[g][l] = INTT(sigma(C1[g][l])); c = 0: C0 += sigma(C0).
-// (MODE 1, two 256-thread CTAs per limb at N = 16384, was measured slower at every chunk size.)
+// Limb unit (g, l): digit D[g][l] = INTT(sigma(C1[g][l])). MODE 1 splits a limb of N = 16384
+// over two 256-thread CTAs (a cluster; the last inverse stage reads the partner's half).
 template <int LOGN, int MODE>
-LIMB_KERNEL_M(LOGN, MODE) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 gal, u64 *C, u64 *D) {
+LIMB_KERNEL_M(LOGN, MODE) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 gal, const u64 *__restrict__ C,
+                                    u64 *D) {
     extern __shared__ u64 sm[];
     LIMB_INDEX_M(LOGN, MODE);
-    constexpr int NT = Split<LOGN, MODE>::NT;
-    const int l = (int)(unit % L), c = (int)((unit / L) % 2);
-    const size_t g = unit / (2 * L);
+    constexpr int NT = Split<LOGN, MODE>::NT, S = Split<LOGN, MODE>::S;
+    const int l = (int)(unit % L);
+    const size_t g = unit / L;
     const ModTab T = mods[l];
-    u64 *limb = C + ((g * 2 + c) * L + l) * (size_t)N;
-    if (c == 1) {
-        u64 *dst = D + (g * L + l) * (size_t)N;
-        // the permuted reads below touch the whole limb in random order: bring it into L2 with
-        // coalesced line prefetches first
-        for (int i = threadIdx.x; i < N / 16; i += NT)
-            asm volatile("prefetch.global.L2 [%0];" ::"l"(limb + 16 * i));
-        limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return limb[auto_src(p, gal, LOGN)]; },
-                                 [&](int p, u64 v) { dst[p] = v; });
-    } else if constexpr (Split<LOGN, MODE>::S == 1) {
-        for (int p = threadIdx.x; p < N; p += NT) sm[p] = limb[p];
-        __syncthreads();
-        for (int p = threadIdx.x; p < N; p += NT) limb[p] = add_mod(sm[p], sm[auto_src(p, gal, LOGN)], T.q);
-    } else {
-        // the permuted operand may sit in the partner CTA's half
-        for (int p = threadIdx.x; p < M; p += NT) sm[p] = limb[h * M + p];
-        cluster_sync();
-        const u32 peer = cluster_map(sm, (u32)(h ^ 1));
-        for (int p = threadIdx.x; p < M; p += NT) {
-            const int src = auto_src(h * M + p, gal, LOGN);
-            const u64 b = (src / M == h) ? sm[src & (M - 1)] : ld_cluster(peer + 8u * (u32)(src & (M - 1)));
-            limb[h * M + p] = add_mod(sm[p], b, T.q);
-        }
-        cluster_sync();
-    }
+    const u64 *limb = C + ((g * 2 + 1) * L + l) * (size_t)N;
+    u64 *dst = D + (g * L + l) * (size_t)N;
+    // the permuted reads below touch the whole limb in random order: bring it into L2 with
+    // coalesced line prefetches first (each CTA of the group a share of the lines)
+    for (int i = threadIdx.x + h * NT; i < N / 16; i += S * NT)
+        asm volatile("prefetch.global.L2 [%0];" ::"l"(limb + 16 * i));
+    limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return limb[auto_src(p, gal, LOGN)]; },
+                             [&](int p, u64 v) { dst[p] = v; });
 }
 
-// ModUp works on halves of H = N/2 evaluation points of a target limb: the first Cooley-Tukey
-// stage is done in the load (each CTA reads both halves of the digit) and the key-product
-// accumulators live in tensor memory, so that a half of up to 16,384 points and its
-// transform fit one CTA (the shared memory holds the transform only).
-template <int LOGN> struct ModUpShape {
-    static constexpr int LOGH = LOGN - 1;
+// ModUp works on parts of H = N / SPLIT evaluation points of a target limb (SPLIT = 2 or 4):
+// the first log2 SPLIT Cooley-Tukey stages are done in the load (each CTA reads SPLIT points of
+// the digit per output point) and the key-product accumulators live in tensor memory, so that a
+// part of up to 16,384 points and its transform fit one CTA (the shared memory holds the
+// transform only).
+template <int LOGN, int SPLIT> struct ModUpShape {
+    static_assert(SPLIT == 2 || SPLIT == 4, "ModUp splits a limb in halves or quarters");
+    static constexpr int LOGS = SPLIT == 4 ? 2 : 1;
+    static constexpr int LOGH = LOGN - LOGS;
     static constexpr int H = 1 << LOGH;
-    // 256 threads where two CTAs fit an SM's shared memory (their barriers then overlap)
-    static constexpr int NT = LOGH == 13 ? 256 : nt_for(LOGH);
-    static constexpr int MINB = LOGH == 13 ? 2 : 1;
+    // halves: 256 threads where two CTAs fit an SM's shared memory (their barriers then
+    // overlap); quarters: 128 threads (four CTAs per SM at N = 16384)
+    static constexpr int NT = SPLIT == 2 ? (LOGH == 13 ? 256 : nt_for(LOGH)) : (LOGH >= 13 ? 256 : 128);
     static constexpr int PTS = H / NT;               // points per thread
     static constexpr unsigned COLS = H / 32;         // 4 cells per point over 128 lanes
-    static constexpr size_t smem = sizeof(u64) * PadSize<H>::value + 16;   // + the TMEM base address
+    static constexpr int PER_SM = 512 / (int)COLS;   // CTAs whose accumulators fit one SM's tensor memory
+    // resident CTAs per SM the registers are budgeted for (128 per thread): no more than the
+    // tensor memory holds
+    static constexpr int MINB = PER_SM < 512 / NT ? PER_SM : 512 / NT;
+    static constexpr size_t need = sizeof(u64) * PadSize<H>::value + 16;   // + the TMEM base address
+    // shared memory large enough that no more CTAs share an SM than its tensor memory holds
+    // (a further CTA would only wait in tcgen05.alloc): 228 KB per SM, 1 KB reserved per CTA
+    static constexpr size_t floor_ = (size_t)228 * 1024 / (PER_SM + 1) - 1024 + 16;
+    static constexpr size_t smem = need > floor_ ? need : floor_;
     static_assert(PTS % 4 == 0 && COLS >= 32 && COLS <= 512 && (COLS & (COLS - 1)) == 0, "ModUp TMEM layout");
+    static_assert(smem <= 227 * 1024, "ModUp shared memory");
 };
 
 // Accumulators in tensor memory: thread t of warp w owns the points p = t + e NT (e < PTS) and
 // keeps them in lane 32 (w % 4) + t % 32, columns 4 PTS (w / 4) + 4 e + {0, 1, 2, 3} = (acc0 low,
 // acc0 high, acc1 low, acc1 high). tacc is the warp's address of its first column.
-// acc_c[p] += v(p) * key_c[p], four points per TMEM access, key loads issued first. The sums
-// are not reduced: L products below 2q each stay below 2 L q <= 30q < 2^64 (reduced at the end).
-template <int H, int NT, class Val>
+// acc_c[p] += v(p) * key_c[p] (+ x0(p) for acc0 when EXTRA), four points per TMEM access, key
+// loads issued first. The sums are not reduced: L products below 2q each plus an addend below
+// 2q stay below 2 (L + 1) q <= 32q < 2^64 (reduced at the end).
+template <int H, int NT, bool EXTRA, class Val>
 __device__ __forceinline__ void key_mac(u32 tacc, const shoup_t *__restrict__ k0, const shoup_t *__restrict__ k1,
                                         u64 q, Val val) {
     constexpr int PTS = H / NT;
 #pragma unroll 1
     for (int e0 = 0; e0 < PTS; e0 += 4) {
-        u64 v[4];
+        u64 v[4], x0[4];
         shoup_t a[4], b[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int p = threadIdx.x + (e0 + e) * NT;
             a[e] = __ldg(k0 + p);
             b[e] = __ldg(k1 + p);
-            v[e] = val(p);
+            val(p, v[e], x0[e]);
         }
         u32 r[16];
         tmem_ld16(tacc + 4u * e0, r);
         tmem_wait_ld();
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
-            const u64 s0 = (((u64)r[4 * e + 1] << 32) | r[4 * e]) + mul_shoup(v[e], a[e], q);
+            u64 s0 = (((u64)r[4 * e + 1] << 32) | r[4 * e]) + mul_shoup(v[e], a[e], q);
+            if constexpr (EXTRA) s0 += x0[e];
             const u64 s1 = (((u64)r[4 * e + 3] << 32) | r[4 * e + 2]) + mul_shoup(v[e], b[e], q);
             r[4 * e] = (u32)s0;
             r[4 * e + 1] = (u32)(s0 >> 32);
@@ -158,19 +161,20 @@ __device__ __forceinline__ void key_mac(u32 tacc, const shoup_t *__restrict__ k0
     tmem_wait_st();
 }
 
-// grid.x = (g, j, h): U[g][c][j][h H + p] = sum_i NTT_j(D[g][i] mod q_j)[h H + p] * key[i][c][j].
-// The digit of index j itself is sigma(C1[g][j]) in evaluation form already (a permuted read).
-template <int LOGN>
-__global__ void __launch_bounds__(ModUpShape<LOGN>::NT, ModUpShape<LOGN>::MINB) k_ks_modup(const ModTab *__restrict__ mods, int L, u32 gal,
-                                                                  const u64 *__restrict__ C, const u64 *__restrict__ D,
-                                                                  const shoup_t *__restrict__ key, u64 *U) {
+// grid.x = (g, j, h): U[g][c][j][h H + p] = sum_i NTT_j(D[g][i] mod q_j)[h H + p] * key[i][c][j],
+// and for j < L also U[g][0][j] += P sigma(C0[g][j]). The digit of index j itself is
+// sigma(C1[g][j]) in evaluation form already (a permuted read, shared with that of C0).
+template <int LOGN, int SPLIT>
+__global__ void __launch_bounds__(ModUpShape<LOGN, SPLIT>::NT, ModUpShape<LOGN, SPLIT>::MINB)
+    k_ks_modup(const ModTab *__restrict__ mods, int L, u32 gal, const u64 *__restrict__ C, const u64 *__restrict__ D,
+               const shoup_t *__restrict__ key, u64 *U) {
     extern __shared__ u64 sm[];
-    using MS = ModUpShape<LOGN>;
+    using MS = ModUpShape<LOGN, SPLIT>;
     constexpr int N = 1 << LOGN, H = MS::H, NT = MS::NT, PTS = MS::PTS;
     u32 *tslot = (u32 *)(sm + PadSize<H>::value);
     const int nqp = L + 1;
-    const int h = blockIdx.x % 2, j = (blockIdx.x / 2) % nqp;
-    const size_t g = blockIdx.x / (2 * nqp);
+    const int h = blockIdx.x % SPLIT, j = (blockIdx.x / SPLIT) % nqp;
+    const size_t g = blockIdx.x / (SPLIT * nqp);
     const ModTab T = mods[j];
     const u64 q = T.q;
     const int warp = threadIdx.x >> 5;
@@ -194,19 +198,26 @@ __global__ void __launch_bounds__(ModUpShape<LOGN>::NT, ModUpShape<LOGN>::MINB) 
         const shoup_t *k0 = key + ((size_t)i * 2 + 0) * keystride + (size_t)j * N + (size_t)h * H;
         const shoup_t *k1 = key + ((size_t)i * 2 + 1) * keystride + (size_t)j * N + (size_t)h * H;
         if (i == j) {
+            const u64 *c0 = C + ((g * 2 + 0) * L + j) * (size_t)N;
             const u64 *c1 = C + ((g * 2 + 1) * L + j) * (size_t)N;
-            key_mac<H, NT>(tacc, k0, k1, q, [&](int p) { return c1[auto_src(h * H + p, gal, LOGN)]; });
+            key_mac<H, NT, true>(tacc, k0, k1, q, [&](int p, u64 &v, u64 &x0) {
+                const int src = auto_src(h * H + p, gal, LOGN);
+                v = c1[src];
+                x0 = mul_shoup(c0[src], T.pmod, T.pmodp, q);
+            });
         } else {
             const u64 *d = D + (g * L + i) * (size_t)N;   // digit i < q_i < 2 q_j
-            ntt_forward_lazy<MS::LOGH, NT, LOGN == 14>(   // outputs feed Shoup products only
-                sm, T, 1, h,
+            ntt_forward_lazy<MS::LOGH, NT, LOGN == 14 && SPLIT == 2>(   // outputs feed Shoup products only
+                sm, T, MS::LOGS, h,
                 [&](int p) {
-                    u64 v[2] = {d[p], d[p + H]};
-                    return fold_stages<1>(T, h, v);
+                    u64 v[SPLIT];
+#pragma unroll
+                    for (int k = 0; k < SPLIT; ++k) v[k] = d[p + k * H];
+                    return fold_stages<MS::LOGS>(T, h, v);
                 },
                 [&](int p, u64 v) { sm[padi(p)] = v; });
             __syncthreads();
-            key_mac<H, NT>(tacc, k0, k1, q, [&](int p) { return sm[padi(p)]; });
+            key_mac<H, NT, false>(tacc, k0, k1, q, [&](int p, u64 &v, u64 &) { v = sm[padi(p)]; });
             __syncthreads();
         }
     }
@@ -248,19 +259,18 @@ LIMB_KERNEL_M(LOGN, MODE) k_ks_moddown_p(const ModTab *__restrict__ mods, int L,
 
 // Limb unit (g, c, l): C[g][c][l] += (U[g][c][l] + NTT_l(floor(P/2) - r)) * P^-1. Split mode 1:
 // two 256-thread CTAs per limb at N = 16384 (the first stage folded into the loads).
-constexpr int kModDownMode = 1;
-template <int LOGN>
-LIMB_KERNEL_M(LOGN, kModDownMode) k_ks_moddown(const ModTab *__restrict__ mods, int L, const u64 *__restrict__ U,
-                                               const u64 *__restrict__ R, u64 *C) {
+template <int LOGN, int MODE>
+LIMB_KERNEL_M(LOGN, MODE) k_ks_moddown(const ModTab *__restrict__ mods, int L, const u64 *__restrict__ U,
+                                       const u64 *__restrict__ R, u64 *C) {
     extern __shared__ u64 sm[];
-    LIMB_INDEX_M(LOGN, kModDownMode);
-    constexpr int NT = Split<LOGN, kModDownMode>::NT;
+    LIMB_INDEX_M(LOGN, MODE);
+    constexpr int NT = Split<LOGN, MODE>::NT;
     const int nqp = L + 1;
     const int l = (int)(unit % L), c = (int)((unit / L) % 2);
     const size_t g = unit / (2 * L);
     const ModTab T = mods[l];
     const u64 *r = R + (g * 2 + c) * (size_t)N;
-    limb_forward<LOGN, true, kModDownMode>(sm, T, h, [&](int p) { return T.phalf + (T.q - red1(r[p], T.q)); },
+    limb_forward<LOGN, true, MODE>(sm, T, h, [&](int p) { return T.phalf + (T.q - red1(r[p], T.q)); },
                        [&](int p, u64 v) { sm[padi(p & (M - 1))] = v; });
     __syncthreads();
     const u64 *u = U + ((g * 2 + c) * nqp + l) * (size_t)N + (size_t)h * M;
@@ -354,6 +364,63 @@ LIMB_KERNEL(LOGN) k_intt_copy(const ModTab *__restrict__ mods, int L, const u64 
 
 int last_err() { return cudaGetLastError() == cudaSuccess ? BFV_OK : BFV_ERR_CUDA; }
 
+// One ModUp launch over ng pairs with limbs split in SPLIT parts.
+template <int LOGN, int SPLIT>
+void launch_modup(const bfv_ctx *c, size_t ng, u32 gal, const u64 *C, const u64 *D, const shoup_t *key, u64 *U,
+                  cudaStream_t st) {
+    using MS = ModUpShape<LOGN, SPLIT>;
+    set_smem(k_ks_modup<LOGN, SPLIT>, MS::smem);
+    k_ks_modup<LOGN, SPLIT><<<(unsigned)(ng * c->nqp * SPLIT), MS::NT, MS::smem, st>>>(c->dmods, c->L, gal, C, D, key, U);
+}
+
+// The four kernels of one key switch (rotation by gal) for the ng pairs of a chunk, each split
+// as the schedule says. Splits of two CTAs per limb exist at N = 16384 only (at N = 32768 every
+// limb already runs on a two-CTA cluster, smaller rings use one CTA per limb).
+template <int LOGN>
+void ks_step(const bfv_ctx *c, const bfv_packed_schedule &sc, size_t ng, u32 gal, const shoup_t *key, u64 *C, u64 *D,
+             u64 *U, u64 *R, cudaStream_t st) {
+    const int L = c->L;
+    constexpr bool PAIRS = LOGN == 14;
+    {
+        ProfScope pr(c, BFV_K_KS_PREP, st);
+        if constexpr (PAIRS) {
+            if (sc.prep_split == 2) launch_limbs<LOGN, 1>(k_ks_prep<LOGN, 1>, ng * L, st, 0, c->dmods, L, gal, (const u64 *)C, D);
+            else launch_limbs<LOGN, 0>(k_ks_prep<LOGN, 0>, ng * L, st, 0, c->dmods, L, gal, (const u64 *)C, D);
+        } else {
+            launch_limbs<LOGN, 0>(k_ks_prep<LOGN, 0>, ng * L, st, 0, c->dmods, L, gal, (const u64 *)C, D);
+        }
+    }
+    {
+        ProfScope pr(c, BFV_K_KS_MODUP, st);
+        if (sc.modup_split == 4) launch_modup<LOGN, 4>(c, ng, gal, C, D, key, U, st);
+        else launch_modup<LOGN, 2>(c, ng, gal, C, D, key, U, st);
+    }
+    {
+        // two limbs per pair leave most SMs idle on small chunks: by default split each over two
+        // CTAs there (measured: 41 -> 33 us per launch at 16 pairs; slower on full chunks)
+        ProfScope pr(c, BFV_K_KS_MODDOWN_P, st);
+        const bool two = sc.moddown_p_split == 2 || (sc.moddown_p_split == 0 && ng * 2 < (size_t)2 * c->sms);
+        if constexpr (PAIRS) {
+            if (two) launch_limbs<LOGN, 1>(k_ks_moddown_p<LOGN, 1>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R);
+            else launch_limbs<LOGN, 0>(k_ks_moddown_p<LOGN, 0>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R);
+        } else {
+            (void)two;
+            launch_limbs<LOGN, 0>(k_ks_moddown_p<LOGN, 0>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R);
+        }
+    }
+    {
+        ProfScope pr(c, BFV_K_KS_MODDOWN, st);
+        if constexpr (PAIRS) {
+            if (sc.moddown_split == 1)
+                launch_limbs<LOGN, 0>(k_ks_moddown<LOGN, 0>, ng * 2 * L, st, 0, c->dmods, L, (const u64 *)U, (const u64 *)R, C);
+            else launch_limbs<LOGN, 1>(k_ks_moddown<LOGN, 1>, ng * 2 * L, st, 0, c->dmods, L, (const u64 *)U, (const u64 *)R, C);
+        } else {
+            launch_limbs<LOGN, 0>(k_ks_moddown<LOGN, 0>, ng * 2 * L, st, 0, c->dmods, L, (const u64 *)U, (const u64 *)R, C);
+        }
+    }
+    count_launch(c, 4);
+}
+
 template <int LOGN>
 int run_packed(const bfv_ctx *c, const bfv_keys *k, int nreq, const u64 *const *X_ct, u64 *const *Y_ct, char *ws,
                const PackedPlan &pl, cudaStream_t st) {
@@ -362,8 +429,6 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, int nreq, const u64 *const *
     const size_t ctw = 2 * (size_t)L * N;
     u64 *Xe = (u64 *)(ws + pl.off_xntt), *Yacc = (u64 *)(ws + pl.off_yacc), *C = (u64 *)(ws + pl.off_state);
     u64 *D = (u64 *)(ws + pl.off_digits), *U = (u64 *)(ws + pl.off_u), *R = (u64 *)(ws + pl.off_r);
-    using MS = ModUpShape<LOGN>;
-    set_smem(k_ks_modup<LOGN>, MS::smem);
 
     int rc;
     if (cudaMemsetAsync(Yacc, 0, pl.nout * ctw * sizeof(u64), st) != cudaSuccess) return BFV_ERR_CUDA;
@@ -385,24 +450,8 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, int nreq, const u64 *const *
         { ProfScope pr(c, BFV_K_MAC, st);
         k_mac<<<dim3((unsigned)(ng * 2 * L), (unsigned)((N + 1023) / 1024)), 256, 0, st>>>(c->dmods, N, L, g0, rt, Xe, C); }
         count_launch(c);
-        for (int s = 0; s < k->ng; ++s) {
-            const u32 gal = (u32)c->galois[s];
-            const shoup_t *key = k->gk_eval + (size_t)s * keyblock;
-            { ProfScope pr(c, BFV_K_KS_PREP, st);
-              launch_limbs<LOGN, 0>(k_ks_prep<LOGN, 0>, ng * 2 * L, st, 0, c->dmods, L, gal, C, D); }
-            { ProfScope pr(c, BFV_K_KS_MODUP, st);
-              k_ks_modup<LOGN><<<(unsigned)(ng * nqp * 2), MS::NT, MS::smem, st>>>(c->dmods, L, gal, C, D, key, U); }
-            // two limbs per pair leave most SMs idle on small chunks: split each over two CTAs
-            // there (measured: 41 -> 33 us per launch at 16 pairs; slower on full chunks)
-            { ProfScope pr(c, BFV_K_KS_MODDOWN_P, st);
-              if (ng * 2 < (size_t)2 * c->sms)
-                  launch_limbs<LOGN, 1>(k_ks_moddown_p<LOGN, 1>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R);
-              else launch_limbs<LOGN, 0>(k_ks_moddown_p<LOGN, 0>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R); }
-            { ProfScope pr(c, BFV_K_KS_MODDOWN, st);
-              launch_limbs<LOGN, kModDownMode>(k_ks_moddown<LOGN>, ng * 2 * L, st, 0, c->dmods, L, (const u64 *)U,
-                                               (const u64 *)R, C); }
-            count_launch(c, 4);
-        }
+        for (int s = 0; s < k->ng; ++s)
+            ks_step<LOGN>(c, pl.sched, ng, (u32)c->galois[s], k->gk_eval + (size_t)s * keyblock, C, D, U, R, st);
         { ProfScope pr(c, BFV_K_BIAS_MASK, st);
         launch_limbs<LOGN>(k_bias_mask<LOGN>, ng * L, st, 0, c->dmods, L, nqp, g0, rt, (const u32 *)c->dmaskpow, C); }
         count_launch(c);
@@ -430,8 +479,36 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, int nreq, const u64 *const *
 
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
+bfv_packed_schedule default_schedule() {
+    bfv_packed_schedule s{};
+    s.pair_chunk = 2048;
+    s.prep_split = 1;
+    s.modup_split = 2;
+    s.moddown_p_split = 0;
+    s.moddown_split = 2;
+    return s;
+}
+
+bool schedule_ok(const bfv_packed_schedule &s) {
+    return s.pair_chunk >= 1 && (s.prep_split == 1 || s.prep_split == 2) &&
+           (s.modup_split == 2 || s.modup_split == 4) && s.moddown_p_split <= 2 &&
+           (s.moddown_split == 1 || s.moddown_split == 2);
+}
+
+bfv_packed_schedule schedule_for(const bfv_ctx *c, size_t npairs, size_t chunk) {
+    bfv_packed_schedule s = default_schedule();
+    {
+        std::lock_guard<std::mutex> g(c->tune_mu);
+        auto it = c->tuned.find(npairs);
+        if (it == c->tuned.end()) it = c->tuned.find(0);
+        if (it != c->tuned.end()) s = it->second;
+    }
+    if (chunk) s.pair_chunk = chunk;
+    return s;
+}
+
 PackedPlan packed_plan_models(const bfv_ctx *c, int nreq, const bfv_model *const *models, const size_t *nXs,
-                              size_t chunk) {
+                              size_t chunk, const bfv_packed_schedule *sched) {
     PackedPlan p{};
     const size_t N = c->N, L = c->L, nqp = c->nqp;
     p.nreq = nreq;
@@ -457,12 +534,9 @@ PackedPlan packed_plan_models(const bfv_ctx *c, int nreq, const bfv_model *const
     p.nX = nreq == 1 ? nXs[0] : 0;
     p.npairs = pairs;
     p.nout = outs;
-    if (!chunk) {
-        std::lock_guard<std::mutex> g(c->tune_mu);
-        auto it = c->tuned_chunk.find(p.npairs);
-        chunk = it != c->tuned_chunk.end() ? it->second : 2048;
-    }
-    p.chunk = std::max<size_t>(1, std::min(chunk, p.npairs));
+    p.sched = sched ? *sched : schedule_for(c, p.npairs, chunk);
+    p.chunk = std::max<size_t>(1, std::min<size_t>(p.sched.pair_chunk, p.npairs));
+    p.sched.pair_chunk = p.chunk;
     for (size_t g0 = 0; g0 < p.npairs; g0 += p.chunk) {
         size_t cts = 0;
         for (int r = 0; r < nreq; ++r) {
@@ -484,14 +558,15 @@ PackedPlan packed_plan_models(const bfv_ctx *c, int nreq, const bfv_model *const
     return p;
 }
 
-PackedPlan packed_plan_multi(const bfv_ctx *c, const bfv_model *m, int nreq, const size_t *nXs, size_t chunk) {
+PackedPlan packed_plan_multi(const bfv_ctx *c, const bfv_model *m, int nreq, const size_t *nXs, size_t chunk,
+                             const bfv_packed_schedule *sched) {
     const bfv_model *ms[kMaxReq];
     for (int r = 0; r < nreq; ++r) ms[r] = m;
-    return packed_plan_models(c, nreq, ms, nXs, chunk);
+    return packed_plan_models(c, nreq, ms, nXs, chunk, sched);
 }
 
-PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t chunk) {
-    return packed_plan_multi(c, m, 1, &nX, chunk);
+PackedPlan packed_plan(const bfv_ctx *c, const bfv_model *m, size_t nX, size_t chunk, const bfv_packed_schedule *sched) {
+    return packed_plan_multi(c, m, 1, &nX, chunk, sched);
 }
 
 int launch_packed_multi(const bfv_ctx *c, const bfv_keys *k, int nreq, const u64 *const *X_ct, u64 *const *Y_ct,

@@ -222,12 +222,15 @@ __global__ void k_enc_sample(const u64 *__restrict__ cdt, int cdt_len, u64 seed,
 // Limb unit (c, l): both components of ciphertext c on limb l from one transform of u:
 // comp 0 -> pk0 u + e1 + Delta m, comp 1 -> pk1 u + e2. The product pk1 u waits in comp 1's
 // output limb (evaluation form) while comp 0 is inverted; the second inverse reads it in its
-// first pass and overwrites it only in its last.
-template <int LOGN>
-LIMB_KERNEL(LOGN) k_enc_main(const ModTab *__restrict__ mods, int L, const shoup_t *__restrict__ pk,
-                             const int8_t *__restrict__ rnd, const u64 *__restrict__ pt, u64 *ct) {
+// first pass and overwrites it only in its last. With two CTAs per limb (MODE 1 at N = 16384,
+// every N = 32768 limb) CTA h owns evaluation positions and coefficients [h M, (h+1) M): it
+// writes and re-reads only its own half of comp 1's limb, and each inverse ends with a cluster
+// barrier after the partner's last read of its shared memory.
+template <int LOGN, int MODE>
+LIMB_KERNEL_M(LOGN, MODE) k_enc_main(const ModTab *__restrict__ mods, int L, const shoup_t *__restrict__ pk,
+                                     const int8_t *__restrict__ rnd, const u64 *__restrict__ pt, u64 *ct) {
     extern __shared__ u64 sm[];
-    LIMB_INDEX(LOGN);
+    LIMB_INDEX_M(LOGN, MODE);
     const int l = (int)(unit % L);
     const size_t c = unit / L;
     const ModTab T = mods[l];
@@ -235,18 +238,18 @@ LIMB_KERNEL(LOGN) k_enc_main(const ModTab *__restrict__ mods, int L, const shoup
     const shoup_t *k0 = pk + (size_t)l * N, *k1 = pk + ((size_t)L + l) * N;
     const u64 *m = pt + c * N;
     u64 *out0 = ct + ((c * 2 + 0) * L + l) * (size_t)N, *out1 = ct + ((c * 2 + 1) * L + l) * (size_t)N;
-    limb_forward<LOGN, true>(sm, T, h, [&](int p) { return lift_small(u[p], T.q); }, [&](int p, u64 v) {
+    limb_forward<LOGN, true, MODE>(sm, T, h, [&](int p) { return lift_small(u[p], T.q); }, [&](int p, u64 v) {
         sm[padi(p & (M - 1))] = mul_shoup(v, k0[p], T.q);
         out1[p] = mul_shoup(v, k1[p], T.q);
     });
     __syncthreads();
-    limb_inverse<LOGN>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) {
+    limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) {
         const u64 r = add_mod(v, lift_small(e1[p], T.q), T.q);
         out0[p] = add_mod(r, mul_barrett(T.delta, m[p] % T.q, T.q, T.mu, T.bits), T.q);
     });
     __syncthreads();
-    limb_inverse<LOGN>(sm, T, h, [&](int p) { return out1[p]; },
-                       [&](int p, u64 v) { out1[p] = add_mod(v, lift_small(e2[p], T.q), T.q); });
+    limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return out1[p]; },
+                             [&](int p, u64 v) { out1[p] = add_mod(v, lift_small(e2[p], T.q), T.q); });
 }
 
 // ------------------------------------------------------------------ decryption
@@ -520,9 +523,13 @@ int launch_encrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *pt, size_t co
     const size_t total = count * c->N;
     if (!total) return BFV_OK;
     k_enc_sample<<<(unsigned)((total + 255) / 256), 256, 0, st>>>(c->dcdt, c->cdt_len, seed, obj0, c->N, total, rnd);
-#define L_(LG) launch_limbs<LG>(k_enc_main<LG>, count * c->L, st, 0, c->dmods, c->L, (const shoup_t *)k->pk_eval, \
+#define L_(LG) launch_limbs<LG>(k_enc_main<LG, 0>, count * c->L, st, 0, c->dmods, c->L, (const shoup_t *)k->pk_eval, \
                                 (const int8_t *)rnd, pt, ct)
-    DISPATCH_LOGN(c, L_)
+    if (c->logN == 14 && c->enc_split == 2)
+        launch_limbs<14, 1>(k_enc_main<14, 1>, count * c->L, st, 0, c->dmods, c->L, (const shoup_t *)k->pk_eval,
+                            (const int8_t *)rnd, pt, ct);
+    else
+        DISPATCH_LOGN(c, L_)
 #undef L_
     count_launch(c, 2);
     return last_err();
@@ -596,32 +603,24 @@ int launch_crt_combine(const int64_t *r0, u64 t0, const int64_t *r1, u64 t1, u64
 //
 // bfv_decrypt_noalloc: decryption whose scratch (the per-limb residues [c0 + c1 s]_{q_l})
 // lives in a fixed device array owned by this file instead of a caller workspace, for
-// callers that must not call cudaMalloc at all. The array is resolved to a device address
-// once per device with cudaGetSymbolAddress (host code cannot pass the symbol itself).
-
-#include <mutex>
+// callers that must not call cudaMalloc at all. Host code cannot pass the array's symbol to a
+// kernel (on the host it names a stand-in, not device memory): its device address is resolved
+// with cudaGetSymbolAddress when a context is created (bfv_setup, the context's device current)
+// and kept in the context, so a context made after a device reset resolves it afresh.
 
 namespace {
 
 constexpr size_t kNoAllocScratchBytes = 4u << 20;   // 4 MiB, held by every device that loads the library
 static __device__ __align__(256) u64 g_noalloc_scratch[kNoAllocScratchBytes / sizeof(u64)];
 
-std::mutex g_noalloc_mu;
-u64 *g_noalloc_ptr[128] = {};   // device address of g_noalloc_scratch, per device ordinal
+}  // namespace
 
-int noalloc_scratch(int device, u64 **out) {
-    if (device < 0 || device >= 128) return BFV_ERR_INVALID_ARG;
-    std::lock_guard<std::mutex> g(g_noalloc_mu);
-    if (!g_noalloc_ptr[device]) {
-        void *p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return BFV_ERR_CUDA;
-        g_noalloc_ptr[device] = (u64 *)p;
-    }
-    *out = g_noalloc_ptr[device];
+int noalloc_scratch_address(u64 **out) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return BFV_ERR_CUDA;
+    *out = (u64 *)p;
     return BFV_OK;
 }
-
-}  // namespace
 
 extern "C" int bfv_decrypt_noalloc(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *ct, size_t count, uint64_t *pt,
                                    uintptr_t stream) {
@@ -632,11 +631,11 @@ extern "C" int bfv_decrypt_noalloc(bfv_ctx *ctx, const bfv_keys *keys, const uin
     int dev = -1;
     if (cudaGetDevice(&dev) != cudaSuccess) return BFV_ERR_CUDA;
     if (dev != ctx->device) return BFV_ERR_INVALID_ARG;
-    u64 *x = nullptr;
-    int rc = noalloc_scratch(dev, &x);
-    if (rc) return rc;
+    u64 *x = ctx->noalloc_scratch;
+    if (!x) return BFV_ERR_CUDA;
     const bfv_ctx *c = ctx;
     cudaStream_t st = (cudaStream_t)stream;
+    ProfScope prof_(c, BFV_K_DECRYPT, st);
     // every scratch word k_dec_round reads is written by k_dec_inner in the same call
 #define L_(LG) launch_limbs<LG>(k_dec_inner<LG>, count * c->L, st, 0, c->dmods, c->L, (const shoup_t *)keys->sk_eval, \
                                 (const u64 *)ct, x)

@@ -14,8 +14,13 @@ output ciphertexts. The server keeps the Galois keys and the encoded models resi
   * with `small_pairs` > 0, keeps two classes: requests of at most `small_pairs` pairs are
     fused and launched on a high-priority stream of their own, so a single-individual request
     is not held behind a large batch (the GPU block scheduler prefers its CTAs);
+  * orders every launch after the work that produced its inputs: a request records an event on
+    the submitting thread's current stream, and the launch's stream waits for it (the inputs
+    may still be being encrypted or copied there);
   * detects completion from CUDA events and reports per-request latency (arrival to the end
-    of its product) with p50/p99 and predictions/s.
+    of its product) with p50/p99 and predictions/s, and each launch's device interval (events
+    recorded on its stream before and after the product), which shows whether launches on
+    different streams overlapped on the device.
 
 Every request's output is bit-identical to running it alone (the fused product computes each
 pair exactly as the single-request call does).
@@ -37,6 +42,7 @@ class Request:
     out: object = None           # device tensor of output ciphertexts, set at launch
     t_done: float | None = None  # seconds on the server clock, set at completion
     batch: int = -1
+    ready: object = None         # CUDA event: the inputs are written (recorded at submission)
 
     @property
     def nX(self) -> int:
@@ -62,7 +68,8 @@ class Server:
         else:
             self.streams = [torch.cuda.Stream() for _ in range(n_streams)]
             self.classes = [None] * n_streams
-        self.busy = [None] * n_streams          # (event, requests, ws bytes, ws) per stream
+        self.busy = [None] * n_streams          # (end event, requests, ws bytes, ws, start event, batch) per stream
+        self.intervals: list[dict] = []         # device interval of every finished launch
         self.waiting: list[Request] = []
         self.done: list[Request] = []
         self.in_flight_bytes = 0
@@ -85,6 +92,8 @@ class Server:
         if not 0 <= model < len(self.models):
             raise ValueError(f"request {rid} names model {model}; the server holds {len(self.models)}")
         r = Request(rid, X_ct, self.now() if t_arrival is None else t_arrival, model)
+        r.ready = self.torch.cuda.Event()
+        r.ready.record(self.torch.cuda.current_stream(X_ct.device))
         self.waiting.append(r)
         return r
 
@@ -97,11 +106,13 @@ class Server:
     def _retire(self):
         for s, b in enumerate(self.busy):
             if b is not None and b[0].query():
-                ev, reqs, nbytes, _ = b
+                ev, reqs, nbytes, _, ev0, bt = b
                 t = self.t0_event.elapsed_time(ev) / 1e3
                 for r in reqs:
                     r.t_done = t
                     self.done.append(r)
+                self.intervals.append({"batch": bt, "stream": s, "start_s": self.t0_event.elapsed_time(ev0) / 1e3,
+                                       "end_s": t, "requests": [r.rid for r in reqs]})
                 self.in_flight_bytes -= nbytes
                 self.busy[s] = None
 
@@ -131,6 +142,11 @@ class Server:
             nbytes = self._ws_bytes(take)
             stream = self.streams[s]
             with torch.cuda.stream(stream):
+                for r in take:                  # the inputs' producers come first
+                    if r.ready is not None:
+                        stream.wait_event(r.ready)
+                ev0 = torch.cuda.Event(enable_timing=True)
+                ev0.record(stream)
                 ws = torch.empty(nbytes, dtype=torch.uint8, device=f"cuda:{self.ctx.device}")
                 outs = self.ctx.lr_scores_packed_models(self.keys, [self.models[r.model] for r in take],
                                                         [r.X_ct for r in take], ws=ws, pair_chunk=self.pair_chunk,
@@ -139,11 +155,14 @@ class Server:
                 ev.record(stream)
             for r, o in zip(take, outs):
                 r.out, r.batch = o, self.nbatches
+                # the inputs were allocated on another stream: keep their memory from being reused
+                # before this stream has read them, even if the caller drops its reference
+                r.X_ct.record_stream(stream)
             self.nbatches += 1
             taken = set(id(r) for r in take)
             self.waiting = [r for r in self.waiting if id(r) not in taken]
             self.in_flight_bytes += nbytes
-            self.busy[s] = (ev, take, nbytes, ws)
+            self.busy[s] = (ev, take, nbytes, ws, ev0, self.nbatches - 1)
             self.max_concurrent = max(self.max_concurrent, sum(x is not None for x in self.busy))
 
     def step(self):

@@ -90,6 +90,33 @@ def test_server_overlaps_a_second_batch_with_the_first(env):
     for r in first + late:
         assert r.t_done is not None
         assert torch.equal(r.out, _alone(ctx, keys, model, r.X_ct))
+    # the two launches' device intervals (events recorded on each stream before and after its
+    # product) intersect: the second batch began on the device before the first had finished
+    iv = sorted(srv.intervals, key=lambda d: d["batch"])
+    assert len(iv) == 2 and iv[0]["stream"] != iv[1]["stream"]
+    assert iv[1]["start_s"] < iv[0]["end_s"] and iv[0]["start_s"] < iv[1]["end_s"]
+
+
+def test_server_waits_for_inputs_encrypted_on_another_stream(env):
+    """make_inputs encrypts on the default stream and returns without synchronising: each
+    launch must wait for that work (an event recorded at submission), so every result is still
+    the single-request product of the finished ciphertexts."""
+    from paper_2204_05496_gb300 import serve
+    bfv, ctx, keys, model, X, W, b, X_ct = env
+    sizes = [3, 1, 5, 1, 2, 6]
+    starts = np.cumsum([0] + sizes)
+    Xd = torch.from_numpy(X).cuda()
+
+    def make_inputs(k, n):
+        pt = ctx.encode_features(Xd[starts[k]:starts[k] + n])
+        return ctx.encrypt(keys, pt.reshape(-1, ctx.N), seed=5, obj0=int(starts[k])).reshape(n, 1, 2, ctx.L, ctx.N)
+
+    srv = serve.Server(ctx, keys, model, hbm_budget_bytes=8 << 30, n_streams=2)
+    done = srv.run([(0.0, n) for n in sizes], make_inputs)
+    for r in done:
+        n = sizes[r.rid]
+        assert torch.equal(r.X_ct, X_ct[starts[r.rid]:starts[r.rid] + n])   # the same encryptions
+        assert torch.equal(r.out, _alone(ctx, keys, model, X_ct[starts[r.rid]:starts[r.rid] + n]))
 
 
 def test_server_priority_classes_keep_results(env):

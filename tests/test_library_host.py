@@ -155,15 +155,17 @@ def test_product_code_never_touches_the_oracle():
         assert "oracle" not in open(os.path.join(ROOT, "include", f)).read()
 
 
-@pytest.mark.parametrize("logn", [12, 13, 14, 15])
-def test_modup_tensor_memory_layout_is_a_partition(logn):
+@pytest.mark.parametrize("logn,split", [(lg, sp) for lg in (12, 13, 14, 15) for sp in (2, 4)])
+def test_modup_tensor_memory_layout_is_a_partition(logn, split):
     """ModUp's key sums in tensor memory: thread t of warp w owns points t + e NT (e < PTS) and
     keeps each in lane 32 (w % 4) + t % 32, columns 4 PTS (w / 4) + 4 e .. + 3. For every ring
     the cells of all threads must tile the allocation (128 lanes x H/32 columns, a power of two
     in 32..512) exactly once, every point must be owned once, and a warp's accesses (16 columns
     at a time) must stay inside its 32-lane quarter and the allocation."""
-    H = 1 << (logn - 1)
-    nt = {11: 128, 12: 256, 13: 256, 14: 512}[logn - 1]     # threads per ModUp CTA
+    logh = logn - (1 if split == 2 else 2)
+    H = 1 << logh
+    # threads per ModUp CTA: halves as before, quarters 256 from 8,192 points up, else 128
+    nt = {11: 128, 12: 256, 13: 256, 14: 512}[logh] if split == 2 else (256 if logh >= 13 else 128)
     pts, cols = H // nt, H // 32
     assert pts % 4 == 0 and 32 <= cols <= 512 and cols & (cols - 1) == 0
     cells, points = set(), set()

@@ -27,6 +27,10 @@ class FakeEvent:
 class FakeStream:
     def __init__(self, priority=0):
         self.priority = priority
+        self.waited = []
+
+    def wait_event(self, ev):
+        self.waited.append(ev)
 
     @staticmethod
     def priority_range():
@@ -51,8 +55,14 @@ class _Ctx:
 
 
 class _X:
+    device = "cuda:0"
+
     def __init__(self, n):
         self.shape = (n,)
+        self.recorded_on = []
+
+    def record_stream(self, s):
+        self.recorded_on.append(s)
 
 
 @pytest.fixture
@@ -61,9 +71,15 @@ def fake_torch():
         Stream = FakeStream
         Event = FakeEvent
 
+        producer = FakeStream()
+
         @staticmethod
         def synchronize():
             pass
+
+        @staticmethod
+        def current_stream(device=None):
+            return _Cuda.producer
 
         @staticmethod
         def stream(s):
@@ -164,3 +180,22 @@ def test_run_gives_up_after_max_seconds(fake_torch):
     srv, _ = make(torch_never, hbm_budget_bytes=10 ** 6, n_streams=1)
     with pytest.raises(TimeoutError):
         srv.run([(0.0, 1)], lambda k, n: _X(n), poll_s=0.0001, max_seconds=0.05)
+
+
+def test_launch_waits_for_the_inputs_producer_and_holds_their_memory(fake_torch):
+    # a request records an event on the submitting thread's current stream (where its inputs may
+    # still be written); its launch stream waits for that event before the product, and the
+    # inputs are marked as used by the launch stream
+    srv, ctx = make(fake_torch, hbm_budget_bytes=10 ** 6, n_streams=2)
+    srv.start()
+    xs = [_X(1), _X(2)]
+    reqs = [srv.submit(k, x) for k, x in enumerate(xs)]
+    srv.step()
+    launched = [srv.streams[s] for s, b in enumerate(srv.busy) if b is not None]
+    assert len(launched) == 1
+    st = launched[0]
+    assert [id(e) for e in st.waited] == [id(r.ready) for r in reqs]
+    assert all(x.recorded_on == [st] for x in xs)
+    srv.step()
+    assert srv.intervals and srv.intervals[0]["requests"] == [0, 1]
+    assert {"start_s", "end_s", "stream", "batch"} <= set(srv.intervals[0])
