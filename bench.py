@@ -859,7 +859,9 @@ def run_paper8k(args):
 
 def run_only_standard(args):
     """Small profiling case: the standard product alone on the first --features features of the
-    batch (same parameters and kernels), --warmup untimed then --steps timed calls."""
+    batch (same parameters and kernels), --warmup untimed then --steps timed calls, for the
+    tensor-core and the dp4a kernel; also the encryption of the feature columns with one and with
+    two CTAs per limb."""
     import torch
     import paper_2204_05496_gb300 as bfv
     bfv.build()
@@ -871,25 +873,50 @@ def run_only_standard(args):
     ctx = bfv.Context.from_shape(w.params)
     keys = ctx.keygen(w.seed_keys)
     model = ctx.model_prepare(W, b)
-    X_ct = ctx.encrypt(keys, ctx.encode_feature_columns(torch.from_numpy(X).cuda()), seed=w.seed_enc)
-    sws = torch.empty(ctx.standard_workspace(model), dtype=torch.uint8, device="cuda")
-    Y = ctx.lr_scores_standard(model, X_ct, len(X), ws=sws)
-    for _ in range(args.warmup - 1):
-        ctx.lr_scores_standard(model, X_ct, len(X), out=Y, ws=sws)
-    torch.cuda.synchronize()
+    cols = ctx.encode_feature_columns(torch.from_numpy(X).cuda())
     a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    a.record()
-    for _ in range(args.steps):
-        ctx.lr_scores_standard(model, X_ct, len(X), out=Y, ws=sws)
-    z.record()
-    torch.cuda.synchronize()
-    ms = a.elapsed_time(z) / args.steps
-    slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
-    ok = bool(np.array_equal(slots[:, :len(X)].T, (X.astype(np.int64) @ W + b[None, :]) % w.params.t))
-    ok = ok and ctx.check_error() == 0
-    gb = args.features * 2 * L * N * 8 / 1e9
-    print(json.dumps({"case": "only-standard", "features": args.features, "ms_per_call": ms,
-                      "gb_per_s": gb / (ms / 1e3), "correct": ok}), flush=True)
+    enc = {}
+    X_ct = None
+    for split in (1, 2):
+        ctx.set_option(bfv.BFV_OPT_ENCRYPT_SPLIT, split)
+        X_ct = ctx.encrypt(keys, cols, seed=w.seed_enc, out=X_ct)
+        torch.cuda.synchronize()
+        a.record()
+        ctx.encrypt(keys, cols, seed=w.seed_enc, out=X_ct)
+        z.record()
+        torch.cuda.synchronize()
+        enc[f"split{split}"] = round(a.elapsed_time(z), 3)
+    ctx.set_option(bfv.BFV_OPT_ENCRYPT_SPLIT, 2)
+    del cols
+    sws = torch.empty(ctx.standard_workspace(model), dtype=torch.uint8, device="cuda")
+    want = (X.astype(np.int64) @ W + b[None, :]) % w.params.t
+    res = {"case": "only-standard", "features": args.features, "encrypt_ms": enc}
+    ok = True
+    Yref = None
+    for name, kind in (("tensor", 0), ("dp4a", 1)):
+        ctx.set_option(bfv.BFV_OPT_STANDARD_KERNEL, kind)
+        Y = ctx.lr_scores_standard(model, X_ct, len(X), ws=sws)
+        for _ in range(args.warmup - 1):
+            ctx.lr_scores_standard(model, X_ct, len(X), out=Y, ws=sws)
+        torch.cuda.synchronize()
+        a.record()
+        for _ in range(args.steps):
+            ctx.lr_scores_standard(model, X_ct, len(X), out=Y, ws=sws)
+        z.record()
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(z) / args.steps
+        slots = ctx.decode(ctx.decrypt(keys, Y)).cpu().numpy()
+        good = bool(np.array_equal(slots[:, :len(X)].T, want)) and ctx.check_error() == 0
+        if Yref is None:
+            Yref = Y.clone()
+        else:
+            good = good and bool(torch.equal(Y, Yref))
+        ok = ok and good
+        gb = args.features * 2 * L * N * 8 / 1e9
+        res[name] = {"ms_per_call": round(ms, 3), "gb_per_s": round(gb / (ms / 1e3), 1), "correct": good}
+    ctx.set_option(bfv.BFV_OPT_STANDARD_KERNEL, 0)
+    res["correct"] = ok
+    print(json.dumps(res), flush=True)
     return 0 if ok else 1
 
 
@@ -917,6 +944,19 @@ def run_serve(args):
         i0 = (k * 131) % (len(X) - n + 1)
         return pool[i0:i0 + n]
 
+    # the client's side when it is in the measured latency: encrypt the request's rows at arrival
+    # (on the submitting stream; the server's launch waits for it) and decrypt + decode its
+    # outputs right after the product, on the launch's stream
+    Xdev = torch.from_numpy(X).cuda()
+
+    def client_inputs(k, n):
+        i0 = (k * 131) % (len(X) - n + 1)
+        ptk = ctx.encode_features(Xdev[i0:i0 + n])
+        return ctx.encrypt(keys, ptk.reshape(-1, N), seed=w.seed_enc + k, obj0=0).reshape(n, model.K, 2, L, N)
+
+    def client_decrypt(r, out):
+        return ctx.decode(ctx.decrypt(keys, out))
+
     # warm-up: one fused launch and one single request
     ctx.lr_scores_packed_multi(keys, model, [pool[:1], pool[1:17]])
     ctx.lr_scores_packed(keys, model, pool[:1])
@@ -938,9 +978,26 @@ def run_serve(args):
         split.update(launches=srv.nbatches, max_concurrent=srv.max_concurrent)
         torch.cuda.empty_cache()
         single = serve.latency_report(serve.run_unbatched(ctx, keys, model, trace, inputs), model.nY)
+        # the same with the client's encryption and decryption inside each request's latency
+        srv = serve.Server(ctx, keys, model, hbm_budget_bytes=64 << 30, n_streams=2, small_pairs=16 * model.nY,
+                           post=client_decrypt)
+        done = srv.run(trace, client_inputs)
+        split_e2e = serve.latency_report(done, model.nY)
+        split_e2e.update(launches=srv.nbatches, max_concurrent=srv.max_concurrent)
+        for r in done[:3]:                            # spot-check the decrypted scores
+            i0 = (r.rid * 131) % (len(X) - r.nX + 1)
+            got = bfv.unpack_packed_scores(N, r.result.cpu().numpy(), r.nX, model.nY)
+            if not np.array_equal(got, (X[i0:i0 + r.nX].astype(np.int64) @ W + b[None, :]) % w.params.t):
+                raise SystemExit("served scores are wrong")
+        torch.cuda.empty_cache()
+        single_e2e = serve.latency_report(serve.run_unbatched(ctx, keys, model, trace, client_inputs,
+                                                              post=client_decrypt), model.nY)
+        torch.cuda.empty_cache()
         results[str(rate)] = {"offered_req_per_s": rate, "batched": batched, "batched_priority": split,
-                              "one_by_one": single}
-        print(json.dumps({"rate": rate, "batched": batched, "batched_priority": split, "one_by_one": single}),
+                              "one_by_one": single, "batched_priority_client_e2e": split_e2e,
+                              "one_by_one_client_e2e": single_e2e}
+        print(json.dumps({"rate": rate, "batched": batched, "batched_priority": split, "one_by_one": single,
+                          "batched_priority_client_e2e": split_e2e, "one_by_one_client_e2e": single_e2e}),
               flush=True)
     print(json.dumps({"case": "serve", "workload": "batch512-40k model, Poisson arrivals (70% x1, 30% x16..512)",
                       "results": results}), flush=True)

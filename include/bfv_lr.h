@@ -314,8 +314,13 @@ int bfv_check_error(bfv_ctx *ctx, int *flags);
 /* Launch options of a context (no counterpart in the paper; speed only, every value gives the
  * same bits). BFV_OPT_ENCRYPT_SPLIT: CTAs per limb of the encryption kernel at N = 16384, 1 (one
  * 512-thread CTA) or 2 (a cluster of two 256-thread CTAs, three of which share an SM; the
- * default); other rings ignore it. bfv_get_option writes the current value to *value. */
+ * default); other rings ignore it. BFV_OPT_STANDARD_KERNEL: the standard product with int8-range
+ * weights (|w| <= 127) runs its byte-plane contraction on the tensor cores (0, the default:
+ * tcgen05.mma kind::f16, exact f32 sums moved to int64 every 256 features) or on dp4a (1); wider
+ * weights always take the 32 x 32 -> 64-bit kernel. bfv_get_option writes the current value to
+ * *value. */
 #define BFV_OPT_ENCRYPT_SPLIT 1
+#define BFV_OPT_STANDARD_KERNEL 2
 int bfv_set_option(bfv_ctx *ctx, int option, int value);
 int bfv_get_option(const bfv_ctx *ctx, int option, int *value);
 

@@ -32,7 +32,7 @@ SOURCES = ["capi.cu", "k_scheme.cu", "k_packed.cu", "k_standard.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 BFV_OK, BFV_ERR_INVALID_ARG, BFV_ERR_BAD_PARAMS, BFV_ERR_OOM = 0, -1, -2, -3
-BFV_OPT_ENCRYPT_SPLIT = 1
+BFV_OPT_ENCRYPT_SPLIT, BFV_OPT_STANDARD_KERNEL = 1, 2
 BFV_ERR_OVER_BUDGET, BFV_ERR_TIMEOUT, BFV_ERR_CUDA = -4, -5, -6
 _ERRS = {-1: "INVALID_ARG", -2: "BAD_PARAMS", -3: "OOM", -4: "OVER_BUDGET", -5: "TIMEOUT", -6: "CUDA"}
 

@@ -32,6 +32,29 @@ def scores_to_real(z, s_x: int = S_X, s_w: int = S_W) -> np.ndarray:
     return np.asarray(z, dtype=np.float64) / (2.0 ** (s_x + s_w))
 
 
+def descale_argmax(z, s_x: int = S_X, s_w: int = S_W):
+    """The client's last step (Section 4.2.4): recombined integer scores z [nX][nY] (any array or
+    CPU/CUDA tensor) -> (real scores z / 2^(s_x + s_w) as float64 [nX][nY], predicted class of
+    each individual = the argmax of its linear scores, int64 [nX]). The softmax of the LR model is
+    monotone, so the argmax of the scores is the argmax of the class probabilities."""
+    if hasattr(z, "cpu"):
+        z = z.cpu().numpy()
+    z = np.asarray(z, dtype=np.int64)
+    return scores_to_real(z, s_x, s_w), np.argmax(z, axis=1).astype(np.int64)
+
+
+def quantization_bound(X, W, s_x: int = S_X, s_w: int = S_W) -> np.ndarray:
+    """Upper bound on |x.w + b - descaled fixed-point score| per individual and class for real X
+    [nX][f] and W [f][nY]: with x~ = round(x 2^s_x) / 2^s_x (error <= 2^-(s_x+1)), w~ likewise
+    (<= 2^-(s_w+1)) and the bias rounded at 2^-(s_x+s_w), |x w - x~ w~| <= |x - x~| |w| + |x~| |w - w~|,
+    summed over the features, plus 2^-(s_x+s_w+1) for the bias. Returns float64 [nX][nY]."""
+    X = np.asarray(X, dtype=np.float64)
+    W = np.asarray(W, dtype=np.float64)
+    xq = to_fixed(X, s_x).astype(np.float64) / 2.0 ** s_x
+    return (2.0 ** -(s_x + 1)) * np.abs(W).sum(axis=0)[None, :] + \
+        (2.0 ** -(s_w + 1)) * np.abs(xq).sum(axis=1)[:, None] + 2.0 ** -(s_x + s_w + 1)
+
+
 def bits_needed(f: int, s_x: int = S_X, s_w: int = S_W) -> int:
     """Precision of the scaled scores for f features (Section 4.2.2)."""
     return 8 + s_x + s_w + math.ceil(math.log2(f))
@@ -69,3 +92,22 @@ class CrtPair:
         (device tensor), centred in (-t0 t1 / 2, t0 t1 / 2]."""
         slots = [c.decode(c.decrypt(keys[r], Y[r])).reshape(-1)[: nX * nY] for r, c in enumerate(self.ctx)]
         return crt_combine(slots[0], self.t[0], slots[1], self.t[1]).reshape(nX, nY)
+
+    def quantize_model(self, W, b, s_x: int = S_X, s_w: int = S_W):
+        """The model owner's step: real weights |w| < 1 and biases -> fixed point (weights by
+        2^s_w, biases by 2^(s_x + s_w)) -> both rings' encoded models."""
+        return self.model_prepare(to_fixed(W, s_w), to_fixed(b, s_x + s_w))
+
+    def predict(self, keys, models, X, seed: int, s_x: int = S_X, s_w: int = S_W, **kw):
+        """The whole protocol for real-valued inputs 0 <= x < 2^8 (Section 4.2.2, Fig. 2): the client
+        quantizes (2^s_x) and encrypts under both plaintext moduli, the server runs the packed
+        product in each ring, the client decrypts, recombines by CRT, descales by 2^(s_x + s_w) and
+        takes the argmax. X: float array [nX][f]. Returns (real scores [nX][nY], predicted class [nX],
+        the integer scores [nX][nY])."""
+        import torch
+        Xi = to_fixed(X, s_x)
+        X_cts = self.encrypt_rows(keys, torch.from_numpy(Xi).to(f"cuda:{self.ctx[0].device}"), seed)
+        Y = self.scores_packed(keys, models, X_cts, **kw)
+        z = self.decrypt_scores(keys, Y, Xi.shape[0], models[0].nY).cpu().numpy()
+        real, cls = descale_argmax(z, s_x, s_w)
+        return real, cls, z

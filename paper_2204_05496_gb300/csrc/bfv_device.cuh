@@ -40,6 +40,54 @@ struct ModTab {
     const ulonglong2 *iw;   // inverse twiddles {psi^-brev(k), Shoup companion}
 };
 
+// ------------------------------------------------------------------ bounds-checked debug build
+//
+// Built with -DBFV_BOUNDS, every global-memory access of the library's kernels goes through
+// BFV_LD / BFV_ST / BFV_LDG (and every bulk copy through BFV_RANGE_OK): the address range must
+// lie inside one of the buffers the current call may touch (the context's tables, the keys, the
+// models, the caller's inputs, outputs and workspace at the sizes the call implies). An access
+// outside them is skipped (a load yields 0) and sets bit 1 (value 2) of the context's error word,
+// so a wrong index shows up as an error code instead of a fault. The table is per translation
+// unit and per process, uploaded in stream order before each call's launches (calls of a
+// bounds-checked build must not overlap). The release build compiles the macros to plain accesses.
+#ifdef BFV_BOUNDS
+#define BFV_MAX_RANGES 64
+struct BoundsTable {
+    int n;
+    int pad_;
+    int *err;
+    unsigned long long lo[BFV_MAX_RANGES], hi[BFV_MAX_RANGES];
+};
+static __device__ BoundsTable g_bounds;
+__device__ __forceinline__ bool bfv_in_bounds(const void *p, unsigned long long bytes) {
+    const unsigned long long a = (unsigned long long)p;
+    const int n = g_bounds.n;
+    for (int i = 0; i < n; ++i)
+        if (a >= g_bounds.lo[i] && a + bytes <= g_bounds.hi[i]) return true;
+    if (g_bounds.err) atomicOr(g_bounds.err, 2);
+    return false;
+}
+template <class T> __device__ __forceinline__ T bfv_ld(const T *p) { return bfv_in_bounds(p, sizeof(T)) ? *p : T{}; }
+template <class T> __device__ __forceinline__ T bfv_ldg(const T *p) { return bfv_in_bounds(p, sizeof(T)) ? __ldg(p) : T{}; }
+template <class T, class V> __device__ __forceinline__ void bfv_st(T *p, V v) {
+    if (bfv_in_bounds(p, sizeof(T))) *p = v;
+}
+#define BFV_LD(p) bfv_ld(p)
+#define BFV_LDG(p) bfv_ldg(p)
+#define BFV_ST(p, v) bfv_st((p), (v))
+#define BFV_RANGE_OK(p, bytes) bfv_in_bounds((p), (bytes))
+// Host side: each translation unit with kernels uploads the table to its own copy.
+#define BFV_BOUNDS_UPLOAD_FN(name)                                                          \
+    cudaError_t name(const BoundsTable &t, cudaStream_t st) {                              \
+        return cudaMemcpyToSymbolAsync(g_bounds, &t, sizeof t, 0, cudaMemcpyHostToDevice, st); \
+    }
+#else
+#define BFV_LD(p) (*(p))
+#define BFV_LDG(p) __ldg(p)
+#define BFV_ST(p, v) (*(p) = (v))
+#define BFV_RANGE_OK(p, bytes) true
+#endif
+
 // ------------------------------------------------------------------ modular arithmetic
 
 __device__ __forceinline__ u64 mul_shoup(u64 x, u64 w, u64 wp, u64 q) {
@@ -126,7 +174,7 @@ __device__ __forceinline__ void fwd_radix(u64 (&x)[1 << R], int s, int gblock, c
 #pragma unroll
         for (int k = 0; k < (1 << u); ++k) {
             const int ti = (1 << (s + u)) + (gblock << u) + k;
-            const ulonglong2 w = __ldg(fw + ti);
+            const ulonglong2 w = BFV_LDG(fw + ti);
 #pragma unroll
             for (int j = 0; j < half; ++j) {
                 if constexpr (LAZY) ct_bfly_lazy(x[k * 2 * half + j], x[k * 2 * half + j + half], w.x, w.y, q, q2);
@@ -153,7 +201,7 @@ __device__ __forceinline__ void inv_radix(u64 (&x)[1 << R], int s0, int block, i
                 gs_bfly_last(x[r], x[r + (1 << u)], ni, nip, il, ilp, q, q2);
             } else {
                 const int ti = (N >> (s0 + u + 1)) + (block << (R - 1 - u)) + (r >> (u + 1));
-                const ulonglong2 w = __ldg(iw + ti);
+                const ulonglong2 w = BFV_LDG(iw + ti);
                 gs_bfly(x[r], x[r + (1 << u)], w.x, w.y, q, q2);
             }
         }
@@ -375,7 +423,7 @@ __device__ __forceinline__ u64 fold_stages(const ModTab &T, int hidx, u64 (&v)[1
     for (int s = 0; s < C; ++s) {
         const int half = 1 << (C - 1 - s);
         const int side = (hidx >> (C - 1 - s)) & 1;
-        const ulonglong2 w = __ldg(T.fw + (1 << s) + (hidx >> (C - s)));
+        const ulonglong2 w = BFV_LDG(T.fw + (1 << s) + (hidx >> (C - s)));
 #pragma unroll
         for (int k = 0; k < half; ++k) {
             const u64 a = red2(v[k], q2), t = mul_shoup(v[k + half], w.x, w.y, q);
@@ -470,6 +518,49 @@ __device__ __forceinline__ void tmem_st16(u32 addr, const u32 (&r)[16]) {
 }
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 __device__ __forceinline__ void tmem_wait_st() { asm volatile("tcgen05.wait::st.sync.aligned;" ::: "memory"); }
+
+// 8 consecutive columns of this thread's lane (warp-wide).
+__device__ __forceinline__ void tmem_ld8(u32 addr, u32 (&r)[8]) {
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0, %1, %2, %3, %4, %5, %6, %7}, [%8];"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7])
+                 : "r"(addr)
+                 : "memory");
+}
+
+// ------------------------------------------------------------------ tensor-core MMA (tcgen05, kind::f16)
+//
+// Shared-memory matrix descriptor of an operand tile in the canonical K-major layout without
+// swizzling: core matrices of 8 rows x 16 bytes (128 contiguous bytes, row r at byte 16 r);
+// `lbo` = bytes between core matrices adjacent along K, `sbo` = bytes between core matrices
+// adjacent along M (or N). Bits: start address >> 4 [0, 14), lbo >> 4 [16, 30), sbo >> 4
+// [32, 46), the descriptor version 1 at bit 46, no base offset, no swizzle.
+__device__ __forceinline__ u64 umma_desc_kmajor(const void *tile, u32 lbo, u32 sbo) {
+    const u32 a = smem_addr(tile);
+    return (u64)((a & 0x3FFFFu) >> 4) | ((u64)(lbo >> 4) << 16) | ((u64)(sbo >> 4) << 32) | (1ull << 46);
+}
+// Instruction descriptor of kind::f16 with f16 A and B, f32 D, both operands K-major: D type
+// at bits [4, 6) (1 = f32), A and B types at [7, 10) and [10, 13) (0 = f16), N >> 3 at [17, 23),
+// M >> 4 at [24, 29).
+__host__ __device__ constexpr u32 umma_idesc_f16_f32(int M, int N) {
+    return (1u << 4) | ((u32)(N >> 3) << 17) | ((u32)(M >> 4) << 24);
+}
+// D[tmem] (+)= A[smem] x B[smem]^T for one K = 16 step; issued by one thread.
+__device__ __forceinline__ void umma_f16(u32 d_tmem, u64 adesc, u64 bdesc, u32 idesc, bool accumulate) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d_tmem),
+        "l"(adesc), "l"(bdesc), "r"(idesc), "r"((u32)accumulate)
+        : "memory");
+}
+// The mbarrier receives one arrival when every MMA this thread issued before has completed
+// (its shared-memory operands read, its tensor-memory results written).
+__device__ __forceinline__ void umma_commit(u64 *bar) {
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(smem_addr(bar))
+                 : "memory");
+}
+// Orders this thread's generic-proxy shared-memory writes before later async-proxy reads (the
+// tensor cores' operand loads) that a barrier hands them to.
+__device__ __forceinline__ void fence_proxy_async_smem() { asm volatile("fence.proxy.async.shared::cta;" ::: "memory"); }
 
 // ------------------------------------------------------------------ ChaCha20 (RFC 8439)
 

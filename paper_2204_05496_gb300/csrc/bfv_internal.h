@@ -9,6 +9,7 @@
 #include <tuple>
 #include <utility>
 #include <cuda_runtime.h>
+#include <nvtx3/nvToolsExt.h>
 
 #include "bfv_device.cuh"
 #include "../../include/bfv_lr.h"
@@ -61,6 +62,7 @@ struct bfv_ctx {
     int inject_extra_tx = 0;         // failure injection: bytes a streaming stage waits for in vain
     u64 *noalloc_scratch = nullptr;  // device address of bfv_decrypt_noalloc's fixed array
     int enc_split = 2;               // CTAs per limb of the encryption kernel at N = 16384 (BFV_OPT_ENCRYPT_SPLIT)
+    int std_kernel = 0;              // standard product with int8 weights: 0 tensor cores, 1 dp4a (BFV_OPT_STANDARD_KERNEL)
     std::map<size_t, bfv_packed_schedule> tuned;   // pairs -> schedule (0: any other pair count)
     mutable std::mutex tune_mu;                    // guards tuned (read by every packed plan)
     // CUDA graphs of whole packed products, keyed by every argument of the call
@@ -88,6 +90,8 @@ struct bfv_model {
     shoup_t *w_eval = nullptr;       // [nY][K][L][N] {value, companion} (packed product)
     int *w16 = nullptr;              // [ceil(nY/16)][f][16] int32 weights, zero-padded (standard product)
     int *w4 = nullptr;               // [ceil(nY/16)][ceil(f/4)][16] four int8 weights per int32 (|w| <= 127)
+    uint16_t *wtc = nullptr;         // [ceil(nY/16)][ceil(f/16)][256] f16 weights, one canonical MMA B tile
+                                     // (K-major: [class/8][feature/8][class%8][feature%8]) per 16 features
     u64 *bias_delta = nullptr;       // [nY][L]: Delta [b_j]_t mod q_l
     int64_t wmax = 0;                // max |w| (bounds the standard product's accumulators)
 };
@@ -97,13 +101,24 @@ inline void count_launch(const bfv_ctx *c, uint64_t n = 1) {
     const_cast<bfv_ctx *>(c)->launches.fetch_add(n, std::memory_order_relaxed);
 }
 
-// Records an event pair around the launches in its scope when profiling is on.
+// Names of the kernel kinds (BFV_K_*), as NVTX range names.
+inline const char *kernel_kind_name(int kind) {
+    static const char *names[BFV_K_COUNT] = {"bfv.ntt", "bfv.ks_prep", "bfv.ks_modup", "bfv.ks_moddown_p",
+                                             "bfv.ks_moddown", "bfv.mac", "bfv.bias_mask", "bfv.compress",
+                                             "bfv.encrypt", "bfv.decrypt", "bfv.encode", "bfv.standard"};
+    return kind >= 0 && kind < BFV_K_COUNT ? names[kind] : "bfv";
+}
+
+// Around the launches in its scope: an NVTX range named after the kernel kind (host-side
+// annotation for profilers; a few nanoseconds when no tool is attached) and, when profiling is
+// on, a CUDA event pair on the launching stream.
 struct ProfScope {
     const bfv_ctx *c;
     int kind;
     cudaStream_t st;
     cudaEvent_t a = nullptr;
     ProfScope(const bfv_ctx *c_, int kind_, cudaStream_t st_) : c(c_), kind(kind_), st(st_) {
+        nvtxRangePushA(kernel_kind_name(kind));
         if (c->prof.on) {
             std::lock_guard<std::mutex> g(c->prof.mu);
             a = c->prof.get();
@@ -117,6 +132,7 @@ struct ProfScope {
             cudaEventRecord(b, st);
             c->prof.pending[kind].push_back({a, b});
         }
+        nvtxRangePop();
     }
 };
 
@@ -239,7 +255,8 @@ int launch_pair_export(const bfv_ctx *c, const PackedPlan &plan, const void *ws,
 struct StandardPlan {
     size_t ntiles, splits, fper, ngroups, bytes;
     int split_bits;
-    bool int8;                       // byte-plane dp4a kernel (|w| <= 127)
+    bool int8;                       // byte-plane kernels (|w| <= 127): tensor cores or dp4a
+    bool tc;                         // byte planes on the tensor cores
 };
 StandardPlan standard_plan(const bfv_ctx *c, const bfv_model *m);
 size_t standard_smem_bytes();

@@ -187,6 +187,17 @@ int gaussian_table_h(uint32_t num, uint32_t den, u64 *out) {
     return tail;
 }
 
+// IEEE binary16 bits of an integer of magnitude below 2048 (exact: 11 significant bits).
+uint16_t f16_of_small(int64_t v) {
+    if (v == 0) return 0;
+    const uint16_t sign = v < 0 ? 0x8000 : 0;
+    uint32_t a = (uint32_t)(v < 0 ? -v : v);
+    int e = 0;
+    while ((a >> (e + 1)) != 0) ++e;                  // a in [2^e, 2^(e+1))
+    const uint32_t mant = (a << (10 - e)) & 0x3FFu;   // the 10 bits below the leading one
+    return (uint16_t)(sign | (uint32_t)(e + 15) << 10 | mant);
+}
+
 bool params_ok(const bfv_params *p) {
     if (!p) return false;
     if (p->N != 4096 && p->N != 8192 && p->N != 16384 && p->N != 32768) return false;
@@ -558,8 +569,9 @@ int bfv_model_prepare(bfv_ctx *ctx, const int64_t *W, const int64_t *b, size_t f
     u64 *dpt = nullptr;
     const size_t ngroups = (nY + 15) / 16;
     const size_t f4 = (f + 3) / 4;
+    const size_t f16s = (f + 15) / 16;
     if ((rc = dalloc(&m->w_eval, nY * K * L * N)) || (rc = dalloc(&m->w16, ngroups * f * 16)) ||
-        (rc = dalloc(&m->w4, ngroups * f4 * 16)) ||
+        (rc = dalloc(&m->w4, ngroups * f4 * 16)) || (rc = dalloc(&m->wtc, ngroups * f16s * 256)) ||
         (rc = dalloc(&m->bias_delta, nY * L)) || (rc = dalloc(&dslots, nY * K * N)) || (rc = dalloc(&dpt, nY * K * N))) {
         cudaFree(dslots);
         cudaFree(dpt);
@@ -583,6 +595,16 @@ int bfv_model_prepare(bfv_ctx *ctx, const int64_t *W, const int64_t *b, size_t f
                 const uint32_t byte = (uint32_t)(uint8_t)(int8_t)W[r * nY + j];
                 w4[((j / 16) * f4 + r / 4) * 16 + j % 16] |= (int)(byte << (8 * (r % 4)));
             }
+    // f16 weights for the tensor-core product: per class group and 16 features one B tile of
+    // 16 classes x 16 features in the canonical K-major layout [class/8][feature/8][class%8][feature%8]
+    std::vector<uint16_t> wtc(ngroups * f16s * 256, 0);
+    if (m->wmax <= 127)
+        for (size_t r = 0; r < f; ++r)
+            for (size_t j = 0; j < nY; ++j) {
+                const size_t st = r / 16, k = r % 16, n = j % 16;
+                wtc[((j / 16) * f16s + st) * 256 + (n / 8) * 128 + (k / 8) * 64 + (n % 8) * 8 + k % 8] =
+                    f16_of_small(W[r * nY + j]);
+            }
     // transposed, packed weights: slot s of plaintext (j, k) = W[k N + s][j]
     std::vector<int64_t> slots(nY * K * N, 0);
     for (size_t j = 0; j < nY; ++j)
@@ -598,6 +620,7 @@ int bfv_model_prepare(bfv_ctx *ctx, const int64_t *W, const int64_t *b, size_t f
     if (cudaMemcpyAsync(dslots, slots.data(), slots.size() * 8, cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(m->w16, w16.data(), w16.size() * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(m->w4, w4.data(), w4.size() * sizeof(int), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaMemcpyAsync(m->wtc, wtc.data(), wtc.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(m->bias_delta, bd.data(), bd.size() * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
         rc = BFV_ERR_CUDA;
     if (!rc) rc = launch_encode(ctx, dslots, nY * K, dpt, st);
@@ -615,6 +638,7 @@ int bfv_model_free(bfv_model *m) {
     cudaFree(m->w_eval);
     cudaFree(m->w16);
     cudaFree(m->w4);
+    cudaFree(m->wtc);
     cudaFree(m->bias_delta);
     delete m;
     return BFV_OK;
@@ -903,6 +927,10 @@ int bfv_set_option(bfv_ctx *ctx, int option, int value) {
             if (value != 1 && value != 2) return BFV_ERR_INVALID_ARG;
             ctx->enc_split = value;
             return BFV_OK;
+        case BFV_OPT_STANDARD_KERNEL:
+            if (value != 0 && value != 1) return BFV_ERR_INVALID_ARG;
+            ctx->std_kernel = value;
+            return BFV_OK;
         default: return BFV_ERR_INVALID_ARG;
     }
 }
@@ -911,6 +939,7 @@ int bfv_get_option(const bfv_ctx *ctx, int option, int *value) {
     if (!ctx || !value) return BFV_ERR_INVALID_ARG;
     switch (option) {
         case BFV_OPT_ENCRYPT_SPLIT: *value = ctx->enc_split; return BFV_OK;
+        case BFV_OPT_STANDARD_KERNEL: *value = ctx->std_kernel; return BFV_OK;
         default: return BFV_ERR_INVALID_ARG;
     }
 }

@@ -13,6 +13,8 @@
 // k_standard_finalize (exact while |w| f 2^max(s, bits-s) < 2^63).
 #include <algorithm>
 
+#include <cuda_fp16.h>
+
 #include "bfv_internal.h"
 
 namespace {
@@ -240,6 +242,212 @@ __global__ void __launch_bounds__(2 * kE8 + 32, 2) k_standard_dp4a(const int *__
     if (__syncthreads_or(failed) && tid == 0) atomicOr(err, 1);
 }
 
+// ------------------------------------------------------------------ int8 weights on the tensor cores
+//
+// The same byte-plane sums as a tensor-core contraction: for each byte plane b < NP,
+// D_b[e][j] = sum_f byte_b(X_f[e]) w[f][j] with M = 128 ciphertext words (a tile), N = 16
+// classes and K = features, as tcgen05.mma kind::f16 (A: the byte planes, B: the weights, both
+// exact in f16; D: f32 in tensor memory). A product is an integer of magnitude at most
+// 255 * 127 and a chunk of 256 features sums to less than 2^23, so every f32 partial sum is an
+// exact integer; after each chunk the sums are moved into the (lo, hi) int64 split sums that the
+// dp4a kernel forms (lo = sum_{b<4} 2^(8b) D_b, hi = sum_{b>=4} 2^(8(b-4)) D_b).
+//
+// Warps 0-7 convert: thread t owns word e = t % 128 of the tile and features 8 (t / 128) ..
+// +7 of each 16-feature stage; it splits its eight residues into byte planes (PRMT), makes each
+// byte an exact f16 (the byte under the exponent bits of 1024, minus 1024) and writes one
+// 16-byte row of each plane's A tile (canonical K-major layout). The same threads drain the
+// accumulators of their TMEM lane (classes 8 (t / 128) .. +7). Warp 8 streams the raw
+// ciphertext rows and the stage's f16 weight tile (already in the canonical B layout) with
+// cp.async.bulk; warp 9 allocates the tensor memory and one of its threads issues the MMAs.
+// Two accumulator sets alternate so that a chunk drains while the next one accumulates. Every
+// wait is bounded: a wait that runs out sets the context's error word and the CTA winds down
+// (its MMAs completed, its copies landed or timed out, its tensor memory freed).
+
+constexpr int kTcE = 128;                 // ciphertext words per tile (MMA M)
+constexpr int kTcChunk = 16;              // stages (16 features each) per f32 accumulation chunk
+constexpr int kTcConv = 256;              // converter threads
+constexpr int kTcThreads = kTcConv + 64;  // + the copy warp and the MMA warp
+constexpr u32 kTcCols = 256;              // tensor-memory columns: 2 sets x 8 planes x 16 classes
+
+template <int NP> struct TcSmem {
+    static constexpr int SR = NP >= 8 ? 2 : 3;        // raw stages in flight
+    static constexpr int SA = 2;                      // converted stages in flight
+    u64 x[SR][kF][kTcE];                              // raw rows: feature ff of the stage, word e
+    uint16_t w[SR][256];                              // the stage's f16 weights (canonical B tile)
+    alignas(128) uint16_t a[SA][NP][kTcE * kF];       // byte planes (canonical A tiles, 4 KB each)
+    alignas(128) uint16_t b[SA][256];                 // the weights of the converted stage
+    u64 raw_full[SR], raw_empty[SR], a_full[SA], a_empty[SA], acc_full[2], acc_empty[2], done;
+    u32 tmem_base;
+};
+
+// Four f16 pairs (features 2i, 2i+1 of word e) of byte plane b from eight residues.
+__device__ __forceinline__ uint4 plane_row(const u64 (&v)[8], int b) {
+    const u32 k = (u32)(b & 3);
+    const u32 sel = k | (k << 4) | ((4 + k) << 8) | ((4 + k) << 12);   // [x_k, x_k, y_k, y_k]
+    u32 o[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+        const u32 x = b < 4 ? (u32)v[2 * i] : (u32)(v[2 * i] >> 32);
+        const u32 y = b < 4 ? (u32)v[2 * i + 1] : (u32)(v[2 * i + 1] >> 32);
+        const u32 t = (prmt(x, y, sel) & 0x00FF00FFu) | 0x64006400u;      // f16 pair 1024 + byte
+        const __half2 h = __hsub2(*reinterpret_cast<const __half2 *>(&t), __half2(__half(1024.0f), __half(1024.0f)));
+        o[i] = *reinterpret_cast<const u32 *>(&h);
+    }
+    return make_uint4(o[0], o[1], o[2], o[3]);
+}
+
+// A bounded wait by a whole warp with one outcome for all its lanes (the tensor-memory loads that
+// follow are warp-collective, so no lane may leave the loop alone).
+__device__ __forceinline__ bool warp_wait(u64 *bar, u32 parity, long long limit) {
+    return __all_sync(0xffffffffu, mbar_wait(bar, parity, limit));
+}
+
+template <int NP>
+__global__ void __launch_bounds__(kTcThreads, 2) k_standard_tc(const uint16_t *__restrict__ Wtc,
+                                                              const u64 *__restrict__ X, size_t ctw, size_t F,
+                                                              size_t fper, longlong2 *partial, int *err,
+                                                              u32 extra_tx, long long wait_limit) {
+    extern __shared__ __align__(1024) unsigned char raw[];
+    using SM = TcSmem<NP>;
+    constexpr int SR = SM::SR, SA = SM::SA;
+    SM &s = *reinterpret_cast<SM *>(raw);
+    const size_t ntiles = ctw / kTcE;
+    const size_t tile = blockIdx.x % ntiles, split = blockIdx.x / ntiles;
+    const size_t e0 = tile * kTcE;
+    const size_t fa = split * fper, fb = std::min(F, fa + fper);
+    const int nst = fa < fb ? (int)((fb - fa + kF - 1) / kF) : 0;
+    const int nchunks = (nst + kTcChunk - 1) / kTcChunk;
+    const int tid = threadIdx.x, warp = tid >> 5;
+    if (tid == 0) {
+        for (int i = 0; i < SR; ++i) { mbar_init(&s.raw_full[i], 1); mbar_init(&s.raw_empty[i], kTcConv / 32); }
+        for (int i = 0; i < SA; ++i) { mbar_init(&s.a_full[i], kTcConv / 32); mbar_init(&s.a_empty[i], 1); }
+        for (int i = 0; i < 2; ++i) { mbar_init(&s.acc_full[i], 1); mbar_init(&s.acc_empty[i], kTcConv / 32); }
+        mbar_init(&s.done, 1);
+        mbar_init_fence();
+    }
+    if (warp == 9) tmem_alloc(&s.tmem_base, kTcCols);
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    const u32 tbase = s.tmem_base;
+    bool failed = false;
+
+    if (warp == 8) {
+        // copy warp: lane 0 streams the stages, refilling a slot once every converter warp let go
+        if (tid == kTcConv) {
+            int st = 0;
+            for (; st < nst; ++st) {
+                const int slot = st % SR;
+                if (st >= SR && !mbar_wait(&s.raw_empty[slot], (u32)(((st - SR) / SR) & 1), wait_limit)) {
+                    failed = true;
+                    break;
+                }
+                const size_t f0 = fa + (size_t)st * kF;
+                const int nf = (int)std::min((size_t)kF, fb - f0);
+                mbar_expect_tx(&s.raw_full[slot], (u32)nf * (kTcE * 8) + 512u + (st == 0 ? extra_tx : 0u));
+                for (int ff = 0; ff < nf; ++ff)
+                    bulk_g2s(&s.x[slot][ff][0], X + (f0 + ff) * ctw + e0, kTcE * 8, &s.raw_full[slot]);
+                bulk_g2s(&s.w[slot][0], Wtc + (f0 / kF) * 256, 512u, &s.raw_full[slot]);
+            }
+            // the last stages issued may still be landing
+            for (int k = st > SR ? st - SR : 0; k < st; ++k) mbar_wait(&s.raw_full[k % SR], (u32)((k / SR) & 1), wait_limit);
+        }
+    } else if (warp == 9) {
+        // MMA warp: one thread issues NP MMAs per stage into the chunk's accumulator set
+        if ((tid & 31) == 0) {
+            constexpr u32 idesc = umma_idesc_f16_f32(kTcE, 16);
+            for (int st = 0; st < nst && !failed; ++st) {
+                const int c = st / kTcChunk, k = st % kTcChunk, set = c & 1, as = st % SA;
+                if (k == 0 && c >= 2) {
+                    if (!mbar_wait(&s.acc_empty[set], (u32)(((c - 2) / 2) & 1), wait_limit)) { failed = true; break; }
+                    tmem_fence_after_sync();
+                }
+                if (!mbar_wait(&s.a_full[as], (u32)((st / SA) & 1), wait_limit)) { failed = true; break; }
+                tmem_fence_after_sync();
+                const u64 bdesc = umma_desc_kmajor(&s.b[as][0], 128, 256);
+#pragma unroll
+                for (int b = 0; b < NP; ++b)
+                    umma_f16(tbase + (u32)(set * 128 + b * 16), umma_desc_kmajor(&s.a[as][b][0], 128, 256), bdesc, idesc,
+                             k > 0);
+                umma_commit(&s.a_empty[as]);
+                if (k == kTcChunk - 1 || st == nst - 1) umma_commit(&s.acc_full[set]);
+            }
+            // every MMA issued has completed before the CTA frees its shared and tensor memory
+            umma_commit(&s.done);
+            mbar_wait(&s.done, 0, wait_limit);
+        }
+    } else {
+        // converters: byte planes in, accumulators out
+        const int e = tid & (kTcE - 1), k8 = tid >> 7;
+        const u32 lane_addr = tbase + ((u32)(32 * (warp & 3)) << 16);
+        long long lo[8], hi[8];
+#pragma unroll
+        for (int j = 0; j < 8; ++j) { lo[j] = 0; hi[j] = 0; }
+        int drained = 0;
+        auto drain = [&](int c) -> bool {
+            const int set = c & 1;
+            if (!warp_wait(&s.acc_full[set], (u32)((c / 2) & 1), wait_limit)) return false;
+            tmem_fence_after_sync();
+#pragma unroll
+            for (int b = 0; b < NP; ++b) {
+                u32 r[8];
+                tmem_ld8(lane_addr + (u32)(set * 128 + b * 16 + k8 * 8), r);
+                tmem_wait_ld();
+#pragma unroll
+                for (int j = 0; j < 8; ++j) {
+                    const long long v = (long long)__float2int_rn(__uint_as_float(r[j]));
+                    if (b < 4) lo[j] += v * (1ll << (8 * b));
+                    else hi[j] += v * (1ll << (8 * (b - 4)));
+                }
+            }
+            tmem_fence_before_sync();
+            __syncwarp();
+            if ((tid & 31) == 0) mbar_arrive(&s.acc_empty[set]);
+            return true;
+        };
+        for (int st = 0; st < nst; ++st) {
+            const int rs = st % SR, as = st % SA;
+            if (!warp_wait(&s.raw_full[rs], (u32)((st / SR) & 1), wait_limit)) { failed = true; break; }
+            if (st >= SA && !warp_wait(&s.a_empty[as], (u32)(((st - SA) / SA) & 1), wait_limit)) { failed = true; break; }
+            u64 v[8];
+#pragma unroll
+            for (int i = 0; i < 8; ++i) v[i] = s.x[rs][k8 * 8 + i][e];   // rows past the range: weights are 0
+#pragma unroll
+            for (int b = 0; b < NP; ++b)
+                *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(&s.a[as][b][0]) + (e >> 3) * 256 + k8 * 128 +
+                                           (e & 7) * 16) = plane_row(v, b);
+            if (k8 == 0) reinterpret_cast<u32 *>(&s.b[as][0])[e] = reinterpret_cast<const u32 *>(&s.w[rs][0])[e];
+            fence_proxy_async_smem();
+            __syncwarp();
+            if ((tid & 31) == 0) {
+                mbar_arrive(&s.raw_empty[rs]);
+                mbar_arrive(&s.a_full[as]);
+            }
+            // a chunk whose last stage the MMA warp finished SA stages ago drains now
+            const int done_st = st - SA;
+            if (done_st >= 0 && done_st % kTcChunk == kTcChunk - 1) {
+                if (!drain(drained)) { failed = true; break; }
+                ++drained;
+            }
+        }
+        while (!failed && drained < nchunks) {
+            if (!drain(drained)) { failed = true; break; }
+            ++drained;
+        }
+        if (!failed) {
+            longlong2 *out = partial + (split * kNY + k8 * 8) * ctw + e0 + e;
+#pragma unroll
+            for (int j = 0; j < 8; ++j) out[(size_t)j * ctw] = make_longlong2(lo[j], hi[j]);
+        }
+    }
+    // a bounded wait ran out somewhere: report it (the output of this launch is invalid)
+    if (__syncthreads_or(failed) && tid == 0) atomicOr(err, 1);
+    tmem_fence_before_sync();
+    __syncthreads();
+    tmem_fence_after_sync();
+    if (warp == 9) tmem_dealloc(tbase, kTcCols);
+}
+
 // Y[j0 + j][e] = (sum over splits of hi 2^s + lo) mod q + Delta [b]_t at coefficient 0 of c0.
 __global__ void __launch_bounds__(256) k_standard_finalize(const ModTab *__restrict__ mods, int N, int L, size_t ctw,
                                                            int splits, int nj, int j0, int split_bits,
@@ -272,11 +480,12 @@ StandardPlan standard_plan(const bfv_ctx *c, const bfv_model *m) {
     StandardPlan p{};
     const size_t ctw = 2 * (size_t)c->L * c->N;
     p.int8 = m->wmax <= 127 && c->bits <= 64;
+    p.tc = p.int8 && c->std_kernel == 0;
     p.ntiles = ctw / (p.int8 ? kE8 : kE);
     const size_t target = (size_t)c->sms * 2 * 6;    // about six waves of two CTAs per SM
     size_t splits = std::max<size_t>(1, (target + p.ntiles - 1) / p.ntiles);
     splits = std::min<size_t>(splits, std::max<size_t>(1, (m->f + 4 * kF - 1) / (4 * kF)));
-    if (p.int8) splits = std::max<size_t>(splits, (m->f + 65535) / 65536);   // int32 plane accumulators
+    if (p.int8 && !p.tc) splits = std::max<size_t>(splits, (m->f + 65535) / 65536);   // int32 plane accumulators
     p.fper = ((m->f + splits - 1) / splits + kF - 1) / kF * kF;
     p.splits = (m->f + p.fper - 1) / p.fper;
     p.ngroups = (m->nY + kNY - 1) / kNY;
@@ -298,7 +507,23 @@ int launch_standard(const bfv_ctx *c, const bfv_model *m, const u64 *X_ct, u64 *
     for (size_t gi = 0; gi < pl.ngroups; ++gi) {
         const int j0 = (int)(gi * kNY), nj = (int)std::min<size_t>(kNY, m->nY - j0);
         const unsigned grid = (unsigned)(pl.ntiles * pl.splits);
-        if (pl.int8) {
+        if (pl.tc) {
+            const uint16_t *wtc = m->wtc + gi * ((m->f + kF - 1) / kF) * 256;
+#define STDTC(NP)                                                                                                  \
+    {                                                                                                              \
+        cudaFuncSetAttribute(k_standard_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem<NP>)); \
+        k_standard_tc<NP><<<grid, kTcThreads, sizeof(TcSmem<NP>), st>>>(wtc, X_ct, ctw, m->f, pl.fper, partial,       \
+                                                                       c->derr, (u32)c->inject_extra_tx, limit);   \
+    }
+            switch (np) {
+                case 4: STDTC(4); break;
+                case 5: STDTC(5); break;
+                case 6: STDTC(6); break;
+                case 7: STDTC(7); break;
+                default: STDTC(8); break;
+            }
+#undef STDTC
+        } else if (pl.int8) {
             const int *w4 = m->w4 + gi * ((m->f + 3) / 4) * kNY;
 #define STD8(NP)                                                                                                   \
     {                                                                                                              \

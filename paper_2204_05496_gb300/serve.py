@@ -43,6 +43,7 @@ class Request:
     t_done: float | None = None  # seconds on the server clock, set at completion
     batch: int = -1
     ready: object = None         # CUDA event: the inputs are written (recorded at submission)
+    result: object = None        # what the server's post step returned for this request
 
     @property
     def nX(self) -> int:
@@ -51,7 +52,7 @@ class Request:
 
 class Server:
     def __init__(self, ctx, keys, model, hbm_budget_bytes: int, n_streams: int = 2, max_pairs: int = 8192,
-                 pair_chunk: int = 0, small_pairs: int = 0, torch_module=None):
+                 pair_chunk: int = 0, small_pairs: int = 0, torch_module=None, post=None):
         if torch_module is None:
             import torch as torch_module
         torch = self.torch = torch_module
@@ -59,6 +60,10 @@ class Server:
         self.models = list(model) if isinstance(model, (list, tuple)) else [model]
         self.budget = int(hbm_budget_bytes)
         self.max_pairs, self.pair_chunk = max_pairs, pair_chunk
+        # post(request, output) runs on the launch's stream right after its product (for instance
+        # the client's decryption in a simulation); its return value is kept in request.result and
+        # the request completes when it has finished on the device
+        self.post = post
         self.small_pairs = small_pairs
         # stream classes: None = any request; "small" / "large" when the classes are split
         if small_pairs > 0:
@@ -151,6 +156,9 @@ class Server:
                 outs = self.ctx.lr_scores_packed_models(self.keys, [self.models[r.model] for r in take],
                                                         [r.X_ct for r in take], ws=ws, pair_chunk=self.pair_chunk,
                                                         stream=stream)
+                if self.post is not None:
+                    for r, o in zip(take, outs):
+                        r.result = self.post(r, o)
                 ev = torch.cuda.Event(enable_timing=True)
                 ev.record(stream)
             for r, o in zip(take, outs):
@@ -222,9 +230,9 @@ def latency_report(reqs, nY: int) -> dict:
     return out
 
 
-def run_unbatched(ctx, keys, model, arrivals, make_inputs, pair_chunk: int = 0):
+def run_unbatched(ctx, keys, model, arrivals, make_inputs, pair_chunk: int = 0, post=None):
     """The same trace served one request at a time (FIFO, one stream, no fusion). `model` may be
-    a list indexed by the arrivals' third field, as for Server.run."""
+    a list indexed by the arrivals' third field, as for Server.run; `post` as for Server."""
     import torch
     models = list(model) if isinstance(model, (list, tuple)) else [model]
     torch.cuda.synchronize()
@@ -239,11 +247,13 @@ def run_unbatched(ctx, keys, model, arrivals, make_inputs, pair_chunk: int = 0):
         while time.perf_counter() - h0 < ta:
             time.sleep(0.0005)
         X = make_inputs(k, nX)
-        ctx.lr_scores_packed(keys, models[m], X, pair_chunk=pair_chunk)
+        r = Request(k, X, ta, m)
+        out = ctx.lr_scores_packed(keys, models[m], X, pair_chunk=pair_chunk)
+        if post is not None:
+            r.result = post(r, out)
         ev = torch.cuda.Event(enable_timing=True)
         ev.record()
         ev.synchronize()
-        r = Request(k, X, ta, m)
         r.t_done = t0.elapsed_time(ev) / 1e3
         done.append(r)
     return done

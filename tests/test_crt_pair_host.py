@@ -44,3 +44,23 @@ def test_precision_budget_at_the_paper_size(crt_pair):
     assert math.ceil(math.log2(worst)) == crt_pair.bits_needed(f) == 44
     assert crt_pair.T0 < 2 ** 43 and crt_pair.T1 < 2 ** 43 < crt_pair.T0 * crt_pair.T1 // 2
     assert math.gcd(crt_pair.T0, crt_pair.T1) == 1
+
+
+def test_descale_argmax_and_quantization_bound(crt_pair):
+    """The client's last step on exact integer scores of quantized real data: the descaled scores
+    lie within quantization_bound of the real-valued model's scores, and wherever the real model's
+    top two classes differ by more than twice the bound, the argmax agrees with the real model."""
+    X, W, b = synth.paper_realvalued(17, 40, 3000, 11)
+    Xi, Wi = crt_pair.to_fixed(X, crt_pair.S_X), crt_pair.to_fixed(W, crt_pair.S_W)
+    bi = crt_pair.to_fixed(b, crt_pair.S_X + crt_pair.S_W)
+    z = Xi @ Wi + bi[None, :]                                  # what the CRT pair recombines to
+    real, cls = crt_pair.descale_argmax(z)
+    assert cls.dtype == np.int64 and cls.shape == (40,)
+    assert np.array_equal(real, z / 2.0 ** 20)
+    ref = X @ W + b[None, :]
+    bound = crt_pair.quantization_bound(X, W)
+    assert np.all(np.abs(real - ref) <= bound)
+    top2 = np.sort(ref, axis=1)[:, -2:]
+    sure = (top2[:, 1] - top2[:, 0]) > 2 * bound.max(axis=1)
+    assert sure.sum() >= 10
+    assert np.array_equal(cls[sure], np.argmax(ref, axis=1)[sure])

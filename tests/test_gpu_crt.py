@@ -96,3 +96,43 @@ def test_crt_combine_kernel_matches_oracle():
     assert np.array_equal(got, oracle.crt_combine(r0 % t0, t0, r1 % t1, t1))
     with pytest.raises(bfv.BfvError):
         bfv.crt_combine(dev(r0), 6, dev(r1), 4)               # not coprime
+
+
+def test_client_pipeline_realvalued_stage_by_stage(pair):
+    """The whole protocol on real-valued inputs shaped like the paper's encodings (Section 4.1.2)
+    through the client calls of crt_pair: quantize (2^6) -> encrypt under t0 and t1 -> packed
+    product -> decrypt -> CRT -> descale (2^-20) -> argmax (Section 4.2.4). Each ring's input
+    ciphertexts, product ciphertexts and decrypted plaintexts equal the oracle's bit for bit; the
+    recombined integers equal X_int W_int + b_int; the descaled scores lie within the quantization
+    bound of the real model's; the argmax equals the real model's wherever its top two classes
+    differ by more than twice that bound."""
+    p, keys, Ps, okeys = pair
+    X, W, b = synth.paper_realvalued(607, 24, 9000, 11)
+    Xi, Wi = crt_pair.to_fixed(X, crt_pair.S_X), crt_pair.to_fixed(W, crt_pair.S_W)
+    bi = crt_pair.to_fixed(b, crt_pair.S_X + crt_pair.S_W)
+    models = p.quantize_model(W, b)
+    seed = 608
+    real, cls, z = p.predict(keys, models, X, seed)
+    exact = Xi @ Wi + bi[None, :]
+    # stage by stage: the same encryptions (same seeds) and products, against the oracle
+    X_cts = p.encrypt_rows(keys, dev(Xi), seed=seed)
+    Y = p.scores_packed(keys, models, X_cts)
+    res = []
+    for r, (P, ok) in enumerate(zip(Ps, okeys)):
+        oX, _, oY = oracle.packed_pipeline(P, ok, Xi, Wi, bi, seed + r)
+        assert np.array_equal(host(X_cts[r]), oX)
+        assert np.array_equal(host(Y[r]), oY)
+        opt = oracle.decrypt(P, ok.sk, oY)
+        assert np.array_equal(host(p.ctx[r].decrypt(keys[r], Y[r])), opt)
+        res.append(oracle.unpack_packed_scores(P, oracle.decode(P, opt), 24, 11))
+    assert np.array_equal(oracle.crt_combine(res[0], Ps[0].t, res[1], Ps[1].t), exact)
+    assert np.array_equal(z, exact)
+    assert np.array_equal(real, exact / 2.0 ** (crt_pair.S_X + crt_pair.S_W))
+    assert np.array_equal(cls, np.argmax(exact, axis=1))
+    ref = X @ W + b[None, :]
+    bound = crt_pair.quantization_bound(X, W)
+    assert np.all(np.abs(real - ref) <= bound)
+    top2 = np.sort(ref, axis=1)[:, -2:]
+    sure = (top2[:, 1] - top2[:, 0]) > 2 * bound.max(axis=1)
+    assert sure.sum() >= 6
+    assert np.array_equal(cls[sure], np.argmax(ref, axis=1)[sure])
