@@ -81,6 +81,9 @@ def parse_args(argv=None):
                    help="with --only-packed: time every split combination of the key-switching kernels")
     p.add_argument("--autotune", action="store_true",
                    help="with --only-packed: run the schedule autotuner and report its choice")
+    p.add_argument("--autotune-save", type=str, default="",
+                   help="tune the schedules of the benchmark's packed products (1 and 512 individuals) and "
+                        "write them to this schedule file")
     p.add_argument("--ring", choices=["16k", "32k"], default="16k", help="parameter set of --only-packed")
     p.add_argument("--uneven", action="store_true",
                    help="the uneven batch: 64 models on the N = 16384 and N = 32768 sets in one CUDA graph")
@@ -272,9 +275,9 @@ def run_reference(args):
     return 0
 
 
-def config_block(args, chunk):
+def config_block(args, chunk, schedule=None):
     w = synth.WORKLOADS[WORKLOAD]
-    return {
+    out = {
         "workload": (f"{WORKLOAD}: BFV N={w.params.N}, L={w.params.L} x {w.params.prime_bits}-bit primes + 1 "
                      f"special prime, t={w.params.t}; {w.n_individuals} individuals x {w.n_features} "
                      f"Bernoulli({w.p_feature}) binary features x {w.n_classes} classes, int8-range weights"),
@@ -286,6 +289,9 @@ def config_block(args, chunk):
         "l2": "flushed (256 MB write) between timed steps; per-step working set ~15 GB >> 129 MB L2",
         "parallelism": f"independent replicas x{max(1, args.gpus)}",
     }
+    if schedule is not None:
+        out["packed_schedule"] = schedule
+    return out
 
 
 # ----------------------------------------------------------------------------- GPU arm
@@ -378,7 +384,7 @@ def run_gpu(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": slow_ms, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "u64", "data": "synthetic (seeded; stands in for iDASH/TCGA)",
-        "config": config_block(args, chunk),
+        "config": config_block(args, chunk, ctx.packed_schedule(nX * nY).as_dict() if not chunk else None),
         "clocks": clocks,
         "gpu_launches": gpu_launches,
         "wall_s_timed_region": wall,
@@ -676,7 +682,7 @@ def run_only_packed(args):
         # every split combination at the plan's chunk (bit-identical results; times only)
         chunk = args.pair_chunk or ctx.packed_schedule(pairs).pair_chunk
         sweep = {}
-        for p_, m_, mp_, md_ in [(p_, m_, mp_, md_) for p_ in (1, 2) for m_ in (2, 4) for mp_ in (1, 2)
+        for p_, m_, mp_, md_ in [(p_, m_, mp_, md_) for p_ in (1, 2) for m_ in (2, 4) for mp_ in (1, 2, 3)
                                  for md_ in (1, 2)]:
             sc = bfv.Schedule(chunk, p_, m_, mp_, md_)
             Ys = ctx.lr_scores_packed_sched(keys, model, X_ct, sc, ws=ws)
@@ -877,7 +883,7 @@ def run_only_standard(args):
     a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     enc = {}
     X_ct = None
-    for split in (1, 2):
+    for split in (1, 2, 3):
         ctx.set_option(bfv.BFV_OPT_ENCRYPT_SPLIT, split)
         X_ct = ctx.encrypt(keys, cols, seed=w.seed_enc, out=X_ct)
         torch.cuda.synchronize()
@@ -886,7 +892,7 @@ def run_only_standard(args):
         z.record()
         torch.cuda.synchronize()
         enc[f"split{split}"] = round(a.elapsed_time(z), 3)
-    ctx.set_option(bfv.BFV_OPT_ENCRYPT_SPLIT, 2)
+    ctx.set_option(bfv.BFV_OPT_ENCRYPT_SPLIT, 3)
     del cols
     sws = torch.empty(ctx.standard_workspace(model), dtype=torch.uint8, device="cuda")
     want = (X.astype(np.int64) @ W + b[None, :]) % w.params.t
@@ -1083,6 +1089,34 @@ def bank_report(done, launches):
     return out
 
 
+def run_autotune_save(args):
+    """The autotuner on the benchmark's two packed products (one individual, 16 pairs; 512
+    individuals, 8,192 pairs) at N = 16384, L = 7; writes the chosen schedules to a schedule file
+    (the package reads paper_2204_05496_gb300/schedules.json at context creation)."""
+    import torch
+    import paper_2204_05496_gb300 as bfv
+    bfv.build()
+    torch.cuda.set_device(0)
+    w = synth.WORKLOADS[WORKLOAD]
+    X, W, b = synth.workload_inputs(w)
+    N, L = w.params.N, w.params.L
+    ctx = bfv.Context.from_shape(w.params)
+    keys = ctx.keygen(w.seed_keys)
+    model = ctx.model_prepare(W, b)
+    out = {}
+    for n in (1, 512):
+        pt = ctx.encode_features(torch.from_numpy(X[:n]).cuda())
+        X_ct = ctx.encrypt(keys, pt.reshape(-1, N), seed=w.seed_enc).reshape(n, model.K, 2, L, N)
+        ws = torch.empty(ctx.packed_workspace(model, n, 16384 if n > 1 else 16), dtype=torch.uint8, device="cuda")
+        best, ms = ctx.autotune_packed_schedule(keys, model, X_ct, ws)
+        out[n] = {"schedule": best.as_dict(), "ms": round(ms, 3)}
+        del ws, X_ct, pt
+        torch.cuda.empty_cache()
+    ctx.save_schedules(args.autotune_save, [n * model.nY for n in (1, 512)])
+    print(json.dumps({"case": "autotune-save", "file": args.autotune_save, "tuned": out}), flush=True)
+    return 0
+
+
 def main(argv=None):
     args = parse_args(argv)
     if args.serve_bank:
@@ -1099,6 +1133,8 @@ def main(argv=None):
         return run_paper8k(args)
     if args.only_standard:
         return run_only_standard(args)
+    if args.autotune_save:
+        return run_autotune_save(args)
     return run_gpu(args)
 
 

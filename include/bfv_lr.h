@@ -252,8 +252,9 @@ int bfv_lr_scores_packed_graph(bfv_ctx *ctx, const bfv_keys *keys, const bfv_mod
  *   pair_chunk       pairs in flight at once, >= 1 (workspace grows with it)
  *   prep_split       1 | 2: CTAs per digit in the inverse transform of the key-switch input
  *   modup_split      2 | 4: CTAs per target limb in ModUp (each folds log2 of it stages into its loads)
- *   moddown_p_split  0 | 1 | 2: CTAs per P limb in ModDown's inverse transform (0: 2 when the
- *                    chunk has fewer than the SM count of pairs, else 1)
+ *   moddown_p_split  0 | 1 | 2 | 3: CTAs per P limb in ModDown's inverse transform: 1 or 2 CTAs of
+ *                    256 threads, 3 = two CTAs of 512 threads (0: 2 when the chunk has fewer than
+ *                    the SM count of pairs, else 1)
  *   moddown_split    1 | 2: CTAs per limb in ModDown's forward transform and P^-1 product
  * No counterpart in the paper (a GPU launch configuration). */
 typedef struct bfv_packed_schedule {
@@ -308,13 +309,14 @@ int bfv_lr_scores_standard(bfv_ctx *ctx, const bfv_model *model, const uint64_t 
                            uint64_t *Y_ct, void *ws, size_t ws_bytes, uintptr_t stream);
 
 /* Synchronises the device, returns the context's device error word in *flags (bit 0: a
- * bounded wait in a kernel ran out) and clears it. Returns BFV_ERR_TIMEOUT if it was set. */
+ * bounded wait in a kernel ran out; bit 1, bounds-checked build only: an access outside the
+ * call's buffers was skipped) and clears it. Returns BFV_ERR_TIMEOUT if it was set. */
 int bfv_check_error(bfv_ctx *ctx, int *flags);
 
 /* Launch options of a context (no counterpart in the paper; speed only, every value gives the
- * same bits). BFV_OPT_ENCRYPT_SPLIT: CTAs per limb of the encryption kernel at N = 16384, 1 (one
- * 512-thread CTA) or 2 (a cluster of two 256-thread CTAs, three of which share an SM; the
- * default); other rings ignore it. BFV_OPT_STANDARD_KERNEL: the standard product with int8-range
+ * same bits). BFV_OPT_ENCRYPT_SPLIT: how the encryption kernel splits a limb at N = 16384: 1 (one
+ * 512-thread CTA), 2 (a cluster of two 256-thread CTAs, two CTAs per SM at 128 registers) or 3
+ * (the same cluster, three CTAs per SM at 80 registers; the default); other rings ignore it. BFV_OPT_STANDARD_KERNEL: the standard product with int8-range
  * weights (|w| <= 127) runs its byte-plane contraction on the tensor cores (0, the default:
  * tcgen05.mma kind::f16, exact f32 sums moved to int64 every 256 features) or on dp4a (1); wider
  * weights always take the 32 x 32 -> 64-bit kernel. bfv_get_option writes the current value to
@@ -328,9 +330,25 @@ int bfv_get_option(const bfv_ctx *ctx, int option, int *value);
  * BFV_INJECT_STREAM_STALL and value = n > 0 (a multiple of 16), the first pipeline stage of
  * every standard-product CTA waits for n bytes that are never sent, so its bounded wait runs
  * out after a short poll limit, the CTA drains its copies, sets the error word and returns
- * (the output is then invalid). value = 0 turns it off. */
+ * (the output is then invalid; the tensor-core kernel's first stage instead waits for an
+ * arrival that never comes). value = 0 turns it off. */
 #define BFV_INJECT_STREAM_STALL 1
+/* With what = BFV_INJECT_BOUNDS_SHRINK and value = n (a multiple of 8), a bounds-checked build
+ * (bfv_bounds_checked() = 1) registers every caller buffer of later calls n bytes shorter than
+ * the call implies, so the last accesses into each are reported as out of bounds (skipped, bit 1
+ * of the error word) although they stay inside the real buffer. The release build returns
+ * BFV_ERR_INVALID_ARG for it. */
+#define BFV_INJECT_BOUNDS_SHRINK 2
 int bfv_debug_inject(bfv_ctx *ctx, int what, int value);
+
+/* 1 if this library was built with bounds checks (-DBFV_BOUNDS), else 0. In that build every
+ * global-memory access of every kernel is checked against the buffers its call may touch (the
+ * context's tables, keys, models, and the caller's buffers at the sizes the call implies); an
+ * access outside them is skipped (a load reads 0) and sets bit 1 (value 2) of the context's error
+ * word (bfv_check_error), so an indexing mistake is reported instead of faulting. Calls of a
+ * bounds-checked build must not overlap on the GPU (the table is one per process). No
+ * counterpart in the paper (a debugging aid). */
+int bfv_bounds_checked(void);
 
 /* ------------------------------------------------------------------ whole-protocol calls */
 

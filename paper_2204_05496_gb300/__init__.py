@@ -25,7 +25,14 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _CSRC = os.path.join(_HERE, "csrc")
 _BUILD = os.path.join(_HERE, "_build")
-LIB_PATH = os.path.join(_BUILD, "libbfv_lr.so")
+# Build variants: the release library, and a bounds-checked one (-DBFV_BOUNDS: every global
+# access of every kernel checked against the call's buffers, violations reported through the
+# context's error word). BFV_LIB_VARIANT=bounds makes this process load the bounds-checked one.
+VARIANTS = {"release": ("libbfv_lr.so", []), "bounds": ("libbfv_lr_bounds.so", ["-DBFV_BOUNDS"])}
+VARIANT = os.environ.get("BFV_LIB_VARIANT", "release")
+if VARIANT not in VARIANTS:
+    raise RuntimeError(f"BFV_LIB_VARIANT={VARIANT!r}: one of {sorted(VARIANTS)} expected")
+LIB_PATH = os.path.join(_BUILD, VARIANTS[VARIANT][0])
 _ROOT = os.path.dirname(_HERE)
 _INCLUDE = os.path.join(_ROOT, "include")
 SOURCES = ["capi.cu", "k_scheme.cu", "k_packed.cu", "k_standard.cu"]
@@ -33,6 +40,7 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 BFV_OK, BFV_ERR_INVALID_ARG, BFV_ERR_BAD_PARAMS, BFV_ERR_OOM = 0, -1, -2, -3
 BFV_OPT_ENCRYPT_SPLIT, BFV_OPT_STANDARD_KERNEL = 1, 2
+BFV_INJECT_STREAM_STALL, BFV_INJECT_BOUNDS_SHRINK = 1, 2
 BFV_ERR_OVER_BUDGET, BFV_ERR_TIMEOUT, BFV_ERR_CUDA = -4, -5, -6
 _ERRS = {-1: "INVALID_ARG", -2: "BAD_PARAMS", -3: "OOM", -4: "OVER_BUDGET", -5: "TIMEOUT", -6: "CUDA"}
 
@@ -50,19 +58,25 @@ def _nvcc():
     return "nvcc"
 
 
-def build(force: bool = False, verbose: bool = False) -> str:
-    """Compile the CUDA library in-tree for sm_103a (translation units in parallel)."""
-    os.makedirs(_BUILD, exist_ok=True)
+def build(force: bool = False, verbose: bool = False, variant: str | None = None) -> str:
+    """Compile the CUDA library in-tree for sm_103a (translation units in parallel); `variant`
+    (default: the one this process loads) "bounds" builds the bounds-checked library beside the
+    release one."""
+    variant = variant or VARIANT
+    lib_name, extra = VARIANTS[variant]
+    lib_path = os.path.join(_BUILD, lib_name)
+    objdir = _BUILD if variant == "release" else os.path.join(_BUILD, variant)
+    os.makedirs(objdir, exist_ok=True)
     deps = [os.path.join(_CSRC, f) for f in os.listdir(_CSRC)] + [os.path.join(_INCLUDE, "bfv_lr.h")]
     newest = max(os.path.getmtime(d) for d in deps)
-    if not force and os.path.exists(LIB_PATH) and os.path.getmtime(LIB_PATH) >= newest:
-        return LIB_PATH
+    if not force and os.path.exists(lib_path) and os.path.getmtime(lib_path) >= newest:
+        return lib_path
     nvcc = _nvcc()
     flags = ARCH + ["-O3", "-lineinfo", "-std=c++17", "--expt-relaxed-constexpr", "-Xcompiler", "-fPIC",
-                    "-I", _INCLUDE, "-I", _CSRC]
+                    "-I", _INCLUDE, "-I", _CSRC] + extra
 
     def compile_one(src):
-        obj = os.path.join(_BUILD, src.replace(".cu", ".o"))
+        obj = os.path.join(objdir, src.replace(".cu", ".o"))
         cmd = [nvcc, "-c", os.path.join(_CSRC, src), "-o", obj] + flags
         r = subprocess.run(cmd, capture_output=True, text=True)
         if r.returncode != 0:
@@ -73,12 +87,12 @@ def build(force: bool = False, verbose: bool = False) -> str:
 
     with ThreadPoolExecutor(max_workers=len(SOURCES)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
-    tmp = LIB_PATH + f".tmp{os.getpid()}"
+    tmp = lib_path + f".tmp{os.getpid()}"
     r = subprocess.run([nvcc, "-shared", "-cudart", "shared", "-o", tmp] + ARCH + objs, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")
-    os.replace(tmp, LIB_PATH)
-    return LIB_PATH
+    os.replace(tmp, lib_path)
+    return lib_path
 
 
 class Params(ctypes.Structure):
@@ -145,6 +159,7 @@ SIGNATURES = {
                             ctypes.POINTER(ctypes.c_double)],
     "bfv_decrypt_noalloc": [_vp, _vp, _vp, _sz, _vp, _up],
     "bfv_set_option": [_vp, ctypes.c_int, ctypes.c_int],
+    "bfv_bounds_checked": [],
     "bfv_get_option": [_vp, ctypes.c_int, ctypes.POINTER(ctypes.c_int)],
     "bfv_packed_schedule_get": [_vp, _sz, ctypes.POINTER(Schedule)],
     "bfv_packed_schedule_set": [_vp, _sz, ctypes.POINTER(Schedule)],
@@ -256,6 +271,11 @@ def _stream(stream=None):
     return s.cuda_stream
 
 
+# Autotuned packed-product schedules shipped with the package (written by
+# `bench.py --autotune-save` on a GB300), keyed "N=...,L=...,pairs=...".
+SCHEDULE_FILE = os.path.join(_HERE, "schedules.json")
+
+
 def load_schedule_file(path: str) -> dict:
     """{key: schedule fields} of a schedule file written by Context.save_schedules ({} if absent)."""
     try:
@@ -325,6 +345,10 @@ class Context:
         _call("bfv_ctx_query", h, ctypes.cast(pr, _vp), ctypes.byref(om), ctypes.cast(de, _vp))
         self.primes, self.omega, self.delta_mod_q = list(pr), om.value, list(de)
         self.device = torch.cuda.current_device()
+        # schedules the autotuner chose on this GPU model for this ring (SCHEDULE_FILE), used by
+        # every packed product called with pair_chunk = 0
+        if os.path.exists(SCHEDULE_FILE):
+            self.load_schedules(SCHEDULE_FILE)
 
     @classmethod
     def from_shape(cls, shape):

@@ -33,7 +33,7 @@ struct ModTab {
     u64 pinv, pinvp;        // P^-1 mod q and companion (ciphertext primes only)
     u64 pmod, pmodp;        // P mod q and companion (ciphertext primes only)
     u64 phalf;              // floor(P/2) mod q
-    u64 delta;              // floor(Q/t) mod q
+    u64 delta, deltap;      // floor(Q/t) mod q and companion
     u64 r64, r64p;          // 2^64 mod q and companion
     u64 onep;               // floor(2^64 / q): Shoup companion of 1 (reduces any 64-bit word to [0, 2q))
     const ulonglong2 *fw;   // forward twiddles {psi^brev(k), Shoup companion}, k < N
@@ -51,7 +51,7 @@ struct ModTab {
 // unit and per process, uploaded in stream order before each call's launches (calls of a
 // bounds-checked build must not overlap). The release build compiles the macros to plain accesses.
 #ifdef BFV_BOUNDS
-#define BFV_MAX_RANGES 64
+#define BFV_MAX_RANGES 512
 struct BoundsTable {
     int n;
     int pad_;
@@ -69,11 +69,13 @@ __device__ __forceinline__ bool bfv_in_bounds(const void *p, unsigned long long 
 }
 template <class T> __device__ __forceinline__ T bfv_ld(const T *p) { return bfv_in_bounds(p, sizeof(T)) ? *p : T{}; }
 template <class T> __device__ __forceinline__ T bfv_ldg(const T *p) { return bfv_in_bounds(p, sizeof(T)) ? __ldg(p) : T{}; }
+template <class T> __device__ __forceinline__ T bfv_ldcs(const T *p) { return bfv_in_bounds(p, sizeof(T)) ? __ldcs(p) : T{}; }
 template <class T, class V> __device__ __forceinline__ void bfv_st(T *p, V v) {
     if (bfv_in_bounds(p, sizeof(T))) *p = v;
 }
 #define BFV_LD(p) bfv_ld(p)
 #define BFV_LDG(p) bfv_ldg(p)
+#define BFV_LDCS(p) bfv_ldcs(p)
 #define BFV_ST(p, v) bfv_st((p), (v))
 #define BFV_RANGE_OK(p, bytes) bfv_in_bounds((p), (bytes))
 // Host side: each translation unit with kernels uploads the table to its own copy.
@@ -84,6 +86,7 @@ template <class T, class V> __device__ __forceinline__ void bfv_st(T *p, V v) {
 #else
 #define BFV_LD(p) (*(p))
 #define BFV_LDG(p) __ldg(p)
+#define BFV_LDCS(p) __ldcs(p)
 #define BFV_ST(p, v) (*(p) = (v))
 #define BFV_RANGE_OK(p, bytes) true
 #endif
@@ -356,6 +359,23 @@ __device__ __forceinline__ bool mbar_wait(u64 *bar, u32 parity, long long limit)
     }
     return false;
 }
+// The same wait with the hardware suspending the thread for up to `hint_ns` nanoseconds per poll
+// until the phase completes (a waiting warp then takes no issue slots); at most `limit` polls.
+__device__ __forceinline__ bool mbar_wait_sleep(u64 *bar, u32 parity, long long limit, u32 hint_ns) {
+    const u32 a = smem_addr(bar);
+    for (long long i = 0; i < limit; ++i) {
+        u32 ok;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(ok)
+            : "r"(a), "r"(parity), "r"(hint_ns)
+            : "memory");
+        if (ok) return true;
+    }
+    return false;
+}
 // One-dimensional bulk copy global -> shared (16-byte aligned addresses, size a multiple of
 // 16), completion counted on `bar`.
 __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, u32 bytes, u64 *bar) {
@@ -363,6 +383,12 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, u32 bytes, 
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
+}
+
+// Asynchronous prefetch of `bytes` (a multiple of 16, 16-byte aligned) of global memory into L2
+// by the bulk-copy engine; nothing is written to shared memory or registers.
+__device__ __forceinline__ void bulk_prefetch_l2(const void *src, u32 bytes) {
+    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
 // ------------------------------------------------------------------ limbs split over a CTA pair
@@ -381,14 +407,16 @@ constexpr int nt_for(int logm) { return logm >= 13 ? 512 : (logm == 12 ? 256 : 1
 // For N <= 16384, S = 1 and these are the single-CTA transforms.
 // MODE 1 also splits an N = 16384 limb over two CTAs of 256 threads (68 KB of shared memory
 // each), three of which share an SM (80 registers each) so that one's barrier waits overlap the
-// others' work.
+// others' work; MODE 2 is the same split with two CTAs per SM (128 registers each); MODE 3 splits
+// the limb over two CTAs of 512 threads (one per SM; for launches too small to fill the GPU, where
+// a transform's latency matters more than its throughput).
 template <int LOGN, int MODE = 0> struct Split {
-    static constexpr bool PAIR16K = MODE == 1 && LOGN == 14;
+    static constexpr bool PAIR16K = (MODE == 1 || MODE == 2 || MODE == 3) && LOGN == 14;
     static constexpr int S = (LOGN > 14 || PAIR16K) ? 2 : 1;
     static constexpr int LOGM = LOGN - (S == 2 ? 1 : 0);
     static constexpr int M = 1 << LOGM;
-    static constexpr int NT = PAIR16K ? 256 : nt_for(LOGM);
-    static constexpr int MINB = PAIR16K ? 3 : 1;
+    static constexpr int NT = PAIR16K ? (MODE == 3 ? 512 : 256) : nt_for(LOGM);
+    static constexpr int MINB = PAIR16K ? (MODE == 1 ? 3 : MODE == 2 ? 2 : 1) : 1;
 };
 
 __device__ __forceinline__ u32 cluster_rank() {
@@ -436,18 +464,20 @@ __device__ __forceinline__ u64 fold_stages(const ModTab &T, int hidx, u64 (&v)[1
 // Forward transform of one limb by CTA h of its group: load(k) returns coefficient k (< 4q,
 // any k < N); store(p, v) receives the evaluation positions p this CTA owns, in [0, q)
 // (LAZY: below 32q, for Shoup-product consumers only).
-template <int LOGN, bool LAZY = false, int MODE = 0, class Load, class Store>
+// ILP2: the two radix-8 groups a thread handles in a pass are interleaved (more independent
+// multiplications in flight; more registers).
+template <int LOGN, bool LAZY = false, int MODE = 0, bool ILP2 = false, class Load, class Store>
 __device__ __forceinline__ void limb_forward(u64 *sm, const ModTab &T, int h, Load load, Store store) {
     using SP = Split<LOGN, MODE>;
     if constexpr (SP::S == 1) {
-        fwd_passes<LOGN, SP::NT, 0, 0, LAZY>(sm, T, 0, 0, load, store);
+        fwd_passes<LOGN, SP::NT, 0, 0, LAZY, ILP2>(sm, T, 0, 0, load, store);
     } else {
         auto ld = [&](int p) {
             u64 v[2] = {load(p), load(p + SP::M)};
             return fold_stages<1>(T, h, v);
         };
         auto st = [&](int p, u64 v) { store(h * SP::M + p, v); };
-        fwd_passes<SP::LOGM, SP::NT, 0, 0, LAZY>(sm, T, 1, h, ld, st);
+        fwd_passes<SP::LOGM, SP::NT, 0, 0, LAZY, ILP2>(sm, T, 1, h, ld, st);
     }
 }
 
@@ -596,7 +626,7 @@ __device__ __forceinline__ int ternary_of(u32 w) { return (int)(((u64)w * 3ull) 
 __device__ __forceinline__ int gauss_of(u32 lo, u32 hi, u32 sgn, const u64 *cdt, int n) {
     const u64 r = (u64)lo | ((u64)hi << 32);
     int mag = 0;
-    for (int k = 0; k < n; ++k) mag += (r >= cdt[k]) ? 1 : 0;
+    for (int k = 0; k < n; ++k) mag += (r >= BFV_LD(cdt + k)) ? 1 : 0;
     return (mag != 0 && (sgn & 1u)) ? -mag : mag;
 }
 

@@ -61,8 +61,10 @@ struct bfv_ctx {
     int *derr = nullptr;             // device error word (bounded waits that ran out set bit 0)
     int inject_extra_tx = 0;         // failure injection: bytes a streaming stage waits for in vain
     u64 *noalloc_scratch = nullptr;  // device address of bfv_decrypt_noalloc's fixed array
-    int enc_split = 2;               // CTAs per limb of the encryption kernel at N = 16384 (BFV_OPT_ENCRYPT_SPLIT)
+    size_t noalloc_bytes = 0;        // its size
+    int enc_split = 3;               // how the encryption kernel splits a limb at N = 16384 (BFV_OPT_ENCRYPT_SPLIT)
     int std_kernel = 0;              // standard product with int8 weights: 0 tensor cores, 1 dp4a (BFV_OPT_STANDARD_KERNEL)
+    int inject_shrink = 0;           // bounds-checked build, tests: caller buffers registered this many bytes short
     std::map<size_t, bfv_packed_schedule> tuned;   // pairs -> schedule (0: any other pair count)
     mutable std::mutex tune_mu;                    // guards tuned (read by every packed plan)
     // CUDA graphs of whole packed products, keyed by every argument of the call
@@ -136,6 +138,85 @@ struct ProfScope {
     }
 };
 
+// ------------------------------------------------------------------ bounds-checked build (host side)
+//
+// Each C entry point that launches kernels lists the buffers its launches may touch (the
+// context's tables, the keys, the models, the caller's buffers at the sizes the call implies,
+// internal temporaries) and uploads the list, in stream order, to every translation unit's
+// device table before its launches. In the release build this is an empty struct.
+#ifdef BFV_BOUNDS
+cudaError_t bounds_upload_scheme(const BoundsTable &t, cudaStream_t st);
+cudaError_t bounds_upload_packed(const BoundsTable &t, cudaStream_t st);
+cudaError_t bounds_upload_standard(const BoundsTable &t, cudaStream_t st);
+struct BoundsCall {
+    BoundsTable t{};
+    bool overflow = false;
+    size_t shrink = 0;
+    BoundsCall() {}                  // a call without a context (no error word to set)
+    explicit BoundsCall(const bfv_ctx *c) : shrink((size_t)c->inject_shrink) {
+        t.err = c->derr;
+        add(c->dmods, sizeof(ModTab) * (c->nqp + 1));
+        add(c->dtw, sizeof(u64) * (size_t)(c->nqp + 1) * 4 * c->N);
+        add(c->dslot, sizeof(u32) * c->N);
+        add(c->dmaskpow, sizeof(u32) * 2 * c->N);
+        add(c->dcdt, sizeof(u64) * 32);
+        add(c->ddec, sizeof(DecConst));
+        add(c->derr, sizeof(int));
+        add(c->noalloc_scratch, c->noalloc_bytes);
+    }
+    void add(const void *p, size_t bytes) {
+        if (!p || !bytes) return;
+        if (t.n >= BFV_MAX_RANGES) { overflow = true; return; }
+        t.lo[t.n] = (unsigned long long)p;
+        t.hi[t.n] = (unsigned long long)p + bytes;
+        ++t.n;
+    }
+    // a caller's buffer (registered `shrink` bytes short under failure injection)
+    void io(const void *p, size_t bytes) { add(p, bytes > shrink ? bytes - shrink : 0); }
+    void keys(const bfv_keys *k) {
+        if (!k) return;
+        const bfv_ctx *c = k->ctx;
+        add(k->sk, (size_t)c->N);
+        add(k->sk_eval, sizeof(shoup_t) * (size_t)c->nqp * c->N);
+        add(k->pk_eval, sizeof(shoup_t) * 2 * (size_t)c->L * c->N);
+        add(k->gk_eval, sizeof(shoup_t) * (size_t)k->ng * c->L * 2 * c->nqp * c->N);
+    }
+    void model(const bfv_model *m) {
+        if (!m) return;
+        const bfv_ctx *c = m->ctx;
+        const size_t ng = (m->nY + 15) / 16;
+        add(m->w_eval, sizeof(shoup_t) * m->nY * m->K * c->L * c->N);
+        add(m->w16, sizeof(int) * ng * m->f * 16);
+        add(m->w4, sizeof(int) * ng * ((m->f + 3) / 4) * 16);
+        add(m->wtc, sizeof(uint16_t) * ng * ((m->f + 15) / 16) * 256);
+        add(m->bias_delta, sizeof(u64) * m->nY * c->L);
+    }
+    int upload(cudaStream_t st) const {
+        if (overflow) return BFV_ERR_INVALID_ARG;
+        if (bounds_upload_scheme(t, st) != cudaSuccess || bounds_upload_packed(t, st) != cudaSuccess ||
+            bounds_upload_standard(t, st) != cudaSuccess)
+            return BFV_ERR_CUDA;
+        return BFV_OK;
+    }
+};
+#else
+struct BoundsCall {
+    BoundsCall() {}
+    explicit BoundsCall(const bfv_ctx *) {}
+    void add(const void *, size_t) {}
+    void io(const void *, size_t) {}
+    void keys(const bfv_keys *) {}
+    void model(const bfv_model *) {}
+    int upload(cudaStream_t) const { return BFV_OK; }
+};
+#endif
+
+#define BFV_BOUNDS_UPLOAD(bc, st)                  \
+    do {                                           \
+        const int brc_ = (bc).upload(st);          \
+        if (brc_) return brc_;                     \
+    } while (0)
+
 #define BFV_CUDA_TRY(expr)                              \
     do {                                                \
         cudaError_t e_ = (expr);                        \
@@ -196,7 +277,7 @@ int launch_noise_bits(const bfv_ctx *c, const bfv_keys *k, const u64 *ct, size_t
                       cudaStream_t st);
 int launch_model_weights(const bfv_ctx *c, bfv_model *m, const u64 *w_pt, cudaStream_t st);
 // Device address of bfv_decrypt_noalloc's fixed scratch array on the current device (k_scheme.cu).
-int noalloc_scratch_address(u64 **out);
+int noalloc_scratch_address(u64 **out, size_t *bytes);
 int launch_crt_combine(const int64_t *r0, u64 t0, const int64_t *r1, u64 t1, u64 inv, size_t n, int64_t *out,
                        cudaStream_t st);
 

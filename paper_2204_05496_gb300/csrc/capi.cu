@@ -234,6 +234,23 @@ cudaStream_t S(uintptr_t s) { return (cudaStream_t)s; }
 
 }  // namespace
 
+// The buffers a packed product's launches may touch: keys, models, each request's inputs and
+// outputs at the sizes the call implies, the workspace (bounds-checked build only).
+static void bounds_packed(BoundsCall &bc, const bfv_ctx *ctx, const bfv_keys *keys, int nreq,
+                          const bfv_model *const *models, const uint64_t *const *X, const size_t *nXs,
+                          uint64_t *const *Y, const void *ws, size_t ws_bytes) {
+    const size_t ctb = sizeof(u64) * 2 * ctx->L * ctx->N;
+    bc.keys(keys);
+    for (int r = 0; r < nreq; ++r) {
+        bool seen = false;
+        for (int q = 0; q < r && !seen; ++q) seen = models[q] == models[r];
+        if (!seen) bc.model(models[r]);
+        bc.io(X[r], nXs[r] * models[r]->K * ctb);
+        bc.io(Y[r], (nXs[r] * models[r]->nY + ctx->N - 1) / ctx->N * ctb);
+    }
+    bc.io(ws, ws_bytes);
+}
+
 // ====================================================================== C ABI
 
 extern "C" {
@@ -326,6 +343,7 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
             T.pmodp = shoup_h(T.pmod, q);
             T.phalf = (P / 2) % q;
             T.delta = mw_mod_small(Qdt, q);
+            T.deltap = shoup_h(T.delta, q);
             c->delta_host[j] = T.delta;
         } else if (j == c->L) {
             T.phalf = P / 2;
@@ -406,7 +424,7 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
     for (u64 s = N / 4; s >= 1; s >>= 1) c->galois.push_back(powmod_h(3, s, 2 * N));
 
     // the device address of bfv_decrypt_noalloc's fixed scratch array, with this device current
-    if ((rc = noalloc_scratch_address(&c->noalloc_scratch))) { free_ctx(c); return rc; }
+    if ((rc = noalloc_scratch_address(&c->noalloc_scratch, &c->noalloc_bytes))) { free_ctx(c); return rc; }
 
     if (cudaDeviceSynchronize() != cudaSuccess) { free_ctx(c); return BFV_ERR_CUDA; }
     *out = c;
@@ -460,6 +478,12 @@ int bfv_keys_free(bfv_keys *k) {
 
 int bfv_keys_export(const bfv_ctx *ctx, const bfv_keys *keys, int8_t *sk, uint64_t *pk, uint64_t *gk, uintptr_t stream) {
     if (!ctx || !keys || keys->ctx != ctx) return BFV_ERR_INVALID_ARG;
+    BoundsCall bc(ctx);
+    bc.keys(keys);
+    bc.io(sk, (size_t)ctx->N);
+    bc.io(pk, sizeof(u64) * 2 * (size_t)ctx->L * ctx->N);
+    bc.io(gk, sizeof(u64) * (size_t)keys->ng * ctx->L * 2 * ctx->nqp * ctx->N);
+    BFV_BOUNDS_UPLOAD(bc, S(stream));
     int rc = launch_keys_export(ctx, keys, sk, (u64 *)pk, (u64 *)gk, S(stream));
     if (rc) return rc;
     return cudaStreamSynchronize(S(stream)) == cudaSuccess ? BFV_OK : BFV_ERR_CUDA;
@@ -468,18 +492,30 @@ int bfv_keys_export(const bfv_ctx *ctx, const bfv_keys *keys, int8_t *sk, uint64
 int bfv_encode(bfv_ctx *ctx, const int64_t *slots, size_t count, uint64_t *pt, uintptr_t stream) {
     if (!ctx || (count && (!slots || !pt))) return BFV_ERR_INVALID_ARG;
     if (!count) return BFV_OK;
+    BoundsCall bc(ctx);
+    bc.io(slots, sizeof(int64_t) * count * ctx->N);
+    bc.io(pt, sizeof(u64) * count * ctx->N);
+    BFV_BOUNDS_UPLOAD(bc, S(stream));
     return launch_encode(ctx, slots, count, (u64 *)pt, S(stream));
 }
 
 int bfv_decode(bfv_ctx *ctx, const uint64_t *pt, size_t count, int64_t *slots, uintptr_t stream) {
     if (!ctx || (count && (!slots || !pt))) return BFV_ERR_INVALID_ARG;
     if (!count) return BFV_OK;
+    BoundsCall bc(ctx);
+    bc.io(pt, sizeof(u64) * count * ctx->N);
+    bc.io(slots, sizeof(int64_t) * count * ctx->N);
+    BFV_BOUNDS_UPLOAD(bc, S(stream));
     return launch_decode(ctx, (const u64 *)pt, count, slots, S(stream));
 }
 
 int bfv_encode_features(bfv_ctx *ctx, const uint8_t *X, size_t nX, size_t f, uint64_t *pt, uintptr_t stream) {
     if (!ctx || (nX && f && (!X || !pt))) return BFV_ERR_INVALID_ARG;
     if (!nX || !f) return BFV_OK;
+    BoundsCall bc(ctx);
+    bc.io(X, nX * f);
+    bc.io(pt, sizeof(u64) * nX * ((f + ctx->N - 1) / ctx->N) * ctx->N);
+    BFV_BOUNDS_UPLOAD(bc, S(stream));
     return launch_encode_features(ctx, X, nX, f, (u64 *)pt, S(stream));
 }
 
@@ -487,6 +523,10 @@ int bfv_encode_feature_columns(bfv_ctx *ctx, const uint8_t *X, size_t nX, size_t
     if (!ctx || nX > (size_t)ctx->N || (nX && f && (!X || !pt))) return BFV_ERR_INVALID_ARG;
     if (!f) return BFV_OK;
     if (!nX) return cudaMemsetAsync(pt, 0, f * ctx->N * 8, S(stream)) == cudaSuccess ? BFV_OK : BFV_ERR_CUDA;
+    BoundsCall bc(ctx);
+    bc.io(X, nX * f);
+    bc.io(pt, sizeof(u64) * f * ctx->N);
+    BFV_BOUNDS_UPLOAD(bc, S(stream));
     return launch_encode_columns(ctx, X, nX, f, (u64 *)pt, S(stream));
 }
 
@@ -506,6 +546,12 @@ int bfv_encrypt(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *pt, size_t c
     size_t need;
     bfv_encrypt_workspace(ctx, count, &need);
     if (ws_bytes < need) return BFV_ERR_OVER_BUDGET;
+    BoundsCall bc(ctx);
+    bc.keys(keys);
+    bc.io(pt, sizeof(u64) * count * ctx->N);
+    bc.io(ct, sizeof(u64) * count * 2 * ctx->L * ctx->N);
+    bc.io(ws, ws_bytes);
+    BFV_BOUNDS_UPLOAD(bc, S(stream));
     return launch_encrypt(ctx, keys, (const u64 *)pt, count, seed, obj0, (u64 *)ct, ws, S(stream));
 }
 
@@ -523,6 +569,12 @@ int bfv_decrypt(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *ct, size_t c
     size_t need;
     bfv_decrypt_workspace(ctx, count, &need);
     if (ws_bytes < need) return BFV_ERR_OVER_BUDGET;
+    BoundsCall bc(ctx);
+    bc.keys(keys);
+    bc.io(ct, sizeof(u64) * count * 2 * ctx->L * ctx->N);
+    bc.io(pt, sizeof(u64) * count * ctx->N);
+    bc.io(ws, ws_bytes);
+    BFV_BOUNDS_UPLOAD(bc, S(stream));
     return launch_decrypt(ctx, keys, (const u64 *)ct, count, (u64 *)pt, ws, S(stream));
 }
 
@@ -543,6 +595,11 @@ int bfv_noise_budget(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *ct, siz
     u64 *x = (u64 *)ws;
     int *bits = (int *)((char *)ws + align256(count * (size_t)ctx->L * ctx->N * 8));
     cudaStream_t st = S(stream);
+    BoundsCall bc(ctx);
+    bc.keys(keys);
+    bc.io(ct, sizeof(u64) * count * 2 * ctx->L * ctx->N);
+    bc.io(ws, ws_bytes);
+    BFV_BOUNDS_UPLOAD(bc, st);
     int rc = launch_noise_bits(ctx, keys, (const u64 *)ct, count, x, bits, st);
     if (rc) return rc;
     std::vector<int> hb(count);
@@ -623,6 +680,11 @@ int bfv_model_prepare(bfv_ctx *ctx, const int64_t *W, const int64_t *b, size_t f
         cudaMemcpyAsync(m->wtc, wtc.data(), wtc.size() * sizeof(uint16_t), cudaMemcpyHostToDevice, st) != cudaSuccess ||
         cudaMemcpyAsync(m->bias_delta, bd.data(), bd.size() * 8, cudaMemcpyHostToDevice, st) != cudaSuccess)
         rc = BFV_ERR_CUDA;
+    BoundsCall bc(ctx);
+    bc.model(m);
+    bc.add(dslots, sizeof(int64_t) * nY * K * N);
+    bc.add(dpt, sizeof(u64) * nY * K * N);
+    if (!rc) rc = bc.upload(st);
     if (!rc) rc = launch_encode(ctx, dslots, nY * K, dpt, st);
     if (!rc) rc = launch_model_weights(ctx, m, dpt, st);
     if (!rc && cudaStreamSynchronize(st) != cudaSuccess) rc = BFV_ERR_CUDA;
@@ -658,6 +720,9 @@ int bfv_lr_scores_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *mo
     if (!X_ct || !Y_ct || !ws) return BFV_ERR_INVALID_ARG;
     PackedPlan plan = packed_plan(ctx, model, nX, pair_chunk);
     if (ws_bytes < plan.total) return BFV_ERR_OVER_BUDGET;
+    BoundsCall bc(ctx);
+    bounds_packed(bc, ctx, keys, 1, &model, &X_ct, &nX, &Y_ct, ws, ws_bytes);
+    BFV_BOUNDS_UPLOAD(bc, S(stream));
     return launch_packed(ctx, keys, (const u64 *)X_ct, (u64 *)Y_ct, ws, plan, S(stream));
 }
 
@@ -679,6 +744,13 @@ int bfv_lr_scores_packed_multi(bfv_ctx *ctx, const bfv_keys *keys, const bfv_mod
         if (!nXs[r] || !X_cts[r] || !Y_cts[r]) return BFV_ERR_INVALID_ARG;
     PackedPlan plan = packed_plan_multi(ctx, model, nreq, nXs, pair_chunk);
     if (ws_bytes < plan.total) return BFV_ERR_OVER_BUDGET;
+    {
+        const bfv_model *ms[kMaxReq];
+        for (int r = 0; r < nreq; ++r) ms[r] = model;
+        BoundsCall bc(ctx);
+        bounds_packed(bc, ctx, keys, nreq, ms, X_cts, nXs, Y_cts, ws, ws_bytes);
+        BFV_BOUNDS_UPLOAD(bc, S(stream));
+    }
     return launch_packed_multi(ctx, keys, nreq, (const u64 *const *)X_cts, (u64 *const *)Y_cts, ws, plan, S(stream));
 }
 
@@ -708,6 +780,9 @@ int bfv_lr_scores_packed_models(bfv_ctx *ctx, const bfv_keys *keys, int nreq, co
         if (!X_cts[r] || !Y_cts[r]) return BFV_ERR_INVALID_ARG;
     PackedPlan plan = packed_plan_models(ctx, nreq, models, nXs, pair_chunk);
     if (ws_bytes < plan.total) return BFV_ERR_OVER_BUDGET;
+    BoundsCall bc(ctx);
+    bounds_packed(bc, ctx, keys, nreq, models, X_cts, nXs, Y_cts, ws, ws_bytes);
+    BFV_BOUNDS_UPLOAD(bc, S(stream));
     return launch_packed_multi(ctx, keys, nreq, (const u64 *const *)X_cts, (u64 *const *)Y_cts, ws, plan, S(stream));
 }
 
@@ -719,6 +794,11 @@ int bfv_crt_combine(const int64_t *r0, uint64_t t0, const int64_t *r1, uint64_t 
     while (h) { const u64 r = g % h; g = h; h = r; }
     if (g != 1) return BFV_ERR_INVALID_ARG;
     const u64 inv = inv_h(t0 % t1, t1);
+    BoundsCall bc;
+    bc.io(r0, sizeof(int64_t) * n);
+    bc.io(r1, sizeof(int64_t) * n);
+    bc.io(out, sizeof(int64_t) * n);
+    BFV_BOUNDS_UPLOAD(bc, S(stream));
     return launch_crt_combine(r0, t0, r1, t1, inv, n, out, S(stream));
 }
 
@@ -731,6 +811,12 @@ int bfv_lr_scores_packed_graph(bfv_ctx *ctx, const bfv_keys *keys, const bfv_mod
     PackedPlan plan = packed_plan(ctx, model, nX, pair_chunk);
     if (ws_bytes < plan.total) return BFV_ERR_OVER_BUDGET;
     cudaStream_t st = S(stream);
+    {
+        // on the caller's stream, before the graph is captured or launched (never inside it)
+        BoundsCall bc(ctx);
+        bounds_packed(bc, ctx, keys, 1, &model, &X_ct, &nX, &Y_ct, ws, ws_bytes);
+        BFV_BOUNDS_UPLOAD(bc, st);
+    }
     if (ctx->prof.on)   // per-launch event timing needs direct launches
         return launch_packed(ctx, keys, (const u64 *)X_ct, (u64 *)Y_ct, ws, plan, st);
     const size_t splits = plan.sched.prep_split | plan.sched.modup_split << 4 | plan.sched.moddown_p_split << 8 |
@@ -789,6 +875,9 @@ int bfv_lr_scores_packed_sched(bfv_ctx *ctx, const bfv_keys *keys, const bfv_mod
     if (!X_ct || !Y_ct || !ws) return BFV_ERR_INVALID_ARG;
     PackedPlan plan = packed_plan(ctx, model, nX, 0, sched);
     if (ws_bytes < plan.total) return BFV_ERR_OVER_BUDGET;
+    BoundsCall bc(ctx);
+    bounds_packed(bc, ctx, keys, 1, &model, &X_ct, &nX, &Y_ct, ws, ws_bytes);
+    BFV_BOUNDS_UPLOAD(bc, S(stream));
     return launch_packed(ctx, keys, (const u64 *)X_ct, (u64 *)Y_ct, ws, plan, S(stream));
 }
 
@@ -839,6 +928,11 @@ int bfv_autotune_packed_schedule(bfv_ctx *ctx, const bfv_keys *keys, const bfv_m
     if (!ctx || !keys || !model || keys->ctx != ctx || model->ctx != ctx || !best) return BFV_ERR_INVALID_ARG;
     if (nX == 0 || !X_ct || !Y_ct || !ws) return BFV_ERR_INVALID_ARG;
     cudaStream_t st = S(stream);
+    {
+        BoundsCall bc(ctx);
+        bounds_packed(bc, ctx, keys, 1, &model, &X_ct, &nX, &Y_ct, ws, ws_bytes);
+        BFV_BOUNDS_UPLOAD(bc, st);
+    }
     cudaEvent_t a = nullptr, b = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess) return BFV_ERR_CUDA;
     if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return BFV_ERR_CUDA; }
@@ -849,9 +943,9 @@ int bfv_autotune_packed_schedule(bfv_ctx *ctx, const bfv_keys *keys, const bfv_m
     uint32_t bfv_packed_schedule::*fields[] = {&bfv_packed_schedule::prep_split, &bfv_packed_schedule::modup_split,
                                                &bfv_packed_schedule::moddown_p_split,
                                                &bfv_packed_schedule::moddown_split};
-    const uint32_t values[4][3] = {{1, 2, 0}, {2, 4, 0}, {1, 2, 0}, {1, 2, 0}};   // 0 ends a list
+    const uint32_t values[4][4] = {{1, 2, 0, 0}, {2, 4, 0, 0}, {1, 2, 3, 0}, {1, 2, 0, 0}};   // 0 ends a list
     for (int f = 0; f < 4 && !rc; ++f) {
-        for (int v = 0; v < 3 && values[f][v] && !rc; ++v) {
+        for (int v = 0; v < 4 && values[f][v] && !rc; ++v) {
             bfv_packed_schedule cand = sc;
             cand.*fields[f] = values[f][v];
             if (cand.*fields[f] == sc.*fields[f]) continue;
@@ -882,6 +976,11 @@ int bfv_autotune_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *mod
     if (!ctx || !keys || !model || keys->ctx != ctx || model->ctx != ctx || !best_chunk) return BFV_ERR_INVALID_ARG;
     if (nX == 0 || !X_ct || !Y_ct || !ws) return BFV_ERR_INVALID_ARG;
     cudaStream_t st = S(stream);
+    {
+        BoundsCall bc(ctx);
+        bounds_packed(bc, ctx, keys, 1, &model, &X_ct, &nX, &Y_ct, ws, ws_bytes);
+        BFV_BOUNDS_UPLOAD(bc, st);
+    }
     cudaEvent_t a = nullptr, b = nullptr;
     if (cudaEventCreate(&a) != cudaSuccess) return BFV_ERR_CUDA;
     if (cudaEventCreate(&b) != cudaSuccess) { cudaEventDestroy(a); return BFV_ERR_CUDA; }
@@ -917,6 +1016,12 @@ int bfv_lr_scores_standard(bfv_ctx *ctx, const bfv_model *model, const uint64_t 
     const int wide = std::max(pl.split_bits, ctx->bits - pl.split_bits);
     if (model->wmax >= (1ll << 31) || (long double)model->wmax * model->f * (long double)(1ull << wide) >= 9.2e18L)
         return BFV_ERR_BAD_PARAMS;
+    BoundsCall bc(ctx);
+    bc.model(model);
+    bc.io(X_ct, sizeof(u64) * model->f * 2 * ctx->L * ctx->N);
+    bc.io(Y_ct, sizeof(u64) * model->nY * 2 * ctx->L * ctx->N);
+    bc.io(ws, ws_bytes);
+    BFV_BOUNDS_UPLOAD(bc, S(stream));
     return launch_standard(ctx, model, (const u64 *)X_ct, (u64 *)Y_ct, ws, pl, S(stream));
 }
 
@@ -924,7 +1029,7 @@ int bfv_set_option(bfv_ctx *ctx, int option, int value) {
     if (!ctx) return BFV_ERR_INVALID_ARG;
     switch (option) {
         case BFV_OPT_ENCRYPT_SPLIT:
-            if (value != 1 && value != 2) return BFV_ERR_INVALID_ARG;
+            if (value < 1 || value > 3) return BFV_ERR_INVALID_ARG;
             ctx->enc_split = value;
             return BFV_OK;
         case BFV_OPT_STANDARD_KERNEL:
@@ -945,10 +1050,30 @@ int bfv_get_option(const bfv_ctx *ctx, int option, int *value) {
 }
 
 int bfv_debug_inject(bfv_ctx *ctx, int what, int value) {
-    if (!ctx) return BFV_ERR_INVALID_ARG;
-    if (what != BFV_INJECT_STREAM_STALL || value < 0 || value % 16) return BFV_ERR_INVALID_ARG;
-    ctx->inject_extra_tx = value;
-    return BFV_OK;
+    if (!ctx || value < 0) return BFV_ERR_INVALID_ARG;
+    if (what == BFV_INJECT_STREAM_STALL) {
+        if (value % 16) return BFV_ERR_INVALID_ARG;
+        ctx->inject_extra_tx = value;
+        return BFV_OK;
+    }
+    if (what == BFV_INJECT_BOUNDS_SHRINK) {
+#ifdef BFV_BOUNDS
+        if (value % 8) return BFV_ERR_INVALID_ARG;
+        ctx->inject_shrink = value;
+        return BFV_OK;
+#else
+        return BFV_ERR_INVALID_ARG;   // only a bounds-checked build has the tables
+#endif
+    }
+    return BFV_ERR_INVALID_ARG;
+}
+
+int bfv_bounds_checked(void) {
+#ifdef BFV_BOUNDS
+    return 1;
+#else
+    return 0;
+#endif
 }
 
 int bfv_check_error(bfv_ctx *ctx, int *flags) {
@@ -967,6 +1092,10 @@ int bfv_lr_packed_pair_from_workspace(bfv_ctx *ctx, const bfv_model *model, size
     if (g >= plan.npairs) return BFV_ERR_INVALID_ARG;
     const size_t last_chunk_start = ((plan.npairs - 1) / plan.chunk) * plan.chunk;
     if (g < last_chunk_start) return BFV_ERR_INVALID_ARG;
+    BoundsCall bc(ctx);
+    bc.io(ws, plan.total);
+    bc.io(ct_out, sizeof(u64) * 2 * ctx->L * ctx->N);
+    BFV_BOUNDS_UPLOAD(bc, S(stream));
     int rc = launch_pair_export(ctx, plan, ws, g - last_chunk_start, (u64 *)ct_out, S(stream));
     if (rc) return rc;
     return cudaStreamSynchronize(S(stream)) == cudaSuccess ? BFV_OK : BFV_ERR_CUDA;
@@ -1025,6 +1154,12 @@ int bfv_lr_predict_packed(bfv_ctx *ctx, const bfv_keys *keys, const bfv_model *m
     if (!X || !scores || !ws) return BFV_ERR_INVALID_ARG;
     PredictPlan pl = predict_plan(ctx, model, nX, pair_chunk);
     if (ws_bytes < pl.total) return BFV_ERR_OVER_BUDGET;
+    BoundsCall bc(ctx);
+    bc.keys(keys);
+    bc.model(model);
+    bc.io(X, nX * model->f);
+    bc.io(ws, ws_bytes);
+    BFV_BOUNDS_UPLOAD(bc, S(stream));
     int rc = run_predict(ctx, keys, model, X, nX, seed, pl, (char *)ws, S(stream));
     if (rc) return rc;
     return cudaMemcpyAsync(scores, (char *)ws + pl.off_slots, nX * model->nY * 8, cudaMemcpyDeviceToDevice,
@@ -1041,6 +1176,11 @@ int bfv_lr_predict_packed_host(bfv_ctx *ctx, const bfv_keys *keys, const bfv_mod
     if (ws_bytes < pl.total) return BFV_ERR_OVER_BUDGET;
     char *w = (char *)ws;
     cudaStream_t st = S(stream);
+    BoundsCall bc(ctx);
+    bc.keys(keys);
+    bc.model(model);
+    bc.io(ws, ws_bytes);
+    BFV_BOUNDS_UPLOAD(bc, st);
     if (cudaMemcpyAsync(w + pl.off_x, X_host, nX * model->f, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return BFV_ERR_CUDA;
     int rc = run_predict(ctx, keys, model, (const uint8_t *)(w + pl.off_x), nX, seed, pl, w, st);

@@ -3,8 +3,8 @@
 // Pairs g = i*|Y| + j (numbered request by request when several requests, each with its own
 // model, share the product) are processed in chunks. Per chunk, in evaluation form:
 //   inputs       the chunk's individuals' ciphertexts -> evaluation form
-//   MAC          C[g] = sum_k X[i][k] (.) W[j][k]                         (Algorithm 1 lines 5-13)
-//   log2 N times C[g] += rot_gal(C[g])                                    (lines 14-17)
+//   MAC          C[g] = sum_k X[i][k] (.) W[j][k]          (Algorithm 1: multiply and add_many)
+//   log2 N times C[g] += rot_gal(C[g])                     (Algorithm 1: rotate and accumulate)
 //       rot(c) = (sigma(c0) + u0', u1'), (u0', u1') = KS(sigma(c1)):
 //       ks_prep     c1 limb l -> sigma -> inverse NTT -> digit d_l (coefficients)
 //       ks_modup    for target limb j of QP and part h of the evaluation points:
@@ -16,8 +16,8 @@
 //                   + KS(...)_0 exactly)
 //       ks_moddown_p  inverse NTT of U_c[P], r = [U_c[P] + floor(P/2)]_P
 //       ks_moddown  C_c[l] += (U_c[l] + NTT_l(floor(P/2) - r)) * P^-1
-//   bias+mask    C0 += Delta b_j; C *= NTT(mask_g), mask_g one-hot at slot g mod N (18-22)
-//   compress     Yacc[g / N] += C[g]                                       (25-42)
+//   bias+mask    C0 += Delta b_j; C *= NTT(mask_g), mask_g one-hot at slot g mod N (Algorithm 1: mask)
+//   compress     Yacc[g / N] += C[g]                       (Algorithm 1: compression)
 // and finally Y = inverse NTT(Yacc).
 //
 // How each key-switching kernel splits a limb over CTAs (the schedule) is a run-time choice
@@ -40,7 +40,7 @@ __device__ __forceinline__ int req_of(const ReqTable &rt, size_t p) {
     return r;
 }
 
-// ------------------------------------------------------------------ MAC (lines 5-13)
+// ------------------------------------------------------------------ MAC (Algorithm 1: multiply, add_many)
 // C[g][c][l][p] = sum_k Xe[i][k][c][l][p] * We[j][k][l][p] with the model of the pair's
 // request; grid.x = (g, c, l), grid.y = tile.
 __global__ void __launch_bounds__(256) k_mac(const ModTab *__restrict__ mods, int N, int L, size_t g0,
@@ -54,7 +54,7 @@ __global__ void __launch_bounds__(256) k_mac(const ModTab *__restrict__ mods, in
     const long long x0 = rt.xoff[r] + (long long)(g / nY) * K;
     const size_t j = g % nY;
     const shoup_t *__restrict__ We = rt.w[r];
-    const u64 q = mods[l].q, q2 = 2 * q;
+    const u64 q = BFV_LD(&mods[l].q), q2 = 2 * q;
     const size_t ctw = 2 * (size_t)L * N;
     const int p0 = blockIdx.y * 1024 + threadIdx.x;
 #pragma unroll
@@ -63,11 +63,11 @@ __global__ void __launch_bounds__(256) k_mac(const ModTab *__restrict__ mods, in
         if (p >= N) break;
         u64 acc = 0;
         for (int k = 0; k < K; ++k) {
-            const u64 xv = Xe[(size_t)(x0 + k) * ctw + ((size_t)c * L + l) * N + p];
-            const shoup_t w = __ldg(We + ((j * K + k) * L + l) * (size_t)N + p);
+            const u64 xv = BFV_LD(Xe + (size_t)(x0 + k) * ctw + ((size_t)c * L + l) * N + p);
+            const shoup_t w = BFV_LDG(We + ((j * K + k) * L + l) * (size_t)N + p);
             acc = red2(acc + mul_shoup(xv, w, q), q2);
         }
-        C[gl * ctw + ((size_t)c * L + l) * N + p] = red1(acc, q);
+        BFV_ST(C + gl * ctw + ((size_t)c * L + l) * N + p, red1(acc, q));
     }
 }
 
@@ -83,15 +83,15 @@ LIMB_KERNEL_M(LOGN, MODE) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 
     constexpr int NT = Split<LOGN, MODE>::NT, S = Split<LOGN, MODE>::S;
     const int l = (int)(unit % L);
     const size_t g = unit / L;
-    const ModTab T = mods[l];
+    const ModTab T = BFV_LD(mods + l);
     const u64 *limb = C + ((g * 2 + 1) * L + l) * (size_t)N;
     u64 *dst = D + (g * L + l) * (size_t)N;
     // the permuted reads below touch the whole limb in random order: bring it into L2 with
     // coalesced line prefetches first (each CTA of the group a share of the lines)
     for (int i = threadIdx.x + h * NT; i < N / 16; i += S * NT)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(limb + 16 * i));
-    limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return limb[auto_src(p, gal, LOGN)]; },
-                             [&](int p, u64 v) { dst[p] = v; });
+    limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return BFV_LD(limb + auto_src(p, gal, LOGN)); },
+                             [&](int p, u64 v) { BFV_ST(dst + p, v); });
 }
 
 // ModUp works on parts of H = N / SPLIT evaluation points of a target limb (SPLIT = 2 or 4):
@@ -139,8 +139,8 @@ __device__ __forceinline__ void key_mac(u32 tacc, const shoup_t *__restrict__ k0
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int p = threadIdx.x + (e0 + e) * NT;
-            a[e] = __ldg(k0 + p);
-            b[e] = __ldg(k1 + p);
+            a[e] = BFV_LDG(k0 + p);
+            b[e] = BFV_LDG(k1 + p);
             val(p, v[e], x0[e]);
         }
         u32 r[16];
@@ -175,7 +175,7 @@ __global__ void __launch_bounds__(ModUpShape<LOGN, SPLIT>::NT, ModUpShape<LOGN, 
     const int nqp = L + 1;
     const int h = blockIdx.x % SPLIT, j = (blockIdx.x / SPLIT) % nqp;
     const size_t g = blockIdx.x / (SPLIT * nqp);
-    const ModTab T = mods[j];
+    const ModTab T = BFV_LD(mods + j);
     const u64 q = T.q;
     const int warp = threadIdx.x >> 5;
     if (warp == 0) tmem_alloc(tslot, MS::COLS);
@@ -202,8 +202,8 @@ __global__ void __launch_bounds__(ModUpShape<LOGN, SPLIT>::NT, ModUpShape<LOGN, 
             const u64 *c1 = C + ((g * 2 + 1) * L + j) * (size_t)N;
             key_mac<H, NT, true>(tacc, k0, k1, q, [&](int p, u64 &v, u64 &x0) {
                 const int src = auto_src(h * H + p, gal, LOGN);
-                v = c1[src];
-                x0 = mul_shoup(c0[src], T.pmod, T.pmodp, q);
+                v = BFV_LD(c1 + src);
+                x0 = mul_shoup(BFV_LD(c0 + src), T.pmod, T.pmodp, q);
             });
         } else {
             const u64 *d = D + (g * L + i) * (size_t)N;   // digit i < q_i < 2 q_j
@@ -212,7 +212,7 @@ __global__ void __launch_bounds__(ModUpShape<LOGN, SPLIT>::NT, ModUpShape<LOGN, 
                 [&](int p) {
                     u64 v[SPLIT];
 #pragma unroll
-                    for (int k = 0; k < SPLIT; ++k) v[k] = d[p + k * H];
+                    for (int k = 0; k < SPLIT; ++k) v[k] = BFV_LD(d + p + k * H);
                     return fold_stages<MS::LOGS>(T, h, v);
                 },
                 [&](int p, u64 v) { sm[padi(p)] = v; });
@@ -232,8 +232,8 @@ __global__ void __launch_bounds__(ModUpShape<LOGN, SPLIT>::NT, ModUpShape<LOGN, 
         for (int e = 0; e < 4; ++e) {
             const int p = threadIdx.x + (e0 + e) * NT;
             const u64 s0 = ((u64)r[4 * e + 1] << 32) | r[4 * e], s1 = ((u64)r[4 * e + 3] << 32) | r[4 * e + 2];
-            u0[p] = red1(mul_shoup(s0, 1, T.onep, q), q);
-            u1[p] = red1(mul_shoup(s1, 1, T.onep, q), q);
+            BFV_ST(u0 + p, red1(mul_shoup(s0, 1, T.onep, q), q));
+            BFV_ST(u1 + p, red1(mul_shoup(s1, 1, T.onep, q), q));
         }
     }
     tmem_fence_before_sync();
@@ -250,11 +250,11 @@ LIMB_KERNEL_M(LOGN, MODE) k_ks_moddown_p(const ModTab *__restrict__ mods, int L,
     LIMB_INDEX_M(LOGN, MODE);
     const int nqp = L + 1;
     const size_t gc = unit;
-    const ModTab T = mods[L];
+    const ModTab T = BFV_LD(mods + L);
     const u64 *src = U + (gc * nqp + L) * (size_t)N;
     u64 *dst = R + gc * N;
-    limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return src[p]; },
-                             [&](int p, u64 v) { dst[p] = add_mod(v, T.phalf, T.q); });
+    limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return BFV_LD(src + p); },
+                             [&](int p, u64 v) { BFV_ST(dst + p, add_mod(v, T.phalf, T.q)); });
 }
 
 // Limb unit (g, c, l): C[g][c][l] += (U[g][c][l] + NTT_l(floor(P/2) - r)) * P^-1. Split mode 1:
@@ -268,9 +268,9 @@ LIMB_KERNEL_M(LOGN, MODE) k_ks_moddown(const ModTab *__restrict__ mods, int L, c
     const int nqp = L + 1;
     const int l = (int)(unit % L), c = (int)((unit / L) % 2);
     const size_t g = unit / (2 * L);
-    const ModTab T = mods[l];
+    const ModTab T = BFV_LD(mods + l);
     const u64 *r = R + (g * 2 + c) * (size_t)N;
-    limb_forward<LOGN, true, MODE>(sm, T, h, [&](int p) { return T.phalf + (T.q - red1(r[p], T.q)); },
+    limb_forward<LOGN, true, MODE>(sm, T, h, [&](int p) { return T.phalf + (T.q - red1(BFV_LD(r + p), T.q)); },
                        [&](int p, u64 v) { sm[padi(p & (M - 1))] = v; });
     __syncthreads();
     const u64 *u = U + ((g * 2 + c) * nqp + l) * (size_t)N + (size_t)h * M;
@@ -280,17 +280,17 @@ LIMB_KERNEL_M(LOGN, MODE) k_ks_moddown(const ModTab *__restrict__ mods, int L, c
     for (int p0 = threadIdx.x; p0 < M; p0 += 4 * NT) {
         u64 a[4], b[4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) { a[e] = u[p0 + e * NT]; b[e] = dst[p0 + e * NT]; }
+        for (int e = 0; e < 4; ++e) { a[e] = BFV_LD(u + p0 + e * NT); b[e] = BFV_LD(dst + p0 + e * NT); }
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
             const int p = p0 + e * NT;
             const u64 v = red1(mul_shoup(a[e] + sm[padi(p)], T.pinv, T.pinvp, T.q), T.q);
-            dst[p] = add_mod(b[e], v, T.q);
+            BFV_ST(dst + p, add_mod(b[e], v, T.q));
         }
     }
 }
 
-// ------------------------------------------------------------------ bias + mask (lines 18-22)
+// ------------------------------------------------------------------ bias + mask (Algorithm 1: mask)
 // Limb unit (g, l): C0 += Delta [b_j]_t; C *= NTT(centred lift of the one-hot plaintext at slot
 // (g0+g) mod N), whose coefficient k is N^-1 omega^(-e k) mod t, e the slot's exponent.
 template <int LOGN>
@@ -304,8 +304,8 @@ LIMB_KERNEL(LOGN) k_bias_mask(const ModTab *__restrict__ mods, int L, int tmod, 
     const int r = req_of(rt, gp);
     const size_t g = gp - rt.pair_start[r];
     const int j = (int)(g % rt.nY[r]), s = (int)(g % N);
-    const ModTab T = mods[l];
-    const u64 t = mods[tmod].q, th = (t - 1) / 2;
+    const ModTab T = BFV_LD(mods + l);
+    const u64 t = BFV_LD(&mods[tmod].q), th = (t - 1) / 2;
     const u32 twoN = 2u * N;
     u32 e = 1, base = 3;                               // e = 3^(s mod N/2) mod 2N
     for (u32 x = (u32)(s % (N / 2)); x; x >>= 1) {
@@ -317,39 +317,39 @@ LIMB_KERNEL(LOGN) k_bias_mask(const ModTab *__restrict__ mods, int L, int tmod, 
         sm, T, h,
         [&](int p) {
             const u32 idx = (twoN - ((e * (u32)p) & (twoN - 1))) & (twoN - 1);
-            const u64 v = maskpow[idx];
+            const u64 v = BFV_LD(maskpow + idx);
             return v <= th ? v : T.q - (t - v);
         },
         [&](int p, u64 v) { sm[padi(p & (M - 1))] = v; });
     __syncthreads();
-    const u64 bd = rt.bias[r][(size_t)j * L + l];
+    const u64 bd = BFV_LD(rt.bias[r] + (size_t)j * L + l);
     u64 *c0 = C + ((gl * 2 + 0) * L + l) * (size_t)N + (size_t)h * M;
     u64 *c1 = C + ((gl * 2 + 1) * L + l) * (size_t)N + (size_t)h * M;
     for (int p = threadIdx.x; p < M; p += NT) {
         const u64 m = sm[padi(p)];
-        c0[p] = mul_barrett(add_mod(c0[p], bd, T.q), m, T.q, T.mu, T.bits);
-        c1[p] = mul_barrett(c1[p], m, T.q, T.mu, T.bits);
+        BFV_ST(c0 + p, mul_barrett(add_mod(BFV_LD(c0 + p), bd, T.q), m, T.q, T.mu, T.bits));
+        BFV_ST(c1 + p, mul_barrett(BFV_LD(c1 + p), m, T.q, T.mu, T.bits));
     }
 }
 
-// ------------------------------------------------------------------ compression (lines 25-42)
+// ------------------------------------------------------------------ compression (Algorithm 1: compression)
 // Yacc[e] += sum_{g in [ga, gb)} C[g - g0][e] for every element e of one output ciphertext.
 __global__ void __launch_bounds__(256) k_compress(const ModTab *__restrict__ mods, int N, int L, size_t ga, size_t gb,
                                                   size_t g0, const u64 *__restrict__ C, u64 *Yacc) {
     const size_t ctw = 2 * (size_t)L * N;
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= ctw) return;
-    const u64 q = mods[(e / N) % L].q;
-    u64 acc = Yacc[e];
+    const u64 q = BFV_LD(&mods[(e / N) % L].q);
+    u64 acc = BFV_LD(Yacc + e);
     size_t g = ga;
     for (; g + 4 <= gb; g += 4) {
-        const u64 a = C[(g - g0) * ctw + e], b = C[(g + 1 - g0) * ctw + e];
-        const u64 c = C[(g + 2 - g0) * ctw + e], d = C[(g + 3 - g0) * ctw + e];
+        const u64 a = BFV_LD(C + (g - g0) * ctw + e), b = BFV_LD(C + (g + 1 - g0) * ctw + e);
+        const u64 c = BFV_LD(C + (g + 2 - g0) * ctw + e), d = BFV_LD(C + (g + 3 - g0) * ctw + e);
         acc = red1(acc + red1(a + b, q), q);
         acc = red1(acc + red1(c + d, q), q);
     }
-    for (; g < gb; ++g) acc = red1(acc + C[(g - g0) * ctw + e], q);
-    Yacc[e] = acc;
+    for (; g < gb; ++g) acc = red1(acc + BFV_LD(C + (g - g0) * ctw + e), q);
+    BFV_ST(Yacc + e, acc);
 }
 
 // Pair state (evaluation form) -> coefficient form; limb unit x uses modulus x % L.
@@ -358,8 +358,9 @@ LIMB_KERNEL(LOGN) k_intt_copy(const ModTab *__restrict__ mods, int L, const u64 
     extern __shared__ u64 sm[];
     LIMB_INDEX(LOGN);
     const size_t x = unit;
-    const ModTab T = mods[x % L];
-    limb_inverse<LOGN>(sm, T, h, [&](int p) { return in[x * N + p]; }, [&](int p, u64 v) { out[x * N + p] = v; });
+    const ModTab T = BFV_LD(mods + x % L);
+    limb_inverse<LOGN>(sm, T, h, [&](int p) { return BFV_LD(in + x * N + p); },
+                       [&](int p, u64 v) { BFV_ST(out + x * N + p, v); });
 }
 
 int last_err() { return cudaGetLastError() == cudaSuccess ? BFV_OK : BFV_ERR_CUDA; }
@@ -401,7 +402,9 @@ void ks_step(const bfv_ctx *c, const bfv_packed_schedule &sc, size_t ng, u32 gal
         ProfScope pr(c, BFV_K_KS_MODDOWN_P, st);
         const bool two = sc.moddown_p_split == 2 || (sc.moddown_p_split == 0 && ng * 2 < (size_t)2 * c->sms);
         if constexpr (PAIRS) {
-            if (two) launch_limbs<LOGN, 1>(k_ks_moddown_p<LOGN, 1>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R);
+            if (sc.moddown_p_split == 3)
+                launch_limbs<LOGN, 3>(k_ks_moddown_p<LOGN, 3>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R);
+            else if (two) launch_limbs<LOGN, 1>(k_ks_moddown_p<LOGN, 1>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R);
             else launch_limbs<LOGN, 0>(k_ks_moddown_p<LOGN, 0>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R);
         } else {
             (void)two;
@@ -477,6 +480,10 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, int nreq, const u64 *const *
 
 }  // namespace
 
+#ifdef BFV_BOUNDS
+BFV_BOUNDS_UPLOAD_FN(bounds_upload_packed)
+#endif
+
 static size_t al256(size_t x) { return (x + 255) & ~(size_t)255; }
 
 bfv_packed_schedule default_schedule() {
@@ -491,7 +498,7 @@ bfv_packed_schedule default_schedule() {
 
 bool schedule_ok(const bfv_packed_schedule &s) {
     return s.pair_chunk >= 1 && (s.prep_split == 1 || s.prep_split == 2) &&
-           (s.modup_split == 2 || s.modup_split == 4) && s.moddown_p_split <= 2 &&
+           (s.modup_split == 2 || s.modup_split == 4) && s.moddown_p_split <= 3 &&
            (s.moddown_split == 1 || s.moddown_split == 2);
 }
 

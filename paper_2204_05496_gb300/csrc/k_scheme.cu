@@ -23,13 +23,13 @@ template <int LOGN, bool FWD>
 LIMB_KERNEL(LOGN) k_ntt_limbs(const ModTab *__restrict__ mods, int L, const u64 *in, u64 *out) {
     extern __shared__ u64 sm[];
     LIMB_INDEX(LOGN);
-    const ModTab T = mods[unit % L];
+    const ModTab T = BFV_LD(mods + unit % L);
     const u64 *src = in + unit * N;
     u64 *dst = out + unit * N;
     if constexpr (FWD)
-        limb_forward<LOGN, true>(sm, T, h, [&](int p) { return src[p]; }, [&](int p, u64 v) { dst[p] = v; });
+        limb_forward<LOGN, true>(sm, T, h, [&](int p) { return BFV_LD(src + p); }, [&](int p, u64 v) { BFV_ST(dst + p, v); });
     else
-        limb_inverse<LOGN>(sm, T, h, [&](int p) { return src[p]; }, [&](int p, u64 v) { dst[p] = v; });
+        limb_inverse<LOGN>(sm, T, h, [&](int p) { return BFV_LD(src + p); }, [&](int p, u64 v) { BFV_ST(dst + p, v); });
 }
 
 // Inverse transform of evaluation-form {value, companion} arrays [limb][N]; limb x uses
@@ -38,10 +38,10 @@ template <int LOGN>
 LIMB_KERNEL(LOGN) k_intt_pairs(const ModTab *__restrict__ mods, int nmod, const shoup_t *__restrict__ in, u64 *out) {
     extern __shared__ u64 sm[];
     LIMB_INDEX(LOGN);
-    const ModTab T = mods[unit % nmod];
+    const ModTab T = BFV_LD(mods + unit % nmod);
     const shoup_t *src = in + unit * N;
     u64 *dst = out + unit * N;
-    limb_inverse<LOGN>(sm, T, h, [&](int p) { return src[p].x; }, [&](int p, u64 v) { dst[p] = v; });
+    limb_inverse<LOGN>(sm, T, h, [&](int p) { return BFV_LD(&src[p].x); }, [&](int p, u64 v) { BFV_ST(dst + p, v); });
 }
 
 // ------------------------------------------------------------------ encode / decode (mod t)
@@ -54,19 +54,19 @@ LIMB_KERNEL(LOGN) k_encode(const ModTab *__restrict__ mods, int tmod, const u32 
                            const int64_t *slots, u64 *pt) {
     extern __shared__ u64 sm[];
     LIMB_INDEX(LOGN);
-    const ModTab T = mods[tmod];
+    const ModTab T = BFV_LD(mods + tmod);
     const int64_t *src = slots + unit * N;
     const int64_t t = (int64_t)T.q;
     for (int l = threadIdx.x; l < N; l += Split<LOGN>::NT) {
-        const u32 pos = slot_pos[l];
+        const u32 pos = BFV_LD(slot_pos + l);
         if ((int)(pos / M) != h) continue;
-        int64_t v = src[l] % t;
+        int64_t v = BFV_LD(src + l) % t;
         if (v < 0) v += t;
         sm[padi(pos % M)] = (u64)v;
     }
     __syncthreads();
     u64 *dst = pt + unit * N;
-    limb_inverse<LOGN>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) { dst[p] = v; });
+    limb_inverse<LOGN>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) { BFV_ST(dst + p, v); });
 }
 
 // Packed features: plaintext (i, k) slot s = X[i][k N + s] (0 past f).
@@ -75,18 +75,19 @@ LIMB_KERNEL(LOGN) k_encode_features(const ModTab *__restrict__ mods, int tmod, c
                                     const uint8_t *__restrict__ X, size_t f, int K, u64 *pt) {
     extern __shared__ u64 sm[];
     LIMB_INDEX(LOGN);
-    const ModTab T = mods[tmod];
+    const ModTab T = BFV_LD(mods + tmod);
     const size_t i = unit / K, k = unit % K;
     const uint8_t *row = X + i * f;
     for (int s = threadIdx.x; s < N; s += Split<LOGN>::NT) {
-        const u32 pos = slot_pos[s];
+        const u32 pos = BFV_LD(slot_pos + s);
         if ((int)(pos / M) != h) continue;
         const size_t col = k * N + s;
-        sm[padi(pos % M)] = col < f ? (u64)row[col] % T.q : 0;
+        const u64 v = col < f ? (u64)BFV_LD(row + col) : 0;
+        sm[padi(pos % M)] = v < T.q ? v : v % T.q;
     }
     __syncthreads();
     u64 *dst = pt + unit * N;
-    limb_inverse<LOGN>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) { dst[p] = v; });
+    limb_inverse<LOGN>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) { BFV_ST(dst + p, v); });
 }
 
 // Feature columns: plaintext f' slot i = X[i][f'] for i < nX.
@@ -95,16 +96,17 @@ LIMB_KERNEL(LOGN) k_encode_columns(const ModTab *__restrict__ mods, int tmod, co
                                    const uint8_t *__restrict__ X, size_t nX, size_t f, u64 *pt) {
     extern __shared__ u64 sm[];
     LIMB_INDEX(LOGN);
-    const ModTab T = mods[tmod];
+    const ModTab T = BFV_LD(mods + tmod);
     const size_t col = unit;
     for (int s = threadIdx.x; s < N; s += Split<LOGN>::NT) {
-        const u32 pos = slot_pos[s];
+        const u32 pos = BFV_LD(slot_pos + s);
         if ((int)(pos / M) != h) continue;
-        sm[padi(pos % M)] = (size_t)s < nX ? (u64)X[s * f + col] % T.q : 0;
+        const u64 v = (size_t)s < nX ? (u64)BFV_LD(X + s * f + col) : 0;
+        sm[padi(pos % M)] = v < T.q ? v : v % T.q;
     }
     __syncthreads();
     u64 *dst = pt + col * N;
-    limb_inverse<LOGN>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) { dst[p] = v; });
+    limb_inverse<LOGN>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) { BFV_ST(dst + p, v); });
 }
 
 template <int LOGN>
@@ -112,14 +114,14 @@ LIMB_KERNEL(LOGN) k_decode(const ModTab *__restrict__ mods, int tmod, const u32 
                            int64_t *slots) {
     extern __shared__ u64 sm[];
     LIMB_INDEX(LOGN);
-    const ModTab T = mods[tmod];
+    const ModTab T = BFV_LD(mods + tmod);
     const u64 *src = pt + unit * N;
-    limb_forward<LOGN>(sm, T, h, [&](int p) { return src[p]; }, [&](int p, u64 v) { sm[padi(p & (M - 1))] = v; });
+    limb_forward<LOGN>(sm, T, h, [&](int p) { return BFV_LD(src + p); }, [&](int p, u64 v) { sm[padi(p & (M - 1))] = v; });
     __syncthreads();
     int64_t *dst = slots + unit * N;
     for (int l = threadIdx.x; l < N; l += Split<LOGN>::NT) {
-        const u32 pos = slot_pos[l];
-        if ((int)(pos / M) == h) dst[l] = (int64_t)sm[padi(pos % M)];
+        const u32 pos = BFV_LD(slot_pos + l);
+        if ((int)(pos / M) == h) BFV_ST(dst + l, (int64_t)sm[padi(pos % M)]);
     }
 }
 
@@ -130,7 +132,7 @@ __global__ void k_keygen_sk(u64 seed, int N, int8_t *sk) {
     if (k >= N) return;
     u32 w[16];
     chacha20_block(seed, (u32)k, kSkPurpose, 0, 0, w);
-    sk[k] = (int8_t)ternary_of(w[0]);
+    BFV_ST(sk + k, (int8_t)ternary_of(w[0]));
 }
 
 // Evaluation form of s for every modulus of QP: out [nqp][N] {value, companion}.
@@ -138,10 +140,10 @@ template <int LOGN>
 LIMB_KERNEL(LOGN) k_keygen_sk_eval(const ModTab *__restrict__ mods, const int8_t *__restrict__ sk, shoup_t *out) {
     extern __shared__ u64 sm[];
     LIMB_INDEX(LOGN);
-    const ModTab T = mods[unit];
+    const ModTab T = BFV_LD(mods + unit);
     shoup_t *dst = out + unit * N;
-    limb_forward<LOGN>(sm, T, h, [&](int p) { return lift_small(sk[p], T.q); },
-                       [&](int p, u64 v) { dst[p] = make_shoup(v, T.q); });
+    limb_forward<LOGN>(sm, T, h, [&](int p) { return lift_small(BFV_LD(sk + p), T.q); },
+                       [&](int p, u64 v) { BFV_ST(dst + p, make_shoup(v, T.q)); });
 }
 
 // Public key limb l: pk1 = a (uniform), pk0 = -(a s + e); out [2][L][N] {value, companion}.
@@ -151,21 +153,21 @@ LIMB_KERNEL(LOGN) k_keygen_pk(const ModTab *__restrict__ mods, const u64 *__rest
     extern __shared__ u64 sm[];
     LIMB_INDEX(LOGN);
     const int l = (int)unit;
-    const ModTab T = mods[l];
+    const ModTab T = BFV_LD(mods + l);
     shoup_t *pk0 = pk + (size_t)l * N, *pk1 = pk + ((size_t)L + l) * N;
     const shoup_t *s = sk_eval + (size_t)l * N;
     limb_forward<LOGN>(
         sm, T, h,
         [&](int p) { u32 w[16]; chacha20_block(seed, (u32)p, kPkA, 0, (u32)l, w); return uniform_of(w, T); },
         [&](int p, u64 v) {
-            pk1[p] = make_shoup(v, T.q);
-            pk0[p].x = red1(mul_shoup(v, s[p], T.q), T.q);   // a s, finished below
+            BFV_ST(pk1 + p, make_shoup(v, T.q));
+            BFV_ST(&pk0[p].x, red1(mul_shoup(v, BFV_LD(s + p), T.q), T.q));   // a s, finished below
         });
     __syncthreads();
     limb_forward<LOGN>(
         sm, T, h,
         [&](int p) { u32 w[16]; chacha20_block(seed, (u32)p, kPkE, 0, 0, w); return lift_small(gauss_of(w[0], w[1], w[2], cdt, cdt_len), T.q); },
-        [&](int p, u64 v) { pk0[p] = make_shoup(sub_mod(0, add_mod(pk0[p].x, v, T.q), T.q), T.q); });
+        [&](int p, u64 v) { BFV_ST(pk0 + p, make_shoup(sub_mod(0, add_mod(BFV_LD(&pk0[p].x), v, T.q), T.q), T.q)); });
 }
 
 // Galois key (element gi, digit i, limb j of QP):
@@ -177,9 +179,9 @@ LIMB_KERNEL(LOGN) k_keygen_galois(const ModTab *__restrict__ mods, const u64 *__
     LIMB_INDEX(LOGN);
     const int nqp = L + 1;
     const int j = (int)(unit % nqp), i = (int)((unit / nqp) % L), gi = (int)(unit / ((size_t)nqp * L));
-    const ModTab T = mods[j];
+    const ModTab T = BFV_LD(mods + j);
     const u32 obj = (u32)gi * 256u + (u32)i;
-    const u32 g = (u32)gal[gi];
+    const u32 g = (u32)BFV_LD(gal + gi);
     shoup_t *k0 = gk + ((((size_t)gi * L + i) * 2 + 0) * nqp + j) * N;
     shoup_t *k1 = gk + ((((size_t)gi * L + i) * 2 + 1) * nqp + j) * N;
     const shoup_t *s = sk_eval + (size_t)j * N;
@@ -187,18 +189,18 @@ LIMB_KERNEL(LOGN) k_keygen_galois(const ModTab *__restrict__ mods, const u64 *__
         sm, T, h,
         [&](int p) { u32 w[16]; chacha20_block(seed, (u32)p, kGkA, obj, (u32)j, w); return uniform_of(w, T); },
         [&](int p, u64 v) {
-            k1[p] = make_shoup(v, T.q);
-            k0[p].x = red1(mul_shoup(v, s[p], T.q), T.q);
+            BFV_ST(k1 + p, make_shoup(v, T.q));
+            BFV_ST(&k0[p].x, red1(mul_shoup(v, BFV_LD(s + p), T.q), T.q));
         });
     __syncthreads();
-    const u64 pmod = mods[L].q % T.q;
+    const u64 pmod = BFV_LD(&mods[L].q) % T.q;
     limb_forward<LOGN>(
         sm, T, h,
         [&](int p) { u32 w[16]; chacha20_block(seed, (u32)p, kGkE, obj, 0, w); return lift_small(gauss_of(w[0], w[1], w[2], cdt, cdt_len), T.q); },
         [&](int p, u64 v) {
-            u64 r = sub_mod(v, k0[p].x, T.q);
-            if (i == j) r = add_mod(r, mul_barrett(pmod, s[auto_src(p, g, LOGN)].x, T.q, T.mu, T.bits), T.q);
-            k0[p] = make_shoup(r, T.q);
+            u64 r = sub_mod(v, BFV_LD(&k0[p].x), T.q);
+            if (i == j) r = add_mod(r, mul_barrett(pmod, BFV_LD(&s[auto_src(p, g, LOGN)].x), T.q, T.mu, T.bits), T.q);
+            BFV_ST(k0 + p, make_shoup(r, T.q));
         });
 }
 
@@ -214,9 +216,9 @@ __global__ void k_enc_sample(const u64 *__restrict__ cdt, int cdt_len, u64 seed,
     u32 w[16];
     chacha20_block(seed, (u32)k, kEnc, obj0 + (u32)c, 0, w);
     int8_t *dst = ws + c * 3 * N;
-    dst[k] = (int8_t)ternary_of(w[0]);
-    dst[N + k] = (int8_t)gauss_of(w[1], w[2], w[3], cdt, cdt_len);
-    dst[2 * N + k] = (int8_t)gauss_of(w[4], w[5], w[6], cdt, cdt_len);
+    BFV_ST(dst + k, (int8_t)ternary_of(w[0]));
+    BFV_ST(dst + N + k, (int8_t)gauss_of(w[1], w[2], w[3], cdt, cdt_len));
+    BFV_ST(dst + 2 * N + k, (int8_t)gauss_of(w[4], w[5], w[6], cdt, cdt_len));
 }
 
 // Limb unit (c, l): both components of ciphertext c on limb l from one transform of u:
@@ -233,23 +235,44 @@ LIMB_KERNEL_M(LOGN, MODE) k_enc_main(const ModTab *__restrict__ mods, int L, con
     LIMB_INDEX_M(LOGN, MODE);
     const int l = (int)(unit % L);
     const size_t c = unit / L;
-    const ModTab T = mods[l];
+    const ModTab T = BFV_LD(mods + l);
     const int8_t *u = rnd + c * 3 * N, *e1 = u + N, *e2 = u + 2 * (size_t)N;
     const shoup_t *k0 = pk + (size_t)l * N, *k1 = pk + ((size_t)L + l) * N;
     const u64 *m = pt + c * N;
     u64 *out0 = ct + ((c * 2 + 0) * L + l) * (size_t)N, *out1 = ct + ((c * 2 + 1) * L + l) * (size_t)N;
-    limb_forward<LOGN, true, MODE>(sm, T, h, [&](int p) { return lift_small(u[p], T.q); }, [&](int p, u64 v) {
-        sm[padi(p & (M - 1))] = mul_shoup(v, k0[p], T.q);
-        out1[p] = mul_shoup(v, k1[p], T.q);
-    });
+    constexpr int NT = Split<LOGN, MODE>::NT;
+    limb_forward<LOGN, true, MODE, MODE == 2>(sm, T, h, [&](int p) { return lift_small(BFV_LD(u + p), T.q); },
+                                              [&](int p, u64 v) { sm[padi(p & (M - 1))] = v; });
+    __syncthreads();
+    // the public-key products in a pass of their own, four points per thread with their key loads
+    // issued together: pk0 u stays in shared memory, pk1 u waits in comp 1's output limb
+    static_assert(M % (4 * NT) == 0, "points per thread must be a multiple of 4");
+#pragma unroll 1
+    for (int p0 = threadIdx.x; p0 < M; p0 += 4 * NT) {
+        shoup_t a[4], b[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            a[e] = BFV_LD(k0 + h * M + p0 + e * NT);
+            b[e] = BFV_LD(k1 + h * M + p0 + e * NT);
+        }
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+            const int p = p0 + e * NT;
+            const u64 v = sm[padi(p)];
+            sm[padi(p)] = mul_shoup(v, a[e], T.q);
+            BFV_ST(out1 + h * M + p, mul_shoup(v, b[e], T.q));
+        }
+    }
     __syncthreads();
     limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) {
-        const u64 r = add_mod(v, lift_small(e1[p], T.q), T.q);
-        out0[p] = add_mod(r, mul_barrett(T.delta, m[p] % T.q, T.q, T.mu, T.bits), T.q);
+        const u64 r = add_mod(v, lift_small(BFV_LD(e1 + p), T.q), T.q);
+        // plaintext coefficients lie in [0, t) with t < q; reduce other words only when needed
+        const u64 mv = BFV_LD(m + p), mr = mv < T.q ? mv : mv % T.q;
+        BFV_ST(out0 + p, add_mod(r, red1(mul_shoup(mr, T.delta, T.deltap, T.q), T.q), T.q));
     });
     __syncthreads();
-    limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return out1[p]; },
-                             [&](int p, u64 v) { out1[p] = add_mod(v, lift_small(e2[p], T.q), T.q); });
+    limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return BFV_LD(out1 + p); },
+                             [&](int p, u64 v) { BFV_ST(out1 + p, add_mod(v, lift_small(BFV_LD(e2 + p), T.q), T.q)); });
 }
 
 // ------------------------------------------------------------------ decryption
@@ -262,15 +285,15 @@ LIMB_KERNEL(LOGN) k_dec_inner(const ModTab *__restrict__ mods, int L, const shou
     LIMB_INDEX(LOGN);
     const int l = (int)(unit % L);
     const size_t c = unit / L;
-    const ModTab T = mods[l];
+    const ModTab T = BFV_LD(mods + l);
     const u64 *c0 = ct + (c * 2 * L + l) * (size_t)N, *c1 = ct + ((c * 2 + 1) * L + l) * (size_t)N;
     const shoup_t *s = sk_eval + (size_t)l * N;
-    limb_forward<LOGN, true>(sm, T, h, [&](int p) { return c1[p]; },
-                       [&](int p, u64 v) { sm[padi(p & (M - 1))] = mul_shoup(v, s[p], T.q); });
+    limb_forward<LOGN, true>(sm, T, h, [&](int p) { return BFV_LD(c1 + p); },
+                       [&](int p, u64 v) { sm[padi(p & (M - 1))] = mul_shoup(v, BFV_LD(s + p), T.q); });
     __syncthreads();
     u64 *dst = x + (c * L + l) * (size_t)N;
     limb_inverse<LOGN>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; },
-                       [&](int p, u64 v) { dst[p] = add_mod(v, c0[p], T.q); });
+                       [&](int p, u64 v) { BFV_ST(dst + p, add_mod(v, BFV_LD(c0 + p), T.q)); });
 }
 
 // Residues v_0..v_{L-1} (v_i < q_i, overwritten) -> the integer x in [0, Q) with x = v_i mod q_i
@@ -279,7 +302,7 @@ __device__ __forceinline__ void crt_words(const ModTab *__restrict__ mods, const
                                           u64 (&v)[BFV_MAXP], u64 (&w)[BFV_MAXW]) {
     const int L = dc->L, W = dc->W;
     for (int i = 0; i < L; ++i) {
-        const u64 qi = mods[i].q;
+        const u64 qi = BFV_LD(&mods[i].q);
         u64 a = v[i];
         for (int j = 0; j < i; ++j) {
             a = sub_mod(a, red1(v[j], qi), qi);
@@ -290,7 +313,7 @@ __device__ __forceinline__ void crt_words(const ModTab *__restrict__ mods, const
     for (int i = 0; i < W; ++i) w[i] = 0;
     w[0] = v[L - 1];
     for (int i = L - 2; i >= 0; --i) {            // w = w * q_i + v_i
-        const u64 qi = mods[i].q;
+        const u64 qi = BFV_LD(&mods[i].q);
         u64 carry = v[i];
         for (int n = 0; n < W; ++n) {
             const u64 lo = w[n] * qi, hi = __umul64hi(w[n], qi);
@@ -309,9 +332,10 @@ __global__ void k_dec_round(const ModTab *__restrict__ mods, const DecConst *__r
     if (idx >= total) return;
     const size_t c = idx / N;
     const int k = (int)(idx % N);
+    if (!BFV_RANGE_OK(dc, sizeof(DecConst))) return;
     const int L = dc->L, W = dc->W;
     u64 v[BFV_MAXP];
-    for (int i = 0; i < L; ++i) v[i] = x[(c * L + i) * (size_t)N + k];
+    for (int i = 0; i < L; ++i) v[i] = BFV_LD(x + (c * L + i) * (size_t)N + k);
     u64 w[BFV_MAXW];
     crt_words(mods, dc, v, w);
     {                                             // w = w * t + floor(Q/2)
@@ -342,7 +366,7 @@ __global__ void k_dec_round(const ModTab *__restrict__ mods, const DecConst *__r
             m |= 1ull << b;
         }
     }
-    pt[idx] = m % dc->t;
+    BFV_ST(pt + idx, m % dc->t);
 }
 
 // Invariant noise of coefficient k of ciphertext c: z = [t x]_Q centred in (-Q/2, Q/2], x = [c0 +
@@ -355,11 +379,12 @@ __global__ void k_noise_bits(const ModTab *__restrict__ mods, const DecConst *__
     if (idx >= total) return;
     const size_t c = idx / N;
     const int k = (int)(idx % N);
+    if (!BFV_RANGE_OK(dc, sizeof(DecConst))) return;
     const int L = dc->L, W = dc->W;
     u64 v[BFV_MAXP];
     for (int i = 0; i < L; ++i) {                  // [t x]_{q_i}; t < q_i
-        const ModTab &T = mods[i];
-        v[i] = mul_barrett(x[(c * L + i) * (size_t)N + k], dc->t, T.q, T.mu, T.bits);
+        const ModTab T = BFV_LD(mods + i);
+        v[i] = mul_barrett(BFV_LD(x + (c * L + i) * (size_t)N + k), dc->t, T.q, T.mu, T.bits);
     }
     u64 w[BFV_MAXW];
     crt_words(mods, dc, v, w);                     // y = [t x]_Q in [0, Q)
@@ -385,7 +410,7 @@ __global__ void k_noise_bits(const ModTab *__restrict__ mods, const DecConst *__
     int b = 0;
     for (int n = W - 1; n >= 0; --n)
         if (w[n]) { b = 64 * n + 64 - __clzll((long long)w[n]); break; }
-    if (b) atomicMax(bits + c, b);
+    if (b && BFV_RANGE_OK(bits + c, sizeof(int))) atomicMax(bits + c, b);
 }
 
 // ------------------------------------------------------------------ model weights
@@ -397,12 +422,12 @@ LIMB_KERNEL(LOGN) k_model_weights(const ModTab *__restrict__ mods, int L, int tm
     LIMB_INDEX(LOGN);
     const int l = (int)(unit % L);
     const size_t jk = unit / L;
-    const ModTab T = mods[l];
-    const u64 t = mods[tmod].q, th = (t - 1) / 2;
+    const ModTab T = BFV_LD(mods + l);
+    const u64 t = BFV_LD(&mods[tmod].q), th = (t - 1) / 2;
     const u64 *src = pt + jk * N;
     shoup_t *dst = out + (jk * L + l) * (size_t)N;
-    limb_forward<LOGN>(sm, T, h, [&](int p) { const u64 v = src[p]; return v <= th ? v : T.q - (t - v); },
-                       [&](int p, u64 v) { dst[p] = make_shoup(v, T.q); });
+    limb_forward<LOGN>(sm, T, h, [&](int p) { const u64 v = BFV_LD(src + p); return v <= th ? v : T.q - (t - v); },
+                       [&](int p, u64 v) { BFV_ST(dst + p, make_shoup(v, T.q)); });
 }
 
 // ------------------------------------------------------------------ dispatch helper
@@ -419,6 +444,10 @@ LIMB_KERNEL(LOGN) k_model_weights(const ModTab *__restrict__ mods, int L, int tm
 int last_err() { return cudaGetLastError() == cudaSuccess ? BFV_OK : BFV_ERR_CUDA; }
 
 }  // namespace
+
+#ifdef BFV_BOUNDS
+BFV_BOUNDS_UPLOAD_FN(bounds_upload_scheme)
+#endif
 
 // ====================================================================== launchers
 
@@ -478,6 +507,13 @@ int launch_keygen(const bfv_ctx *c, bfv_keys *k, u64 seed, cudaStream_t st) {
         cudaFree(dgal);
         return BFV_ERR_CUDA;
     }
+    {
+        BoundsCall bc(c);
+        bc.keys(k);
+        bc.add(dgal, sizeof(u64) * c->galois.size());
+        const int brc = bc.upload(st);
+        if (brc) { cudaFree(dgal); return brc; }
+    }
     k_keygen_sk<<<(c->N + 255) / 256, 256, 0, st>>>(seed, c->N, k->sk);
 #define L_(LG)                                                                                                  \
     {                                                                                                           \
@@ -526,6 +562,9 @@ int launch_encrypt(const bfv_ctx *c, const bfv_keys *k, const u64 *pt, size_t co
 #define L_(LG) launch_limbs<LG>(k_enc_main<LG, 0>, count * c->L, st, 0, c->dmods, c->L, (const shoup_t *)k->pk_eval, \
                                 (const int8_t *)rnd, pt, ct)
     if (c->logN == 14 && c->enc_split == 2)
+        launch_limbs<14, 2>(k_enc_main<14, 2>, count * c->L, st, 0, c->dmods, c->L, (const shoup_t *)k->pk_eval,
+                            (const int8_t *)rnd, pt, ct);
+    else if (c->logN == 14 && c->enc_split == 3)
         launch_limbs<14, 1>(k_enc_main<14, 1>, count * c->L, st, 0, c->dmods, c->L, (const shoup_t *)k->pk_eval,
                             (const int8_t *)rnd, pt, ct);
     else
@@ -583,11 +622,11 @@ __global__ void k_crt_combine(const int64_t *__restrict__ r0, const int64_t *__r
     const size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (i >= n) return;
     const int64_t s0 = (int64_t)t0, s1 = (int64_t)t1;
-    const u64 a = (u64)(((r0[i] % s0) + s0) % s0), b = (u64)(((r1[i] % s1) + s1) % s1);
+    const u64 a = (u64)(((BFV_LD(r0 + i) % s0) + s0) % s0), b = (u64)(((BFV_LD(r1 + i) % s1) + s1) % s1);
     const u64 d = (b + t1 - a % t1) % t1;               // (r1 - r0) mod t1
     const u64 x = a + t0 * ((d * inv) % t1);            // < t0 t1 < 2^62
     const u64 T = t0 * t1;
-    out[i] = x > T / 2 ? (int64_t)x - (int64_t)T : (int64_t)x;
+    BFV_ST(out + i, x > T / 2 ? (int64_t)x - (int64_t)T : (int64_t)x);
 }
 
 }  // namespace
@@ -615,10 +654,11 @@ static __device__ __align__(256) u64 g_noalloc_scratch[kNoAllocScratchBytes / si
 
 }  // namespace
 
-int noalloc_scratch_address(u64 **out) {
+int noalloc_scratch_address(u64 **out, size_t *bytes) {
     void *p = nullptr;
     if (cudaGetSymbolAddress(&p, g_noalloc_scratch) != cudaSuccess || !p) return BFV_ERR_CUDA;
     *out = (u64 *)p;
+    *bytes = kNoAllocScratchBytes;
     return BFV_OK;
 }
 
@@ -635,6 +675,11 @@ extern "C" int bfv_decrypt_noalloc(bfv_ctx *ctx, const bfv_keys *keys, const uin
     if (!x) return BFV_ERR_CUDA;
     const bfv_ctx *c = ctx;
     cudaStream_t st = (cudaStream_t)stream;
+    BoundsCall bc(c);
+    bc.keys(keys);
+    bc.io(ct, sizeof(u64) * count * 2 * c->L * c->N);
+    bc.io(pt, sizeof(u64) * count * c->N);
+    BFV_BOUNDS_UPLOAD(bc, st);
     ProfScope prof_(c, BFV_K_DECRYPT, st);
     // every scratch word k_dec_round reads is written by k_dec_inner in the same call
 #define L_(LG) launch_limbs<LG>(k_dec_inner<LG>, count * c->L, st, 0, c->dmods, c->L, (const shoup_t *)keys->sk_eval, \

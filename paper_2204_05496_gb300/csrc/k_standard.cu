@@ -13,8 +13,6 @@
 // k_standard_finalize (exact while |w| f 2^max(s, bits-s) < 2^63).
 #include <algorithm>
 
-#include <cuda_fp16.h>
-
 #include "bfv_internal.h"
 
 namespace {
@@ -54,8 +52,11 @@ __global__ void __launch_bounds__(kE, 2) k_standard_stream(const int *__restrict
         const int nf = (int)std::min((size_t)kF, fb - f0);
         // extra_tx (failure injection only) adds bytes that never arrive to the first stage
         mbar_expect_tx(&s.full[slot], (u32)nf * (kE * 8 + kNY * 4) + (st == 0 ? extra_tx : 0u));
-        for (int ff = 0; ff < nf; ++ff) bulk_g2s(&s.x[slot][ff][0], X + (f0 + ff) * ctw + e0, kE * 8, &s.full[slot]);
-        bulk_g2s(&s.w[slot][0][0], W16 + f0 * kNY, (u32)nf * kNY * 4, &s.full[slot]);
+        for (int ff = 0; ff < nf; ++ff)
+            if (BFV_RANGE_OK(X + (f0 + ff) * ctw + e0, kE * 8))
+                bulk_g2s(&s.x[slot][ff][0], X + (f0 + ff) * ctw + e0, kE * 8, &s.full[slot]);
+        if (BFV_RANGE_OK(W16 + f0 * kNY, (u32)nf * kNY * 4))
+            bulk_g2s(&s.w[slot][0][0], W16 + f0 * kNY, (u32)nf * kNY * 4, &s.full[slot]);
     };
     if (tid == 0)
         for (int st = 0; st < (nst < kS ? nst : kS); ++st) issue(st);
@@ -99,7 +100,7 @@ __global__ void __launch_bounds__(kE, 2) k_standard_stream(const int *__restrict
     }
     longlong2 *out = partial + split * kNY * ctw + e0 + tid;
 #pragma unroll
-    for (int j = 0; j < kNY; ++j) out[(size_t)j * ctw] = make_longlong2(lo[j], hi[j]);
+    for (int j = 0; j < kNY; ++j) BFV_ST(out + (size_t)j * ctw, make_longlong2(lo[j], hi[j]));
 }
 
 // ------------------------------------------------------------------ int8 weights: byte planes + dp4a
@@ -180,8 +181,10 @@ __global__ void __launch_bounds__(2 * kE8 + 32, 2) k_standard_dp4a(const int *__
                 const int ng = (nf + 3) / 4;
                 mbar_expect_tx(&s.full[slot], (u32)nf * (kE8 * 8) + (u32)ng * kNY * 4 + (st == 0 ? extra_tx : 0u));
                 for (int ff = 0; ff < nf; ++ff)
-                    bulk_g2s(&s.x[slot][ff][0], X + (f0 + ff) * ctw + e0, kE8 * 8, &s.full[slot]);
-                bulk_g2s(&s.w[slot][0][0], W4 + (f0 / 4) * kNY, (u32)ng * kNY * 4, &s.full[slot]);
+                    if (BFV_RANGE_OK(X + (f0 + ff) * ctw + e0, kE8 * 8))
+                        bulk_g2s(&s.x[slot][ff][0], X + (f0 + ff) * ctw + e0, kE8 * 8, &s.full[slot]);
+                if (BFV_RANGE_OK(W4 + (f0 / 4) * kNY, (u32)ng * kNY * 4))
+                    bulk_g2s(&s.w[slot][0][0], W4 + (f0 / 4) * kNY, (u32)ng * kNY * 4, &s.full[slot]);
             }
             // drain: the last stages issued may still be landing
             for (int k = st > kS8 ? st - kS8 : 0; k < st; ++k) mbar_wait(&s.full[k % kS8], (u32)((k / kS8) & 1), wait_limit);
@@ -234,7 +237,7 @@ __global__ void __launch_bounds__(2 * kE8 + 32, 2) k_standard_dp4a(const int *__
                     if (k < 4) lo += (long long)acc[j][k] * (1ll << (8 * k));
                     else hi += (long long)acc[j][k] * (1ll << (8 * (k - 4)));
                 }
-                out[(size_t)j * ctw] = make_longlong2(lo, hi);
+                BFV_ST(out + (size_t)j * ctw, make_longlong2(lo, hi));
             }
         }
     }
@@ -247,20 +250,22 @@ __global__ void __launch_bounds__(2 * kE8 + 32, 2) k_standard_dp4a(const int *__
 // The same byte-plane sums as a tensor-core contraction: for each byte plane b < NP,
 // D_b[e][j] = sum_f byte_b(X_f[e]) w[f][j] with M = 128 ciphertext words (a tile), N = 16
 // classes and K = features, as tcgen05.mma kind::f16 (A: the byte planes, B: the weights, both
-// exact in f16; D: f32 in tensor memory). A product is an integer of magnitude at most
-// 255 * 127 and a chunk of 256 features sums to less than 2^23, so every f32 partial sum is an
-// exact integer; after each chunk the sums are moved into the (lo, hi) int64 split sums that the
+// exact in f16; D: f32 in tensor memory). A plane holds 1024 + byte (the byte placed under the
+// exponent bits of 1024 by byte permutes, plane_rows), and after each plane's MMA a
+// second MMA with a constant tile of -1024 removes the offset, so D_b sums byte x weight exactly:
+// every product and every partial sum is an integer below 2^24 in magnitude (a chunk of 256
+// features sums to below 2^23, an offset MMA adds at most 16 x 1279 x 127 before the correction
+// removes it). After each chunk the sums are moved into the (lo, hi) int64 split sums that the
 // dp4a kernel forms (lo = sum_{b<4} 2^(8b) D_b, hi = sum_{b>=4} 2^(8(b-4)) D_b).
 //
 // Warps 0-7 convert: thread t owns word e = t % 128 of the tile and features 8 (t / 128) ..
-// +7 of each 16-feature stage; it splits its eight residues into byte planes (PRMT), makes each
-// byte an exact f16 (the byte under the exponent bits of 1024, minus 1024) and writes one
+// +7 of each 16-feature stage; it splits its eight residues into byte planes and writes one
 // 16-byte row of each plane's A tile (canonical K-major layout). The same threads drain the
 // accumulators of their TMEM lane (classes 8 (t / 128) .. +7). Warp 8 streams the raw
 // ciphertext rows and the stage's f16 weight tile (already in the canonical B layout) with
 // cp.async.bulk; warp 9 allocates the tensor memory and one of its threads issues the MMAs.
-// Two accumulator sets alternate so that a chunk drains while the next one accumulates. Every
-// wait is bounded: a wait that runs out sets the context's error word and the CTA winds down
+// Two accumulator sets alternate so that a chunk drains while the next one accumulates. Waiting
+// threads sleep in the barrier (a suspend-time hint) rather than spin. Every wait is bounded: a wait that runs out sets the context's error word and the CTA winds down
 // (its MMAs completed, its copies landed or timed out, its tensor memory freed).
 
 constexpr int kTcE = 128;                 // ciphertext words per tile (MMA M)
@@ -276,30 +281,44 @@ template <int NP> struct TcSmem {
     uint16_t w[SR][256];                              // the stage's f16 weights (canonical B tile)
     alignas(128) uint16_t a[SA][NP][kTcE * kF];       // byte planes (canonical A tiles, 4 KB each)
     alignas(128) uint16_t b[SA][256];                 // the weights of the converted stage
+    alignas(128) uint16_t neg[kTcE * kF];             // a constant A tile of -1024 (the offset correction)
     u64 raw_full[SR], raw_empty[SR], a_full[SA], a_empty[SA], acc_full[2], acc_empty[2], done;
     u32 tmem_base;
 };
 
-// Four f16 pairs (features 2i, 2i+1 of word e) of byte plane b from eight residues.
-__device__ __forceinline__ uint4 plane_row(const u64 (&v)[8], int b) {
-    const u32 k = (u32)(b & 3);
-    const u32 sel = k | (k << 4) | ((4 + k) << 8) | ((4 + k) << 12);   // [x_k, x_k, y_k, y_k]
-    u32 o[4];
+// The A rows of all NP byte planes from eight residues v[0..7] (features 8 k8 .. +7 of word e):
+// row b holds the f16 pairs (1024 + byte_b(v[2i]), 1024 + byte_b(v[2i+1])), i < 4. For each pair
+// of residues and each 32-bit half, one PRMT interleaves the bytes of planes {0, 2} and one those
+// of {1, 3} ([x_0, y_0, x_2, y_2], [x_1, y_1, x_3, y_3]); one PRMT per plane then places two of
+// them under the exponent byte 0x64 of 1024 (three PRMTs per two f16 pairs).
+template <int NP>
+__device__ __forceinline__ void plane_rows(const u64 (&v)[8], uint4 (&row)[NP]) {
+    constexpr u32 C64 = 0x64646464u;
+    u32 o[NP][4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) {
-        const u32 x = b < 4 ? (u32)v[2 * i] : (u32)(v[2 * i] >> 32);
-        const u32 y = b < 4 ? (u32)v[2 * i + 1] : (u32)(v[2 * i + 1] >> 32);
-        const u32 t = (prmt(x, y, sel) & 0x00FF00FFu) | 0x64006400u;      // f16 pair 1024 + byte
-        const __half2 h = __hsub2(*reinterpret_cast<const __half2 *>(&t), __half2(__half(1024.0f), __half(1024.0f)));
-        o[i] = *reinterpret_cast<const u32 *>(&h);
+#pragma unroll
+        for (int half = 0; half < 2; ++half) {
+            if (4 * half >= NP) continue;
+            const u32 x = half ? (u32)(v[2 * i] >> 32) : (u32)v[2 * i];
+            const u32 y = half ? (u32)(v[2 * i + 1] >> 32) : (u32)v[2 * i + 1];
+            const u32 t02 = prmt(x, y, 0x6240u), t13 = prmt(x, y, 0x7351u);
+            const int b0 = 4 * half;
+            if (b0 + 0 < NP) o[b0 + 0][i] = prmt(t02, C64, 0x4140u);     // [x_0, 64, y_0, 64]
+            if (b0 + 2 < NP) o[b0 + 2][i] = prmt(t02, C64, 0x4342u);     // [x_2, 64, y_2, 64]
+            if (b0 + 1 < NP) o[b0 + 1][i] = prmt(t13, C64, 0x4140u);     // [x_1, 64, y_1, 64]
+            if (b0 + 3 < NP) o[b0 + 3][i] = prmt(t13, C64, 0x4342u);     // [x_3, 64, y_3, 64]
+        }
     }
-    return make_uint4(o[0], o[1], o[2], o[3]);
+#pragma unroll
+    for (int b = 0; b < NP; ++b) row[b] = make_uint4(o[b][0], o[b][1], o[b][2], o[b][3]);
 }
 
 // A bounded wait by a whole warp with one outcome for all its lanes (the tensor-memory loads that
 // follow are warp-collective, so no lane may leave the loop alone).
+constexpr u32 kTcSleepNs = 20000;         // suspend-time hint of a poll
 __device__ __forceinline__ bool warp_wait(u64 *bar, u32 parity, long long limit) {
-    return __all_sync(0xffffffffu, mbar_wait(bar, parity, limit));
+    return __all_sync(0xffffffffu, mbar_wait_sleep(bar, parity, limit, kTcSleepNs));
 }
 
 template <int NP>
@@ -325,6 +344,8 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_standard_tc(const uint16_t *_
         mbar_init(&s.done, 1);
         mbar_init_fence();
     }
+    for (int i = tid; i < kTcE * kF / 2; i += kTcThreads) reinterpret_cast<u32 *>(s.neg)[i] = 0xE400E400u;  // -1024
+    fence_proxy_async_smem();
     if (warp == 9) tmem_alloc(&s.tmem_base, kTcCols);
     tmem_fence_before_sync();
     __syncthreads();
@@ -338,7 +359,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_standard_tc(const uint16_t *_
             int st = 0;
             for (; st < nst; ++st) {
                 const int slot = st % SR;
-                if (st >= SR && !mbar_wait(&s.raw_empty[slot], (u32)(((st - SR) / SR) & 1), wait_limit)) {
+                if (st >= SR && !mbar_wait_sleep(&s.raw_empty[slot], (u32)(((st - SR) / SR) & 1), wait_limit, kTcSleepNs)) {
                     failed = true;
                     break;
                 }
@@ -346,11 +367,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_standard_tc(const uint16_t *_
                 const int nf = (int)std::min((size_t)kF, fb - f0);
                 mbar_expect_tx(&s.raw_full[slot], (u32)nf * (kTcE * 8) + 512u + (st == 0 ? extra_tx : 0u));
                 for (int ff = 0; ff < nf; ++ff)
-                    bulk_g2s(&s.x[slot][ff][0], X + (f0 + ff) * ctw + e0, kTcE * 8, &s.raw_full[slot]);
-                bulk_g2s(&s.w[slot][0], Wtc + (f0 / kF) * 256, 512u, &s.raw_full[slot]);
+                    if (BFV_RANGE_OK(X + (f0 + ff) * ctw + e0, kTcE * 8))
+                        bulk_g2s(&s.x[slot][ff][0], X + (f0 + ff) * ctw + e0, kTcE * 8, &s.raw_full[slot]);
+                if (BFV_RANGE_OK(Wtc + (f0 / kF) * 256, 512u))
+                    bulk_g2s(&s.w[slot][0], Wtc + (f0 / kF) * 256, 512u, &s.raw_full[slot]);
             }
             // the last stages issued may still be landing
-            for (int k = st > SR ? st - SR : 0; k < st; ++k) mbar_wait(&s.raw_full[k % SR], (u32)((k / SR) & 1), wait_limit);
+            for (int k = st > SR ? st - SR : 0; k < st; ++k)
+                mbar_wait_sleep(&s.raw_full[k % SR], (u32)((k / SR) & 1), wait_limit, kTcSleepNs);
         }
     } else if (warp == 9) {
         // MMA warp: one thread issues NP MMAs per stage into the chunk's accumulator set
@@ -359,22 +383,24 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_standard_tc(const uint16_t *_
             for (int st = 0; st < nst && !failed; ++st) {
                 const int c = st / kTcChunk, k = st % kTcChunk, set = c & 1, as = st % SA;
                 if (k == 0 && c >= 2) {
-                    if (!mbar_wait(&s.acc_empty[set], (u32)(((c - 2) / 2) & 1), wait_limit)) { failed = true; break; }
+                    if (!mbar_wait_sleep(&s.acc_empty[set], (u32)(((c - 2) / 2) & 1), wait_limit, kTcSleepNs)) { failed = true; break; }
                     tmem_fence_after_sync();
                 }
-                if (!mbar_wait(&s.a_full[as], (u32)((st / SA) & 1), wait_limit)) { failed = true; break; }
+                if (!mbar_wait_sleep(&s.a_full[as], (u32)((st / SA) & 1), wait_limit, kTcSleepNs)) { failed = true; break; }
                 tmem_fence_after_sync();
-                const u64 bdesc = umma_desc_kmajor(&s.b[as][0], 128, 256);
+                const u64 bdesc = umma_desc_kmajor(&s.b[as][0], 128, 256), ndesc = umma_desc_kmajor(s.neg, 128, 256);
 #pragma unroll
-                for (int b = 0; b < NP; ++b)
-                    umma_f16(tbase + (u32)(set * 128 + b * 16), umma_desc_kmajor(&s.a[as][b][0], 128, 256), bdesc, idesc,
-                             k > 0);
+                for (int b = 0; b < NP; ++b) {
+                    const u32 d = tbase + (u32)(set * 128 + b * 16);
+                    umma_f16(d, umma_desc_kmajor(&s.a[as][b][0], 128, 256), bdesc, idesc, k > 0);
+                    umma_f16(d, ndesc, bdesc, idesc, true);          // minus 1024 x the stage's weights
+                }
                 umma_commit(&s.a_empty[as]);
                 if (k == kTcChunk - 1 || st == nst - 1) umma_commit(&s.acc_full[set]);
             }
             // every MMA issued has completed before the CTA frees its shared and tensor memory
             umma_commit(&s.done);
-            mbar_wait(&s.done, 0, wait_limit);
+            mbar_wait_sleep(&s.done, 0, wait_limit, kTcSleepNs);
         }
     } else {
         // converters: byte planes in, accumulators out
@@ -412,10 +438,12 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_standard_tc(const uint16_t *_
             u64 v[8];
 #pragma unroll
             for (int i = 0; i < 8; ++i) v[i] = s.x[rs][k8 * 8 + i][e];   // rows past the range: weights are 0
+            uint4 rows[NP];
+            plane_rows<NP>(v, rows);
 #pragma unroll
             for (int b = 0; b < NP; ++b)
                 *reinterpret_cast<uint4 *>(reinterpret_cast<unsigned char *>(&s.a[as][b][0]) + (e >> 3) * 256 + k8 * 128 +
-                                           (e & 7) * 16) = plane_row(v, b);
+                                           (e & 7) * 16) = rows[b];
             if (k8 == 0) reinterpret_cast<u32 *>(&s.b[as][0])[e] = reinterpret_cast<const u32 *>(&s.w[rs][0])[e];
             fence_proxy_async_smem();
             __syncwarp();
@@ -437,7 +465,7 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_standard_tc(const uint16_t *_
         if (!failed) {
             longlong2 *out = partial + (split * kNY + k8 * 8) * ctw + e0 + e;
 #pragma unroll
-            for (int j = 0; j < 8; ++j) out[(size_t)j * ctw] = make_longlong2(lo[j], hi[j]);
+            for (int j = 0; j < 8; ++j) BFV_ST(out + (size_t)j * ctw, make_longlong2(lo[j], hi[j]));
         }
     }
     // a bounded wait ran out somewhere: report it (the output of this launch is invalid)
@@ -459,22 +487,26 @@ __global__ void __launch_bounds__(256) k_standard_finalize(const ModTab *__restr
     const size_t e = idx % ctw;
     long long lo = 0, hi = 0;
     for (int sp = 0; sp < splits; ++sp) {
-        const longlong2 v = partial[((size_t)sp * kNY + j) * ctw + e];
+        const longlong2 v = BFV_LD(partial + ((size_t)sp * kNY + j) * ctw + e);
         lo += v.x;
         hi += v.y;
     }
     const int l = (int)((e / N) % L);
-    const ModTab T = mods[l];
+    const ModTab T = BFV_LD(mods + l);
     const long long q = (long long)T.q;
     long long h = hi % q; if (h < 0) h += q;
     long long a = lo % q; if (a < 0) a += q;
     const u64 sh = (1ull << split_bits) % T.q;
     u64 v = add_mod(mul_barrett((u64)h, sh, T.q, T.mu, T.bits), (u64)a, T.q);
-    if (e < (size_t)L * N && e % N == 0) v = add_mod(v, bias_delta[(size_t)(j0 + j) * L + l], T.q);
-    Y[(size_t)(j0 + j) * ctw + e] = v;
+    if (e < (size_t)L * N && e % N == 0) v = add_mod(v, BFV_LD(bias_delta + (size_t)(j0 + j) * L + l), T.q);
+    BFV_ST(Y + (size_t)(j0 + j) * ctw + e, v);
 }
 
 }  // namespace
+
+#ifdef BFV_BOUNDS
+BFV_BOUNDS_UPLOAD_FN(bounds_upload_standard)
+#endif
 
 StandardPlan standard_plan(const bfv_ctx *c, const bfv_model *m) {
     StandardPlan p{};
@@ -513,8 +545,9 @@ int launch_standard(const bfv_ctx *c, const bfv_model *m, const u64 *X_ct, u64 *
     {                                                                                                              \
         cudaFuncSetAttribute(k_standard_tc<NP>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sizeof(TcSmem<NP>)); \
         k_standard_tc<NP><<<grid, kTcThreads, sizeof(TcSmem<NP>), st>>>(wtc, X_ct, ctw, m->f, pl.fper, partial,       \
-                                                                       c->derr, (u32)c->inject_extra_tx, limit);   \
+                                                                       c->derr, (u32)c->inject_extra_tx, tc_limit); \
     }
+            const long long tc_limit = c->inject_extra_tx ? (1ll << 7) : (1ll << 16);   // <= ~1.3 s of polls
             switch (np) {
                 case 4: STDTC(4); break;
                 case 5: STDTC(5); break;

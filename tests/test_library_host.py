@@ -181,3 +181,10 @@ def test_modup_tensor_memory_layout_is_a_partition(logn, split):
             assert first % 16 == 0 and first + 15 < cols
     assert points == set(range(H))
     assert cells == {(ln, c) for ln in range(128) for c in range(cols)}
+
+
+def test_release_library_is_not_the_bounds_checked_build(bfv):
+    """The release library reports no bounds checks; the bounds-checked build is a separate
+    variant (libbfv_lr_bounds.so, selected with BFV_LIB_VARIANT=bounds)."""
+    assert bfv.lib().bfv_bounds_checked() == 0
+    assert bfv.VARIANTS["bounds"][1] == ["-DBFV_BOUNDS"]
