@@ -951,14 +951,22 @@ def run_serve(args):
         return pool[i0:i0 + n]
 
     # the client's side when it is in the measured latency: encrypt the request's rows at arrival
-    # (on the submitting stream; the server's launch waits for it) and decrypt + decode its
-    # outputs right after the product, on the launch's stream
+    # and decrypt + decode its outputs right after the product, on the launch's stream. A real
+    # client encrypts on its own machine; simulated on the server's GPU, its encryption runs on a
+    # high-priority stream of its own so that it does not queue behind the CTAs of the server's
+    # large products, and the launch waits for the event recorded after it
     Xdev = torch.from_numpy(X).cuda()
+    lo_pri, hi_pri = torch.cuda.Stream.priority_range()
+    client_stream = torch.cuda.Stream(priority=min(lo_pri, hi_pri))
 
     def client_inputs(k, n):
         i0 = (k * 131) % (len(X) - n + 1)
-        ptk = ctx.encode_features(Xdev[i0:i0 + n])
-        return ctx.encrypt(keys, ptk.reshape(-1, N), seed=w.seed_enc + k, obj0=0).reshape(n, model.K, 2, L, N)
+        with torch.cuda.stream(client_stream):
+            ptk = ctx.encode_features(Xdev[i0:i0 + n])
+            ct = ctx.encrypt(keys, ptk.reshape(-1, N), seed=w.seed_enc + k, obj0=0).reshape(n, model.K, 2, L, N)
+            ev = torch.cuda.Event()
+            ev.record(client_stream)
+        return ct, ev
 
     def client_decrypt(r, out):
         return ctx.decode(ctx.decrypt(keys, out))

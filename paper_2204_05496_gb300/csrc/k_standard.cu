@@ -409,26 +409,36 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_standard_tc(const uint16_t *_
         long long lo[8], hi[8];
 #pragma unroll
         for (int j = 0; j < 8; ++j) { lo[j] = 0; hi[j] = 0; }
-        int drained = 0;
-        auto drain = [&](int c) -> bool {
+        // Chunk c's sums drain one plane per converted stage (the MMA warp needs that set again
+        // only 16 stages later), so the converters never stop for a whole drain.
+        int drained = 0, dplane = -1;                  // chunks drained; plane of the drain in progress
+        auto drain_plane = [&](int c, int b) -> bool {
             const int set = c & 1;
-            if (!warp_wait(&s.acc_full[set], (u32)((c / 2) & 1), wait_limit)) return false;
-            tmem_fence_after_sync();
-#pragma unroll
-            for (int b = 0; b < NP; ++b) {
-                u32 r[8];
-                tmem_ld8(lane_addr + (u32)(set * 128 + b * 16 + k8 * 8), r);
-                tmem_wait_ld();
-#pragma unroll
-                for (int j = 0; j < 8; ++j) {
-                    const long long v = (long long)__float2int_rn(__uint_as_float(r[j]));
-                    if (b < 4) lo[j] += v * (1ll << (8 * b));
-                    else hi[j] += v * (1ll << (8 * (b - 4)));
-                }
+            if (b == 0) {
+                if (!warp_wait(&s.acc_full[set], (u32)((c / 2) & 1), wait_limit)) return false;
+                tmem_fence_after_sync();
             }
-            tmem_fence_before_sync();
-            __syncwarp();
-            if ((tid & 31) == 0) mbar_arrive(&s.acc_empty[set]);
+            u32 r[8];
+            tmem_ld8(lane_addr + (u32)(set * 128 + b * 16 + k8 * 8), r);
+            tmem_wait_ld();
+            const int sh = 8 * (b & 3);
+#pragma unroll
+            for (int j = 0; j < 8; ++j) {
+                const long long v = (long long)__float2int_rn(__uint_as_float(r[j])) * (1ll << sh);
+                if (b < 4) lo[j] += v;
+                else hi[j] += v;
+            }
+            if (b == NP - 1) {
+                tmem_fence_before_sync();
+                __syncwarp();
+                if ((tid & 31) == 0) mbar_arrive(&s.acc_empty[set]);
+            }
+            return true;
+        };
+        auto drain_step = [&]() -> bool {
+            if (dplane < 0) return true;
+            if (!drain_plane(drained, dplane)) return false;
+            if (++dplane == NP) { dplane = -1; ++drained; }
             return true;
         };
         for (int st = 0; st < nst; ++st) {
@@ -451,16 +461,14 @@ __global__ void __launch_bounds__(kTcThreads, 2) k_standard_tc(const uint16_t *_
                 mbar_arrive(&s.raw_empty[rs]);
                 mbar_arrive(&s.a_full[as]);
             }
-            // a chunk whose last stage the MMA warp finished SA stages ago drains now
+            // a chunk whose last stage the MMA warp finished SA stages ago starts draining
             const int done_st = st - SA;
-            if (done_st >= 0 && done_st % kTcChunk == kTcChunk - 1) {
-                if (!drain(drained)) { failed = true; break; }
-                ++drained;
-            }
+            if (done_st >= 0 && done_st % kTcChunk == kTcChunk - 1) dplane = 0;
+            if (!drain_step()) { failed = true; break; }
         }
-        while (!failed && drained < nchunks) {
-            if (!drain(drained)) { failed = true; break; }
-            ++drained;
+        while (!failed && (dplane >= 0 || drained < nchunks)) {
+            if (dplane < 0) dplane = 0;
+            if (!drain_step()) { failed = true; break; }
         }
         if (!failed) {
             longlong2 *out = partial + (split * kNY + k8 * 8) * ctw + e0 + e;

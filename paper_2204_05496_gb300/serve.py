@@ -93,12 +93,16 @@ class Server:
     def now(self) -> float:
         return time.perf_counter() - self.t0_host
 
-    def submit(self, rid: int, X_ct, t_arrival: float | None = None, model: int = 0) -> Request:
+    def submit(self, rid: int, X_ct, t_arrival: float | None = None, model: int = 0, ready=None) -> Request:
+        """Queues a request. `ready`: a CUDA event recorded after the work that writes X_ct; by
+        default one is recorded now on the current stream of X_ct's device."""
         if not 0 <= model < len(self.models):
             raise ValueError(f"request {rid} names model {model}; the server holds {len(self.models)}")
         r = Request(rid, X_ct, self.now() if t_arrival is None else t_arrival, model)
-        r.ready = self.torch.cuda.Event()
-        r.ready.record(self.torch.cuda.current_stream(X_ct.device))
+        if ready is None:
+            ready = self.torch.cuda.Event()
+            ready.record(self.torch.cuda.current_stream(X_ct.device))
+        r.ready = ready
         self.waiting.append(r)
         return r
 
@@ -191,8 +195,9 @@ class Server:
 
     def run(self, arrivals, make_inputs, poll_s: float = 0.0005, max_seconds: float = 600.0):
         """Replays an arrival trace: arrivals = [(t_seconds, nX)] or [(t_seconds, nX, model)],
-        make_inputs(i, nX) -> X_ct. Returns the completed requests. Raises TimeoutError after
-        max_seconds of wall time."""
+        make_inputs(i, nX) -> X_ct, or (X_ct, event) when the inputs are written on a stream of
+        their own (the event recorded after that work). Returns the completed requests. Raises
+        TimeoutError after max_seconds of wall time."""
         self.start()
         k = 0
         while k < len(arrivals) or not self.idle():
@@ -201,7 +206,8 @@ class Server:
                 raise TimeoutError(f"trace not served within {max_seconds} s")
             while k < len(arrivals) and arrivals[k][0] <= now:
                 a = arrivals[k]
-                self.submit(k, make_inputs(k, a[1]), a[0], a[2] if len(a) > 2 else 0)
+                X, ready = _inputs_and_event(make_inputs(k, a[1]))
+                self.submit(k, X, a[0], a[2] if len(a) > 2 else 0, ready=ready)
                 k += 1
             self.step()
             self._check_admissible()
@@ -212,6 +218,11 @@ class Server:
         self.torch.cuda.synchronize()
         self._retire()
         return sorted(self.done, key=lambda r: r.rid)
+
+
+def _inputs_and_event(inp):
+    """make_inputs' result as (X_ct, ready event or None)."""
+    return inp if isinstance(inp, tuple) else (inp, None)
 
 
 def latency_report(reqs, nY: int) -> dict:
@@ -246,7 +257,9 @@ def run_unbatched(ctx, keys, model, arrivals, make_inputs, pair_chunk: int = 0, 
         m = a[2] if len(a) > 2 else 0
         while time.perf_counter() - h0 < ta:
             time.sleep(0.0005)
-        X = make_inputs(k, nX)
+        X, ready = _inputs_and_event(make_inputs(k, nX))
+        if ready is not None:
+            torch.cuda.current_stream().wait_event(ready)
         r = Request(k, X, ta, m)
         out = ctx.lr_scores_packed(keys, models[m], X, pair_chunk=pair_chunk)
         if post is not None:

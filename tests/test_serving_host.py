@@ -199,3 +199,18 @@ def test_launch_waits_for_the_inputs_producer_and_holds_their_memory(fake_torch)
     srv.step()
     assert srv.intervals and srv.intervals[0]["requests"] == [0, 1]
     assert {"start_s", "end_s", "stream", "batch"} <= set(srv.intervals[0])
+
+
+def test_inputs_written_on_their_own_stream_bring_their_event(fake_torch):
+    # make_inputs may return (X_ct, event) when it writes the inputs on a stream of its own: the
+    # launch then waits for that event instead of one recorded on the current stream
+    srv, ctx = make(fake_torch, hbm_budget_bytes=10 ** 6, n_streams=1)
+    evs = {}
+
+    def make_inputs(k, n):
+        evs[k] = FakeEvent()
+        return _X(n), evs[k]
+
+    done = srv.run([(0.0, 1), (0.0, 2)], make_inputs, poll_s=0.0001, max_seconds=5)
+    assert [r.ready for r in done] == [evs[0], evs[1]]
+    assert [id(e) for e in srv.streams[0].waited] == [id(evs[0]), id(evs[1])]
