@@ -122,7 +122,7 @@ def modmuls_per_pair(kind, N, L, K):
         "ks_moddown_p": 2 * B,                              # inverse NTT of the two P limbs
         "ks_moddown": 2 * L * B + 2 * L * N,                # NTT of the corrections + P^-1 product
         "mac": 2 * L * K * N,
-        "bias_mask": L * B + 2 * L * N,
+        "bias_mask": 2 * L * N,                             # the two mask products (masks gathered)
     }[kind]
 
 
@@ -682,8 +682,8 @@ def run_only_packed(args):
         # every split combination at the plan's chunk (bit-identical results; times only)
         chunk = args.pair_chunk or ctx.packed_schedule(pairs).pair_chunk
         sweep = {}
-        for p_, m_, mp_, md_ in [(p_, m_, mp_, md_) for p_ in (1, 2) for m_ in (2, 4) for mp_ in (1, 2, 3)
-                                 for md_ in (1, 2)]:
+        for p_, m_, mp_, md_ in [(p_, m_, mp_, md_) for p_ in (1, 2, 3) for m_ in (2, 4) for mp_ in (1, 2, 3, 4)
+                                 for md_ in (1, 2, 3)]:
             sc = bfv.Schedule(chunk, p_, m_, mp_, md_)
             Ys = ctx.lr_scores_packed_sched(keys, model, X_ct, sc, ws=ws)
             ok = ok and bool(torch.equal(Ys, Y))

@@ -250,12 +250,17 @@ int bfv_lr_scores_packed_graph(bfv_ctx *ctx, const bfv_keys *keys, const bfv_mod
  * finer splits that fill the SMs). A split of 2 CTAs per limb takes effect at N = 16384 only:
  * at N = 32768 every limb kernel already runs on a two-CTA cluster, at N <= 8192 on one CTA.
  *   pair_chunk       pairs in flight at once, >= 1 (workspace grows with it)
- *   prep_split       1 | 2: CTAs per digit in the inverse transform of the key-switch input
+ *   prep_split       1 | 2 | 3: CTAs per digit in the inverse transform of the key-switch input:
+ *                    1 CTA of 512 threads, 2 CTAs of 256 threads (three per SM), 3 = two CTAs of
+ *                    256 threads with twice the registers (two per SM)
  *   modup_split      2 | 4: CTAs per target limb in ModUp (each folds log2 of it stages into its loads)
- *   moddown_p_split  0 | 1 | 2 | 3: CTAs per P limb in ModDown's inverse transform: 1 or 2 CTAs of
- *                    256 threads, 3 = two CTAs of 512 threads (0: 2 when the chunk has fewer than
- *                    the SM count of pairs, else 1)
- *   moddown_split    1 | 2: CTAs per limb in ModDown's forward transform and P^-1 product
+ *   moddown_p_split  0 | 1 | 2 | 3 | 4: CTAs per P limb in ModDown's inverse transform: 1 CTA of 512
+ *                    threads, 2 CTAs of 256 threads (three per SM), 3 = two CTAs of 512 threads,
+ *                    4 = two CTAs of 256 threads with twice the registers (0: 2 when the chunk has
+ *                    fewer than the SM count of pairs, else 1)
+ *   moddown_split    1 | 2 | 3: CTAs per limb in ModDown's forward transform and P^-1 product:
+ *                    1 CTA of 512 threads, 2 CTAs of 256 threads (three per SM), 3 = two CTAs of
+ *                    256 threads with twice the registers (two per SM)
  * No counterpart in the paper (a GPU launch configuration). */
 typedef struct bfv_packed_schedule {
     uint64_t pair_chunk;

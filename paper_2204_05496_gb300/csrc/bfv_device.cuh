@@ -276,7 +276,8 @@ __device__ __forceinline__ void ntt_forward_lazy(u64 *sm, const ModTab &T, int C
 // stage. load(p) must return values < 2q (local position p); store(p, v) receives local
 // position p in [0, q) -- for the whole transform, coefficient p.
 
-template <int LOGN, int LOGM, int NT, int P, int S, class Load, class Store>
+// ILP2: the two radix-8 groups a thread handles in a pass are interleaved.
+template <int LOGN, int LOGM, int NT, int P, int S, bool ILP2, class Load, class Store>
 __device__ __forceinline__ void inv_passes(u64 *sm, const ModTab &T, int hidx, Load &load, Store &store) {
     constexpr int NP = Sched<LOGM>::NP;
     constexpr int R = Sched<LOGM>::template R<P>::value;
@@ -284,7 +285,7 @@ __device__ __forceinline__ void inv_passes(u64 *sm, const ModTab &T, int hidx, L
     constexpr int TL = 1 << S;
     constexpr int G = M >> R;
     const u64 q = T.q, q2 = T.q2;
-#pragma unroll 1
+#pragma unroll (ILP2 && R == 3 && G >= 2 * NT ? 2 : 1)
     for (int g = threadIdx.x; g < G; g += NT) {
         const int block = g >> S, off = g & (TL - 1);
         const int base = block * (TL << R) + off;
@@ -304,13 +305,13 @@ __device__ __forceinline__ void inv_passes(u64 *sm, const ModTab &T, int hidx, L
     }
     if constexpr (P < NP - 1) {
         __syncthreads();
-        inv_passes<LOGN, LOGM, NT, P + 1, S + R>(sm, T, hidx, load, store);
+        inv_passes<LOGN, LOGM, NT, P + 1, S + R, ILP2>(sm, T, hidx, load, store);
     }
 }
 
-template <int LOGN, int NT, class Load, class Store>
+template <int LOGN, int NT, bool ILP2 = false, class Load, class Store>
 __device__ __forceinline__ void ntt_inverse(u64 *sm, const ModTab &T, Load load, Store store) {
-    inv_passes<LOGN, LOGN, NT, 0, 0>(sm, T, 0, load, store);
+    inv_passes<LOGN, LOGN, NT, 0, 0, ILP2>(sm, T, 0, load, store);
 }
 
 // ------------------------------------------------------------------ index maps
@@ -383,12 +384,6 @@ __device__ __forceinline__ void bulk_g2s(void *dst, const void *src, u32 bytes, 
         "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(smem_addr(dst)),
         "l"(src), "r"(bytes), "r"(smem_addr(bar))
         : "memory");
-}
-
-// Asynchronous prefetch of `bytes` (a multiple of 16, 16-byte aligned) of global memory into L2
-// by the bulk-copy engine; nothing is written to shared memory or registers.
-__device__ __forceinline__ void bulk_prefetch_l2(const void *src, u32 bytes) {
-    asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(src), "r"(bytes) : "memory");
 }
 
 // ------------------------------------------------------------------ limbs split over a CTA pair
@@ -485,16 +480,16 @@ __device__ __forceinline__ void limb_forward(u64 *sm, const ModTab &T, int h, Lo
 // (< 2q) for the positions this CTA owns; store(k, v) receives the coefficients k it owns,
 // in [0, q). With S = 2 every thread of the cluster must call it (two cluster barriers), and
 // sm must not be written by the caller between the call and the caller's next barrier.
-template <int LOGN, int MODE = 0, class Load, class Store>
+template <int LOGN, int MODE = 0, bool ILP2 = false, class Load, class Store>
 __device__ __forceinline__ void limb_inverse(u64 *sm, const ModTab &T, int h, Load load, Store store) {
     using SP = Split<LOGN, MODE>;
     if constexpr (SP::S == 1) {
-        ntt_inverse<LOGN, SP::NT>(sm, T, load, store);
+        ntt_inverse<LOGN, SP::NT, ILP2>(sm, T, load, store);
     } else {
         constexpr int M = SP::M;
         auto ld = [&](int p) { return load(h * M + p); };
         auto st = [&](int p, u64 v) { sm[padi(p)] = v; };
-        inv_passes<LOGN, SP::LOGM, SP::NT, 0, 0>(sm, T, h, ld, st);
+        inv_passes<LOGN, SP::LOGM, SP::NT, 0, 0, ILP2>(sm, T, h, ld, st);
         cluster_sync();
         const u32 peer = cluster_map(sm, (u32)(h ^ 1));
         const u64 q = T.q, q2 = T.q2;

@@ -52,6 +52,7 @@ struct bfv_ctx {
     u64 *dtw = nullptr;              // twiddle tables [nqp+1][4][N]
     u32 *dslot = nullptr;            // [N] evaluation position of slot l (mod-t transform)
     u32 *dmaskpow = nullptr;         // [2N] N^-1 omega^i mod t
+    shoup_t *dmaskev = nullptr;      // [L][N] evaluation form of the slot-0 one-hot mask (Shoup form)
     u64 *dcdt = nullptr;             // Gaussian thresholds
     int cdt_len = 0;
     DecConst *ddec = nullptr;        // decryption constants
@@ -159,6 +160,7 @@ struct BoundsCall {
         add(c->dtw, sizeof(u64) * (size_t)(c->nqp + 1) * 4 * c->N);
         add(c->dslot, sizeof(u32) * c->N);
         add(c->dmaskpow, sizeof(u32) * 2 * c->N);
+        add(c->dmaskev, sizeof(shoup_t) * (size_t)c->L * c->N);
         add(c->dcdt, sizeof(u64) * 32);
         add(c->ddec, sizeof(DecConst));
         add(c->derr, sizeof(int));
@@ -263,6 +265,7 @@ cudaError_t launch_limbs(void (*kern)(KArgs...), size_t units, cudaStream_t st, 
 // Each returns BFV_OK or BFV_ERR_CUDA (launch error); all are asynchronous on `st`.
 
 int launch_ntt_limbs(const bfv_ctx *c, const u64 *in, u64 *out, size_t nct, bool forward, cudaStream_t st);
+int launch_mask_base(const bfv_ctx *c, cudaStream_t st);
 int launch_encode(const bfv_ctx *c, const int64_t *slots, size_t count, u64 *pt, cudaStream_t st);
 int launch_decode(const bfv_ctx *c, const u64 *pt, size_t count, int64_t *slots, cudaStream_t st);
 int launch_encode_features(const bfv_ctx *c, const uint8_t *X, size_t nX, size_t f, u64 *pt, cudaStream_t st);

@@ -224,6 +224,7 @@ void free_ctx(bfv_ctx *c) {
     cudaFree(c->dtw);
     cudaFree(c->dslot);
     cudaFree(c->dmaskpow);
+    cudaFree(c->dmaskev);
     cudaFree(c->dcdt);
     cudaFree(c->ddec);
     cudaFree(c->derr);
@@ -422,6 +423,13 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
     // rotate-and-sum Galois elements: 2N-1, then 3^(N/4), ..., 3^1 mod 2N
     c->galois.push_back(2 * N - 1);
     for (u64 s = N / 4; s >= 1; s >>= 1) c->galois.push_back(powmod_h(3, s, 2 * N));
+
+    // evaluation form of the slot-0 one-hot mask: the packed product gathers every slot's mask from it
+    if ((rc = dalloc(&c->dmaskev, (size_t)c->L * N))) { free_ctx(c); return rc; }
+    {
+        BoundsCall bc(c);
+        if ((rc = bc.upload(0)) || (rc = launch_mask_base(c, 0))) { free_ctx(c); return rc; }
+    }
 
     // the device address of bfv_decrypt_noalloc's fixed scratch array, with this device current
     if ((rc = noalloc_scratch_address(&c->noalloc_scratch, &c->noalloc_bytes))) { free_ctx(c); return rc; }
@@ -943,9 +951,9 @@ int bfv_autotune_packed_schedule(bfv_ctx *ctx, const bfv_keys *keys, const bfv_m
     uint32_t bfv_packed_schedule::*fields[] = {&bfv_packed_schedule::prep_split, &bfv_packed_schedule::modup_split,
                                                &bfv_packed_schedule::moddown_p_split,
                                                &bfv_packed_schedule::moddown_split};
-    const uint32_t values[4][4] = {{1, 2, 0, 0}, {2, 4, 0, 0}, {1, 2, 3, 0}, {1, 2, 0, 0}};   // 0 ends a list
+    const uint32_t values[4][5] = {{1, 2, 3, 0, 0}, {2, 4, 0, 0, 0}, {1, 2, 3, 4, 0}, {1, 2, 3, 0, 0}};   // 0 ends a list
     for (int f = 0; f < 4 && !rc; ++f) {
-        for (int v = 0; v < 4 && values[f][v] && !rc; ++v) {
+        for (int v = 0; v < 5 && values[f][v] && !rc; ++v) {
             bfv_packed_schedule cand = sc;
             cand.*fields[f] = values[f][v];
             if (cand.*fields[f] == sc.*fields[f]) continue;

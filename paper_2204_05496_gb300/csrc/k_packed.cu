@@ -90,7 +90,7 @@ LIMB_KERNEL_M(LOGN, MODE) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 
     // coalesced line prefetches first (each CTA of the group a share of the lines)
     for (int i = threadIdx.x + h * NT; i < N / 16; i += S * NT)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(limb + 16 * i));
-    limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return BFV_LD(limb + auto_src(p, gal, LOGN)); },
+    limb_inverse<LOGN, MODE, MODE != 1>(sm, T, h, [&](int p) { return BFV_LD(limb + auto_src(p, gal, LOGN)); },
                              [&](int p, u64 v) { BFV_ST(dst + p, v); });
 }
 
@@ -253,12 +253,12 @@ LIMB_KERNEL_M(LOGN, MODE) k_ks_moddown_p(const ModTab *__restrict__ mods, int L,
     const ModTab T = BFV_LD(mods + L);
     const u64 *src = U + (gc * nqp + L) * (size_t)N;
     u64 *dst = R + gc * N;
-    limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return BFV_LD(src + p); },
+    limb_inverse<LOGN, MODE, MODE != 1>(sm, T, h, [&](int p) { return BFV_LD(src + p); },
                              [&](int p, u64 v) { BFV_ST(dst + p, add_mod(v, T.phalf, T.q)); });
 }
 
-// Limb unit (g, c, l): C[g][c][l] += (U[g][c][l] + NTT_l(floor(P/2) - r)) * P^-1. Split mode 1:
-// two 256-thread CTAs per limb at N = 16384 (the first stage folded into the loads).
+// Limb unit (g, c, l): C[g][c][l] += (U[g][c][l] + NTT_l(floor(P/2) - r)) * P^-1. Split modes 1
+// and 2: two 256-thread CTAs per limb at N = 16384 (the first stage folded into the loads).
 template <int LOGN, int MODE>
 LIMB_KERNEL_M(LOGN, MODE) k_ks_moddown(const ModTab *__restrict__ mods, int L, const u64 *__restrict__ U,
                                        const u64 *__restrict__ R, u64 *C) {
@@ -270,7 +270,7 @@ LIMB_KERNEL_M(LOGN, MODE) k_ks_moddown(const ModTab *__restrict__ mods, int L, c
     const size_t g = unit / (2 * L);
     const ModTab T = BFV_LD(mods + l);
     const u64 *r = R + (g * 2 + c) * (size_t)N;
-    limb_forward<LOGN, true, MODE>(sm, T, h, [&](int p) { return T.phalf + (T.q - red1(BFV_LD(r + p), T.q)); },
+    limb_forward<LOGN, true, MODE, MODE == 2>(sm, T, h, [&](int p) { return T.phalf + (T.q - red1(BFV_LD(r + p), T.q)); },
                        [&](int p, u64 v) { sm[padi(p & (M - 1))] = v; });
     __syncthreads();
     const u64 *u = U + ((g * 2 + c) * nqp + l) * (size_t)N + (size_t)h * M;
@@ -291,44 +291,71 @@ LIMB_KERNEL_M(LOGN, MODE) k_ks_moddown(const ModTab *__restrict__ mods, int L, c
 }
 
 // ------------------------------------------------------------------ bias + mask (Algorithm 1: mask)
-// Limb unit (g, l): C0 += Delta [b_j]_t; C *= NTT(centred lift of the one-hot plaintext at slot
-// (g0+g) mod N), whose coefficient k is N^-1 omega^(-e k) mod t, e the slot's exponent.
+// The one-hot plaintext at slot s has coefficient k = N^-1 omega^(-e k) mod t, e = e_s the
+// exponent of the slot's evaluation point (3^(s mod N/2) mod 2N, negated for s >= N/2). Since
+// omega^N = -1 it is the automorphism X -> X^f of the slot-0 mask (e = 1), f = e_s^-1 mod 2N, and
+// in evaluation form an automorphism is a permutation of positions: mask_s[p] = mask_0[auto_src(p,
+// f)]. The context keeps mask_0 per limb; a product's masks are gathered from it.
+
+// Limb unit l: maskev[l] = NTT_l(centred lift of the slot-0 mask) in Shoup form.
 template <int LOGN>
-LIMB_KERNEL(LOGN) k_bias_mask(const ModTab *__restrict__ mods, int L, int tmod, size_t g0, const ReqTable rt,
-                              const u32 *__restrict__ maskpow, u64 *C) {
+LIMB_KERNEL(LOGN) k_mask_base(const ModTab *__restrict__ mods, int tmod, const u32 *__restrict__ maskpow,
+                              shoup_t *maskev) {
     extern __shared__ u64 sm[];
     LIMB_INDEX(LOGN);
-    constexpr int NT = Split<LOGN>::NT;
-    const int l = (int)(unit % L);
-    const size_t gl = unit / L, gp = g0 + gl;
-    const int r = req_of(rt, gp);
-    const size_t g = gp - rt.pair_start[r];
-    const int j = (int)(g % rt.nY[r]), s = (int)(g % N);
+    const int l = (int)unit;
     const ModTab T = BFV_LD(mods + l);
     const u64 t = BFV_LD(&mods[tmod].q), th = (t - 1) / 2;
     const u32 twoN = 2u * N;
-    u32 e = 1, base = 3;                               // e = 3^(s mod N/2) mod 2N
-    for (u32 x = (u32)(s % (N / 2)); x; x >>= 1) {
-        if (x & 1) e = (e * base) & (twoN - 1);
-        base = (base * base) & (twoN - 1);
-    }
-    if (s >= N / 2) e = twoN - e;
     limb_forward<LOGN>(
         sm, T, h,
         [&](int p) {
-            const u32 idx = (twoN - ((e * (u32)p) & (twoN - 1))) & (twoN - 1);
-            const u64 v = BFV_LD(maskpow + idx);
+            const u64 v = BFV_LD(maskpow + ((twoN - (u32)p) & (twoN - 1)));
             return v <= th ? v : T.q - (t - v);
         },
-        [&](int p, u64 v) { sm[padi(p & (M - 1))] = v; });
-    __syncthreads();
+        [&](int p, u64 v) { BFV_ST(maskev + (size_t)l * N + p, make_shoup(v, T.q)); });
+}
+
+// grid.x = (g, l, part of kBmPts x 256 points): C[g][0][l] = (C[g][0][l] + Delta [b_j]_t) mask_s and
+// C[g][1][l] *= mask_s for the pair's slot s = (g0 + g) mod N.
+constexpr int kBmThreads = 256, kBmPts = 8;
+template <int LOGN>
+__global__ void __launch_bounds__(kBmThreads) k_bias_mask(const ModTab *__restrict__ mods, int L, size_t g0,
+                                                          const ReqTable rt, const shoup_t *__restrict__ maskev,
+                                                          u64 *C) {
+    constexpr int N = 1 << LOGN, PART = kBmThreads * kBmPts, NPART = N / PART;
+    const size_t x = blockIdx.x;
+    const int part = (int)(x % NPART), l = (int)((x / NPART) % L);
+    const size_t gl = x / ((size_t)NPART * L), gp = g0 + gl;
+    const int r = req_of(rt, gp);
+    const size_t g = gp - rt.pair_start[r];
+    const int j = (int)(g % rt.nY[r]), s = (int)(g % N);
+    const u64 q = BFV_LD(&mods[l].q);
+    // f = e_s^-1 mod 2N: 3 has order N/2 mod 2N, so 3^-y = 3^(N/2 - y); negated with e_s
+    const u32 twoN = 2u * N;
+    u32 f = 1, base = 3;
+    for (u32 y = (u32)((N / 2 - s % (N / 2)) % (N / 2)); y; y >>= 1) {
+        if (y & 1) f = (f * base) & (twoN - 1);
+        base = (base * base) & (twoN - 1);
+    }
+    if (s >= N / 2) f = twoN - f;
     const u64 bd = BFV_LD(rt.bias[r] + (size_t)j * L + l);
-    u64 *c0 = C + ((gl * 2 + 0) * L + l) * (size_t)N + (size_t)h * M;
-    u64 *c1 = C + ((gl * 2 + 1) * L + l) * (size_t)N + (size_t)h * M;
-    for (int p = threadIdx.x; p < M; p += NT) {
-        const u64 m = sm[padi(p)];
-        BFV_ST(c0 + p, mul_barrett(add_mod(BFV_LD(c0 + p), bd, T.q), m, T.q, T.mu, T.bits));
-        BFV_ST(c1 + p, mul_barrett(BFV_LD(c1 + p), m, T.q, T.mu, T.bits));
+    const shoup_t *mk = maskev + (size_t)l * N;
+    u64 *c0 = C + ((gl * 2 + 0) * L + l) * (size_t)N, *c1 = C + ((gl * 2 + 1) * L + l) * (size_t)N;
+    u64 a[kBmPts], b[kBmPts];
+    shoup_t m[kBmPts];
+#pragma unroll
+    for (int e = 0; e < kBmPts; ++e) {
+        const int p = part * PART + e * kBmThreads + threadIdx.x;
+        m[e] = BFV_LDG(mk + auto_src(p, f, LOGN));
+        a[e] = BFV_LD(c0 + p);
+        b[e] = BFV_LD(c1 + p);
+    }
+#pragma unroll
+    for (int e = 0; e < kBmPts; ++e) {
+        const int p = part * PART + e * kBmThreads + threadIdx.x;
+        BFV_ST(c0 + p, red1(mul_shoup(add_mod(a[e], bd, q), m[e], q), q));
+        BFV_ST(c1 + p, red1(mul_shoup(b[e], m[e], q), q));
     }
 }
 
@@ -386,6 +413,7 @@ void ks_step(const bfv_ctx *c, const bfv_packed_schedule &sc, size_t ng, u32 gal
         ProfScope pr(c, BFV_K_KS_PREP, st);
         if constexpr (PAIRS) {
             if (sc.prep_split == 2) launch_limbs<LOGN, 1>(k_ks_prep<LOGN, 1>, ng * L, st, 0, c->dmods, L, gal, (const u64 *)C, D);
+            else if (sc.prep_split == 3) launch_limbs<LOGN, 2>(k_ks_prep<LOGN, 2>, ng * L, st, 0, c->dmods, L, gal, (const u64 *)C, D);
             else launch_limbs<LOGN, 0>(k_ks_prep<LOGN, 0>, ng * L, st, 0, c->dmods, L, gal, (const u64 *)C, D);
         } else {
             launch_limbs<LOGN, 0>(k_ks_prep<LOGN, 0>, ng * L, st, 0, c->dmods, L, gal, (const u64 *)C, D);
@@ -404,6 +432,8 @@ void ks_step(const bfv_ctx *c, const bfv_packed_schedule &sc, size_t ng, u32 gal
         if constexpr (PAIRS) {
             if (sc.moddown_p_split == 3)
                 launch_limbs<LOGN, 3>(k_ks_moddown_p<LOGN, 3>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R);
+            else if (sc.moddown_p_split == 4)
+                launch_limbs<LOGN, 2>(k_ks_moddown_p<LOGN, 2>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R);
             else if (two) launch_limbs<LOGN, 1>(k_ks_moddown_p<LOGN, 1>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R);
             else launch_limbs<LOGN, 0>(k_ks_moddown_p<LOGN, 0>, ng * 2, st, 0, c->dmods, L, (const u64 *)U, R);
         } else {
@@ -416,6 +446,8 @@ void ks_step(const bfv_ctx *c, const bfv_packed_schedule &sc, size_t ng, u32 gal
         if constexpr (PAIRS) {
             if (sc.moddown_split == 1)
                 launch_limbs<LOGN, 0>(k_ks_moddown<LOGN, 0>, ng * 2 * L, st, 0, c->dmods, L, (const u64 *)U, (const u64 *)R, C);
+            else if (sc.moddown_split == 3)
+                launch_limbs<LOGN, 2>(k_ks_moddown<LOGN, 2>, ng * 2 * L, st, 0, c->dmods, L, (const u64 *)U, (const u64 *)R, C);
             else launch_limbs<LOGN, 1>(k_ks_moddown<LOGN, 1>, ng * 2 * L, st, 0, c->dmods, L, (const u64 *)U, (const u64 *)R, C);
         } else {
             launch_limbs<LOGN, 0>(k_ks_moddown<LOGN, 0>, ng * 2 * L, st, 0, c->dmods, L, (const u64 *)U, (const u64 *)R, C);
@@ -456,7 +488,8 @@ int run_packed(const bfv_ctx *c, const bfv_keys *k, int nreq, const u64 *const *
         for (int s = 0; s < k->ng; ++s)
             ks_step<LOGN>(c, pl.sched, ng, (u32)c->galois[s], k->gk_eval + (size_t)s * keyblock, C, D, U, R, st);
         { ProfScope pr(c, BFV_K_BIAS_MASK, st);
-        launch_limbs<LOGN>(k_bias_mask<LOGN>, ng * L, st, 0, c->dmods, L, nqp, g0, rt, (const u32 *)c->dmaskpow, C); }
+        k_bias_mask<LOGN><<<(unsigned)(ng * L * (N / (kBmThreads * kBmPts))), kBmThreads, 0, st>>>(c->dmods, L, g0, rt,
+                                                                                                c->dmaskev, C); }
         count_launch(c);
         // compression: the pairs of request r that land in its output o are one contiguous range
         for (int r = 0; r < nreq; ++r) {
@@ -497,9 +530,9 @@ bfv_packed_schedule default_schedule() {
 }
 
 bool schedule_ok(const bfv_packed_schedule &s) {
-    return s.pair_chunk >= 1 && (s.prep_split == 1 || s.prep_split == 2) &&
-           (s.modup_split == 2 || s.modup_split == 4) && s.moddown_p_split <= 3 &&
-           (s.moddown_split == 1 || s.moddown_split == 2);
+    return s.pair_chunk >= 1 && s.prep_split >= 1 && s.prep_split <= 3 &&
+           (s.modup_split == 2 || s.modup_split == 4) && s.moddown_p_split <= 4 &&
+           s.moddown_split >= 1 && s.moddown_split <= 3;
 }
 
 bfv_packed_schedule schedule_for(const bfv_ctx *c, size_t npairs, size_t chunk) {
@@ -590,6 +623,19 @@ int launch_packed_multi(const bfv_ctx *c, const bfv_keys *k, int nreq, const u64
 int launch_packed(const bfv_ctx *c, const bfv_keys *k, const u64 *X_ct, u64 *Y_ct, void *ws, const PackedPlan &plan,
                   cudaStream_t st) {
     return launch_packed_multi(c, k, 1, &X_ct, &Y_ct, ws, plan, st);
+}
+
+int launch_mask_base(const bfv_ctx *c, cudaStream_t st) {
+#define L_(LG) launch_limbs<LG>(k_mask_base<LG>, (size_t)c->L, st, 0, c->dmods, c->nqp, (const u32 *)c->dmaskpow, c->dmaskev)
+    switch (c->logN) {
+        case 12: L_(12); break;
+        case 13: L_(13); break;
+        case 14: L_(14); break;
+        case 15: L_(15); break;
+        default: return BFV_ERR_BAD_PARAMS;
+    }
+#undef L_
+    return last_err();
 }
 
 int launch_pair_export(const bfv_ctx *c, const PackedPlan &plan, const void *ws, size_t slot, u64 *ct_out,

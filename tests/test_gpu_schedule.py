@@ -28,7 +28,7 @@ def host(t):
 
 
 def schedules(chunk):
-    for p, m, mp, md in itertools.product((1, 2), (2, 4), (1, 2, 3), (1, 2)):
+    for p, m, mp, md in itertools.product((1, 2, 3), (2, 4), (1, 2, 3, 4), (1, 2, 3)):
         yield bfv.Schedule(chunk, p, m, mp, md)
 
 
@@ -57,7 +57,7 @@ def paper():
 
 
 def test_every_schedule_matches_oracle_tiny(tiny):
-    """128 pairs at N = 4096: all 24 split combinations, one chunk holding every pair and a
+    """128 pairs at N = 4096: all 72 split combinations, one chunk holding every pair and a
     ragged chunk of 5 pairs."""
     ctx, keys, P, okeys = tiny
     X, W, b, model, Xd, Y = run(ctx, keys, P, okeys, "tiny-16")
@@ -69,7 +69,7 @@ def test_every_schedule_matches_oracle_tiny(tiny):
 
 def test_every_schedule_matches_oracle_single_individual(paper):
     """One individual x 40,000 features x 16 classes at N = 16384 (the latency workload), where
-    every split takes effect: all 24 combinations bit-exact, and a ragged chunk of 3 pairs."""
+    every split takes effect: all 72 combinations bit-exact, and a ragged chunk of 3 pairs."""
     ctx, keys, P, okeys = paper
     X, W, b, model, Xd, Y = run(ctx, keys, P, okeys, "single-40k")
     for sc in schedules(16):
@@ -104,8 +104,9 @@ def test_autotuned_schedule_is_recorded_persisted_and_bit_exact(paper, tmp_path)
 
 def test_schedule_fields_are_checked(tiny):
     ctx, keys, P, okeys = tiny
-    for bad in (bfv.Schedule(0, 1, 2, 0, 2), bfv.Schedule(8, 3, 2, 0, 2), bfv.Schedule(8, 1, 3, 0, 2),
-                bfv.Schedule(8, 1, 2, 4, 2), bfv.Schedule(8, 1, 2, 0, 0)):
+    for bad in (bfv.Schedule(0, 1, 2, 0, 2), bfv.Schedule(8, 4, 2, 0, 2), bfv.Schedule(8, 0, 2, 0, 2),
+                bfv.Schedule(8, 1, 3, 0, 2), bfv.Schedule(8, 1, 2, 5, 2), bfv.Schedule(8, 1, 2, 0, 0),
+                bfv.Schedule(8, 1, 2, 0, 4)):
         with pytest.raises(bfv.BfvError):
             ctx.set_packed_schedule(5, bad)
 

@@ -259,6 +259,25 @@ def test_galois_elements_rotate_rows_and_swap(shape, small, tiny):
     assert np.all(oracle.decode(P, p) == int(v.sum()) % t)
 
 
+@pytest.mark.parametrize("shape", ["small", "tiny"])
+def test_slot_masks_are_automorphisms_of_the_slot0_mask(shape, small, tiny):
+    """The mask step's one-hot plaintext at slot s is X -> X^f applied to the one at slot 0,
+    f = e_s^-1 mod 2N (e_s the slot's exponent): the identity the library's bias/mask kernel uses
+    to gather every slot's mask from one transformed mask per limb."""
+    P = small if shape == "small" else tiny
+    N, t = P.N, P.t
+    e = oracle.slot_exponents(N)
+    one_hot = np.zeros(N, dtype=np.int64)
+    one_hot[0] = 1
+    mask0 = oracle.encode(P, one_hot)
+    for s in sorted({0, 1, 2, N // 4, N // 2 - 1, N // 2, N // 2 + 3, N - 1}):
+        one_hot[:] = 0
+        one_hot[s] = 1
+        f = pow(e[s], -1, 2 * N)
+        assert f == (pow(3, (N // 2 - s % (N // 2)) % (N // 2), 2 * N) * (1 if s < N // 2 else -1)) % (2 * N)
+        assert np.array_equal(oracle.encode(P, one_hot), oracle.automorph(mask0, t, f)), s
+
+
 # ----------------------------------------------------------------------------- keys and encryption
 
 def test_public_key_relation(small, small_keys):
