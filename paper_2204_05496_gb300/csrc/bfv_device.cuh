@@ -4,13 +4,15 @@
 // encoded weights, P^-1) are multiplied with Shoup's method (a precomputed companion
 // w' = floor(w 2^64 / q) turns the reduction into one high and two low 64-bit products);
 // variable x variable products use Barrett reduction with mu = floor(2^(2b) / q).
-// Butterflies keep values lazily in [0, 4q) (Cooley-Tukey forward) or [0, 2q)
-// (Gentleman-Sande inverse), Harvey's bounds.
+// Both transforms use Cooley-Tukey butterflies with Harvey's lazy bounds (values in [0, 4q), or
+// unreduced where only Shoup products consume them).
 //
 // NTT layout: forward transform of a (coefficient order) leaves at position p the value
-// a(psi^(2 brev(p) + 1)) (bit-reversed evaluation order); the inverse transform takes that
-// layout back to coefficients and folds in N^-1. Every evaluation-form array in the library
-// (keys, encoded weights, ciphertexts in flight) uses this layout.
+// a(psi^(2 brev(p) + 1)) (bit-reversed evaluation order). The inverse transform takes that
+// layout back to coefficients: a decimation-in-time cyclic transform with omega^-1 = psi^-2 on
+// the bit-reversed input gives b_k = sum_m B_m omega^(-m k) in natural order, and a post-twist by
+// N^-1 psi^-k gives a_k. Every evaluation-form array in the library (keys, encoded weights,
+// ciphertexts in flight) uses this layout.
 #pragma once
 #include <cstdint>
 #include <cuda_runtime.h>
@@ -26,7 +28,6 @@ typedef unsigned int u32;
 struct ModTab {
     u64 q, q2;              // q and 2q
     u64 ninv, ninvp;        // N^-1 mod q and its Shoup companion
-    u64 ilast, ilastp;      // psi^-brev(1) * N^-1 (last inverse stage) and companion
     u64 mu;                 // Barrett constant floor(2^(2 bits) / q)
     int bits;               // bit length of q
     int pad_;
@@ -37,7 +38,8 @@ struct ModTab {
     u64 r64, r64p;          // 2^64 mod q and companion
     u64 onep;               // floor(2^64 / q): Shoup companion of 1 (reduces any 64-bit word to [0, 2q))
     const ulonglong2 *fw;   // forward twiddles {psi^brev(k), Shoup companion}, k < N
-    const ulonglong2 *iw;   // inverse twiddles {psi^-brev(k), Shoup companion}
+    const ulonglong2 *dt;   // inverse twiddles: dt[h + j] = {omega^-(j N / 2h), companion}, h = 2^s, j < h
+    const ulonglong2 *tw;   // inverse post-twist {N^-1 psi^-k, companion}, k < N
 };
 
 // ------------------------------------------------------------------ bounds-checked debug build
@@ -149,16 +151,6 @@ __device__ __forceinline__ void ct_bfly_lazy(u64 &X, u64 &Y, u64 w, u64 wp, u64 
     X = x + t;
     Y = x - t + q2;
 }
-__device__ __forceinline__ void gs_bfly(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 q2) {
-    const u64 s = X + Y, d = X - Y + q2;
-    X = red2(s, q2);
-    Y = mul_shoup(d, w, wp, q);
-}
-__device__ __forceinline__ void gs_bfly_last(u64 &X, u64 &Y, u64 ni, u64 nip, u64 w, u64 wp, u64 q, u64 q2) {
-    const u64 s = X + Y, d = X - Y + q2;
-    X = mul_shoup(s, ni, nip, q);
-    Y = mul_shoup(d, w, wp, q);
-}
 
 // Shared-memory index with one pad word every 16 words (conflict-free strided groups).
 __device__ __forceinline__ int padi(int p) { return p + (p >> 4); }
@@ -187,31 +179,29 @@ __device__ __forceinline__ void fwd_radix(u64 (&x)[1 << R], int s, int gblock, c
     }
 }
 
-// Inverse Gentleman-Sande stages s0 .. s0+R-1 (stride 2^(s0+u)) on a full-size array;
-// block is the block index of size 2^(s0+R). When LASTSTAGE, the final stage of the whole
-// transform is stage s0+R-1 and N^-1 is folded into it. (Indexing by r keeps x[] in
-// registers; the repeated twiddle loads of one stage hit the same address.)
-template <int R, bool LASTSTAGE>
-__device__ __forceinline__ void inv_radix(u64 (&x)[1 << R], int s0, int block, int N,
-                                          const ulonglong2 *__restrict__ iw, u64 ni, u64 nip, u64 il, u64 ilp, u64 q,
+// Inverse (decimation-in-time) stages S .. S+R-1 on a group of 2^R values x[r] = a[base + r 2^S],
+// off = base mod 2^S: at stage S+u the pair (r, r + 2^u) sits at distance h = 2^(S+u) and its
+// twiddle is dt[h + j], j = off + (r mod 2^u) 2^S its position in the half-block. Lazy
+// butterflies: each stage adds less than 2q to the bound.
+template <int R>
+__device__ __forceinline__ void inv_radix(u64 (&x)[1 << R], int S, int off, const ulonglong2 *__restrict__ dt, u64 q,
                                           u64 q2) {
 #pragma unroll
     for (int u = 0; u < R; ++u) {
 #pragma unroll
-        for (int r = 0; r < (1 << R); ++r) {
-            if (r & (1 << u)) continue;
-            if (LASTSTAGE && u == R - 1) {
-                gs_bfly_last(x[r], x[r + (1 << u)], ni, nip, il, ilp, q, q2);
-            } else {
-                const int ti = (N >> (s0 + u + 1)) + (block << (R - 1 - u)) + (r >> (u + 1));
-                const ulonglong2 w = BFV_LDG(iw + ti);
-                gs_bfly(x[r], x[r + (1 << u)], w.x, w.y, q, q2);
+        for (int m = 0; m < (1 << u); ++m) {
+            const ulonglong2 w = BFV_LDG(dt + (1 << (S + u)) + off + (m << S));
+#pragma unroll
+            for (int k = 0; k < (1 << (R - 1 - u)); ++k) {
+                const int r = m + (k << (u + 1));
+                ct_bfly_lazy(x[r], x[r + (1 << u)], w.x, w.y, q, q2);
             }
         }
     }
 }
 
-// Pass schedule: LOGM stages in ceil(LOGM/4) passes of radix 2^3 or 2^4, larger first.
+// Pass schedule: LOGM stages in ceil(LOGM/4) passes of radix 2^3 or 2^4, R<P> larger first (the
+// inverse driver takes them in reverse order).
 template <int LOGM> struct Sched {
     static constexpr int NP = (LOGM + 3) / 4;
     template <int P> struct R { static constexpr int value = LOGM / NP + (P < LOGM % NP ? 1 : 0); };
@@ -270,22 +260,21 @@ __device__ __forceinline__ void ntt_forward_lazy(u64 *sm, const ModTab &T, int C
 
 // ------------------------------------------------------------------ inverse NTT driver
 //
-// Runs the first LOGM Gentleman-Sande stages of the size-2^LOGN inverse transform on the
-// sub-array `hidx` of M = 2^LOGM consecutive evaluation positions (their butterflies never
-// leave it). With LOGM = LOGN this is the whole transform and N^-1 is folded into its last
-// stage. load(p) must return values < 2q (local position p); store(p, v) receives local
-// position p in [0, q) -- for the whole transform, coefficient p.
-
-// ILP2: the two radix-8 groups a thread handles in a pass are interleaved.
-template <int LOGN, int LOGM, int NT, int P, int S, bool ILP2, class Load, class Store>
-__device__ __forceinline__ void inv_passes(u64 *sm, const ModTab &T, int hidx, Load &load, Store &store) {
+// The first LOGM decimation-in-time stages of the inverse transform on M = 2^LOGM consecutive
+// evaluation positions (their butterflies never leave them; the twiddles depend only on the
+// position inside a half-block, so any aligned sub-array runs the same code). Passes of radix
+// 2^3 or 2^4, smaller first (the first pass's twiddles are the same for every group). load(p)
+// must return values < 2q (local position p); store(p, v) receives local position p unreduced,
+// below (2 + 2 LOGM) q. The driver ends without a barrier after the last store.
+template <int LOGM, int NT, int P, int S, class Load, class Store>
+__device__ __forceinline__ void inv_passes(u64 *sm, const ModTab &T, Load &load, Store &store) {
     constexpr int NP = Sched<LOGM>::NP;
-    constexpr int R = Sched<LOGM>::template R<P>::value;
+    constexpr int R = Sched<LOGM>::template R<NP - 1 - P>::value;
     constexpr int M = 1 << LOGM;
     constexpr int TL = 1 << S;
     constexpr int G = M >> R;
     const u64 q = T.q, q2 = T.q2;
-#pragma unroll (ILP2 && R == 3 && G >= 2 * NT ? 2 : 1)
+#pragma unroll 1
     for (int g = threadIdx.x; g < G; g += NT) {
         const int block = g >> S, off = g & (TL - 1);
         const int base = block * (TL << R) + off;
@@ -295,23 +284,28 @@ __device__ __forceinline__ void inv_passes(u64 *sm, const ModTab &T, int hidx, L
             if constexpr (P == 0) x[r] = load(base + r * TL);
             else x[r] = sm[padi(base + r * TL)];
         }
-        inv_radix<R, LOGM == LOGN && P == NP - 1>(x, S, (hidx << (LOGM - S - R)) + block, 1 << LOGN, T.iw, T.ninv,
-                                                  T.ninvp, T.ilast, T.ilastp, q, q2);
+        inv_radix<R>(x, S, off, T.dt, q, q2);
 #pragma unroll
         for (int r = 0; r < (1 << R); ++r) {
-            if constexpr (P == NP - 1) store(base + r * TL, red1(x[r], q));
+            if constexpr (P == NP - 1) store(base + r * TL, x[r]);
             else sm[padi(base + r * TL)] = x[r];
         }
     }
     if constexpr (P < NP - 1) {
         __syncthreads();
-        inv_passes<LOGN, LOGM, NT, P + 1, S + R, ILP2>(sm, T, hidx, load, store);
+        inv_passes<LOGM, NT, P + 1, S + R>(sm, T, load, store);
     }
 }
 
-template <int LOGN, int NT, bool ILP2 = false, class Load, class Store>
+// The whole inverse transform of 2^LOGN points in one CTA: store(k, v) receives coefficient k in
+// [0, q) (the post-twist N^-1 psi^-k applied to values below (2 + 2 LOGN) q < 32q).
+template <int LOGN, int NT, class Load, class Store>
 __device__ __forceinline__ void ntt_inverse(u64 *sm, const ModTab &T, Load load, Store store) {
-    inv_passes<LOGN, LOGN, NT, 0, 0, ILP2>(sm, T, 0, load, store);
+    auto st = [&](int k, u64 v) {
+        const ulonglong2 w = BFV_LDG(T.tw + k);
+        store(k, red1(mul_shoup(v, w.x, w.y, T.q), T.q));
+    };
+    inv_passes<LOGN, NT, 0, 0>(sm, T, load, st);
 }
 
 // ------------------------------------------------------------------ index maps
@@ -480,25 +474,34 @@ __device__ __forceinline__ void limb_forward(u64 *sm, const ModTab &T, int h, Lo
 // (< 2q) for the positions this CTA owns; store(k, v) receives the coefficients k it owns,
 // in [0, q). With S = 2 every thread of the cluster must call it (two cluster barriers), and
 // sm must not be written by the caller between the call and the caller's next barrier.
-template <int LOGN, int MODE = 0, bool ILP2 = false, class Load, class Store>
+template <int LOGN, int MODE = 0, class Load, class Store>
 __device__ __forceinline__ void limb_inverse(u64 *sm, const ModTab &T, int h, Load load, Store store) {
     using SP = Split<LOGN, MODE>;
     if constexpr (SP::S == 1) {
-        ntt_inverse<LOGN, SP::NT, ILP2>(sm, T, load, store);
+        ntt_inverse<LOGN, SP::NT>(sm, T, load, store);
     } else {
         constexpr int M = SP::M;
         auto ld = [&](int p) { return load(h * M + p); };
         auto st = [&](int p, u64 v) { sm[padi(p)] = v; };
-        inv_passes<LOGN, SP::LOGM, SP::NT, 0, 0, ILP2>(sm, T, h, ld, st);
+        inv_passes<SP::LOGM, SP::NT, 0, 0>(sm, T, ld, st);
+        __syncthreads();
+        const u64 q = T.q, q2 = T.q2;
+        // last stage (distance M, across the pair): u = x[p] on CTA 0, t = dt[M + p] x[M + p] on CTA 1
+        if (h == 1) {
+#pragma unroll 4
+            for (int p = threadIdx.x; p < M; p += SP::NT) {
+                const ulonglong2 w = BFV_LDG(T.dt + M + p);
+                sm[padi(p)] = mul_shoup(sm[padi(p)], w.x, w.y, q);
+            }
+        }
         cluster_sync();
         const u32 peer = cluster_map(sm, (u32)(h ^ 1));
-        const u64 q = T.q, q2 = T.q2;
 #pragma unroll 4
         for (int p = threadIdx.x; p < M; p += SP::NT) {
             const u64 own = sm[padi(p)], other = ld_cluster(peer + 8u * (u32)padi(p));
-            const u64 x0 = h == 0 ? own : other, x1 = h == 0 ? other : own;
-            const u64 v = h == 0 ? mul_shoup(x0 + x1, T.ninv, T.ninvp, q) : mul_shoup(x0 - x1 + q2, T.ilast, T.ilastp, q);
-            store(h * M + p, red1(v, q));
+            const u64 x = h == 0 ? own + other : other - own + q2;   // u + t, or u - t (below 32q)
+            const ulonglong2 w = BFV_LDG(T.tw + h * M + p);
+            store(h * M + p, red1(mul_shoup(x, w.x, w.y, q), q));
         }
         cluster_sync();
     }

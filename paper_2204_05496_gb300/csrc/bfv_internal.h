@@ -49,7 +49,7 @@ struct bfv_ctx {
     std::vector<u64> primes;         // L+1 (index L = P)
     std::vector<ModTab> hmods;       // host copy, nqp + 1 entries (index nqp = t)
     ModTab *dmods = nullptr;         // device copy
-    u64 *dtw = nullptr;              // twiddle tables [nqp+1][4][N]
+    u64 *dtw = nullptr;              // twiddle tables [nqp+1][6][N]
     u32 *dslot = nullptr;            // [N] evaluation position of slot l (mod-t transform)
     u32 *dmaskpow = nullptr;         // [2N] N^-1 omega^i mod t
     shoup_t *dmaskev = nullptr;      // [L][N] evaluation form of the slot-0 one-hot mask (Shoup form)
@@ -157,7 +157,7 @@ struct BoundsCall {
     explicit BoundsCall(const bfv_ctx *c) : shrink((size_t)c->inject_shrink) {
         t.err = c->derr;
         add(c->dmods, sizeof(ModTab) * (c->nqp + 1));
-        add(c->dtw, sizeof(u64) * (size_t)(c->nqp + 1) * 4 * c->N);
+        add(c->dtw, sizeof(u64) * (size_t)(c->nqp + 1) * 6 * c->N);
         add(c->dslot, sizeof(u32) * c->N);
         add(c->dmaskpow, sizeof(u32) * 2 * c->N);
         add(c->dmaskev, sizeof(shoup_t) * (size_t)c->L * c->N);

@@ -303,7 +303,7 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
     mw_divmod_small(Qdt, c->t);
 
     // twiddles and per-modulus constants
-    std::vector<u64> tw((size_t)nmod * 4 * N);
+    std::vector<u64> tw((size_t)nmod * 6 * N);
     c->hmods.assign(nmod, ModTab{});
     c->delta_host.assign(c->L, 0);
     int rc = dalloc(&c->dtw, tw.size());
@@ -318,23 +318,31 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
             c->omega = psi;
         }
         const u64 psii = inv_h(psi, q);
-        // [j][fw pairs (2N words)][iw pairs (2N words)], each pair {w, w'}
-        u64 *fwv = &tw[(size_t)j * 4 * N], *iwv = &tw[(size_t)j * 4 * N + 2 * N];
+        // [j][fw pairs (2N words)][dt pairs (2N words)][tw pairs (2N words)], each pair {w, w'}:
+        // fw[k] = psi^brev(k); dt[h + j] = omega^-(j N / 2h) = psi^-(j N / h) for h = 2^s, j < h;
+        // tw[k] = N^-1 psi^-k
+        u64 *fwv = &tw[(size_t)j * 6 * N], *dtv = fwv + 2 * N, *twv = fwv + 4 * N;
         std::vector<u64> pw(N), ipw(N);
         pw[0] = ipw[0] = 1;
         for (u64 i = 1; i < N; ++i) { pw[i] = mulmod_h(pw[i - 1], psi, q); ipw[i] = mulmod_h(ipw[i - 1], psii, q); }
+        const u64 ninv = inv_h(N % q, q);
+        dtv[0] = 1; dtv[1] = shoup_h(1, q);   // unused
+        for (u64 h = 1; h < N; h <<= 1)
+            for (u64 i = 0; i < h; ++i) {
+                const u64 w = ipw[i * (N / h)];
+                dtv[2 * (h + i)] = w; dtv[2 * (h + i) + 1] = shoup_h(w, q);
+            }
         for (u64 k = 0; k < N; ++k) {
             const u64 b = brev_h(k, c->logN);
             fwv[2 * k] = pw[b]; fwv[2 * k + 1] = shoup_h(pw[b], q);
-            iwv[2 * k] = ipw[b]; iwv[2 * k + 1] = shoup_h(ipw[b], q);
+            const u64 t = mulmod_h(ninv, ipw[k], q);
+            twv[2 * k] = t; twv[2 * k + 1] = shoup_h(t, q);
         }
         ModTab &T = c->hmods[j];
         T.q = q;
         T.q2 = 2 * q;
-        T.ninv = inv_h(N % q, q);
+        T.ninv = ninv;
         T.ninvp = shoup_h(T.ninv, q);
-        T.ilast = mulmod_h(iwv[2], T.ninv, q);
-        T.ilastp = shoup_h(T.ilast, q);
         T.bits = ilog2_h(q + 1);
         T.mu = (u64)(((u128)1 << (2 * T.bits)) / q);
         if (j < c->L) {
@@ -352,9 +360,10 @@ int bfv_setup(const bfv_params *p, bfv_ctx **out) {
         T.r64 = (u64)(((u128)1 << 64) % q);
         T.r64p = shoup_h(T.r64, q);
         T.onep = shoup_h(1, q);
-        const u64 *base = c->dtw + (size_t)j * 4 * N;
+        const u64 *base = c->dtw + (size_t)j * 6 * N;
         T.fw = (const ulonglong2 *)base;
-        T.iw = (const ulonglong2 *)(base + 2 * N);
+        T.dt = (const ulonglong2 *)(base + 2 * N);
+        T.tw = (const ulonglong2 *)(base + 4 * N);
     }
     if (cudaMemcpy(c->dtw, tw.data(), tw.size() * 8, cudaMemcpyHostToDevice) != cudaSuccess) { free_ctx(c); return BFV_ERR_CUDA; }
     if ((rc = dalloc(&c->dmods, nmod))) { free_ctx(c); return rc; }

@@ -90,7 +90,7 @@ LIMB_KERNEL_M(LOGN, MODE) k_ks_prep(const ModTab *__restrict__ mods, int L, u32 
     // coalesced line prefetches first (each CTA of the group a share of the lines)
     for (int i = threadIdx.x + h * NT; i < N / 16; i += S * NT)
         asm volatile("prefetch.global.L2 [%0];" ::"l"(limb + 16 * i));
-    limb_inverse<LOGN, MODE, MODE != 1>(sm, T, h, [&](int p) { return BFV_LD(limb + auto_src(p, gal, LOGN)); },
+    limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return BFV_LD(limb + auto_src(p, gal, LOGN)); },
                              [&](int p, u64 v) { BFV_ST(dst + p, v); });
 }
 
@@ -253,7 +253,7 @@ LIMB_KERNEL_M(LOGN, MODE) k_ks_moddown_p(const ModTab *__restrict__ mods, int L,
     const ModTab T = BFV_LD(mods + L);
     const u64 *src = U + (gc * nqp + L) * (size_t)N;
     u64 *dst = R + gc * N;
-    limb_inverse<LOGN, MODE, MODE != 1>(sm, T, h, [&](int p) { return BFV_LD(src + p); },
+    limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return BFV_LD(src + p); },
                              [&](int p, u64 v) { BFV_ST(dst + p, add_mod(v, T.phalf, T.q)); });
 }
 

@@ -29,7 +29,7 @@ LIMB_KERNEL(LOGN) k_ntt_limbs(const ModTab *__restrict__ mods, int L, const u64 
     if constexpr (FWD)
         limb_forward<LOGN, true>(sm, T, h, [&](int p) { return BFV_LD(src + p); }, [&](int p, u64 v) { BFV_ST(dst + p, v); });
     else
-        limb_inverse<LOGN, 0, true>(sm, T, h, [&](int p) { return BFV_LD(src + p); }, [&](int p, u64 v) { BFV_ST(dst + p, v); });
+        limb_inverse<LOGN>(sm, T, h, [&](int p) { return BFV_LD(src + p); }, [&](int p, u64 v) { BFV_ST(dst + p, v); });
 }
 
 // Inverse transform of evaluation-form {value, companion} arrays [limb][N]; limb x uses
@@ -264,14 +264,14 @@ LIMB_KERNEL_M(LOGN, MODE) k_enc_main(const ModTab *__restrict__ mods, int L, con
         }
     }
     __syncthreads();
-    limb_inverse<LOGN, MODE, MODE != 1>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) {
+    limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; }, [&](int p, u64 v) {
         const u64 r = add_mod(v, lift_small(BFV_LD(e1 + p), T.q), T.q);
         // plaintext coefficients lie in [0, t) with t < q; reduce other words only when needed
         const u64 mv = BFV_LD(m + p), mr = mv < T.q ? mv : mv % T.q;
         BFV_ST(out0 + p, add_mod(r, red1(mul_shoup(mr, T.delta, T.deltap, T.q), T.q), T.q));
     });
     __syncthreads();
-    limb_inverse<LOGN, MODE, MODE != 1>(sm, T, h, [&](int p) { return BFV_LD(out1 + p); },
+    limb_inverse<LOGN, MODE>(sm, T, h, [&](int p) { return BFV_LD(out1 + p); },
                              [&](int p, u64 v) { BFV_ST(out1 + p, add_mod(v, lift_small(BFV_LD(e2 + p), T.q), T.q)); });
 }
 
@@ -292,7 +292,7 @@ LIMB_KERNEL(LOGN) k_dec_inner(const ModTab *__restrict__ mods, int L, const shou
                        [&](int p, u64 v) { sm[padi(p & (M - 1))] = mul_shoup(v, BFV_LD(s + p), T.q); });
     __syncthreads();
     u64 *dst = x + (c * L + l) * (size_t)N;
-    limb_inverse<LOGN, 0, true>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; },
+    limb_inverse<LOGN>(sm, T, h, [&](int p) { return sm[padi(p & (M - 1))]; },
                        [&](int p, u64 v) { BFV_ST(dst + p, add_mod(v, BFV_LD(c0 + p), T.q)); });
 }
 
