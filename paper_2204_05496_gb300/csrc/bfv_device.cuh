@@ -390,9 +390,10 @@ constexpr int nt_for(int logm) { return logm >= 13 ? 512 : (logm == 12 ? 256 : 1
 // positions and the coefficients [h M, (h+1) M), M = N/2:
 //  * forward: the first Cooley-Tukey stage (distance N/2) is done in the load -- each CTA
 //    reads both halves of the input -- and CTA h runs the remaining stages on its half;
-//  * inverse: CTA h runs the first log2 N - 1 Gentleman-Sande stages on its own half of the
+//  * inverse: CTA h runs the first log2 N - 1 decimation-in-time stages on its own half of the
 //    evaluation points (their butterflies stay inside it); after a cluster barrier the last
-//    stage (distance N/2, with N^-1) reads the partner's half from distributed shared memory.
+//    stage (distance N/2) reads the partner's half from distributed shared memory and applies
+//    the post-twist.
 // For N <= 16384, S = 1 and these are the single-CTA transforms.
 // MODE 1 also splits an N = 16384 limb over two CTAs of 256 threads (68 KB of shared memory
 // each), three of which share an SM (80 registers each) so that one's barrier waits overlap the
