@@ -141,10 +141,11 @@ __device__ __forceinline__ void ct_bfly(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u6
     X = x + t;
     Y = x - t + q2;
 }
-// Without the reduction of X: both outputs exceed the inputs' bound by less than 2q (t < 2q),
-// so a transform entered below 4q leaves below (4 + 2 stages) q -- below 32q < 2^60 for the
-// 15 stages of N = 32768 and primes below 2^55. Only for outputs consumed by Shoup products
-// (which take any 64-bit input).
+// Without the reduction of X: both outputs exceed the inputs' bound by less than 2q (t < 2q).
+// The lazy forward runs at most 14 such stages after an entry below 4q (at N = 32768 the first
+// stage is the reducing fold), the inverse at most 15 after an entry below 2q: both stay below
+// 32q < 2^64 for the primes below 2^59 the library accepts. The outputs then meet only Shoup
+// products (which take any 64-bit input) or the inverse's post-twist.
 __device__ __forceinline__ void ct_bfly_lazy(u64 &X, u64 &Y, u64 w, u64 wp, u64 q, u64 q2) {
     const u64 t = mul_shoup(Y, w, wp, q);
     const u64 x = X;
