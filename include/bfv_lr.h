@@ -152,9 +152,8 @@ int bfv_noise_budget(bfv_ctx *ctx, const bfv_keys *keys, const uint64_t *ct, siz
 
 /* Decryption that allocates nothing (no paper counterpart; a library convenience). Some
  * callers cannot call cudaMalloc: it may synchronise the whole device and can fail under a
- * fixed memory reservation, so latency-critical serving threads, code that runs while a
- * stream is being captured into a CUDA graph, and processes whose device memory belongs to
- * another allocator need an entry point that never allocates. This one computes exactly
+ * fixed memory reservation, so latency-critical serving threads and processes whose device
+ * memory belongs to another allocator need an entry point that never allocates. This one computes exactly
  * what bfv_decrypt computes but keeps its scratch (the per-limb residues) in a fixed 4 MiB
  * device array inside the library, which every GPU that loads the library holds until the
  * process exits. Limits and rules:
